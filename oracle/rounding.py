@@ -1,0 +1,117 @@
+"""Sketches of a tensor already in TTN format (Sec. 7, "Structured sketchings
+for TTNN and STTNN").  ORACLE: test infrastructure only.
+
+With Khatri-Rao DRMs every sketch entry is a contraction of the input network
+with rank-one vectors (the entrywise formulas for Omega_{1,1}, Psi_{1,1} of
+Sec. 7), so the sketches are formed by two sweeps over the input cores C_t
+(axis order: root (R_c1..R_cm), transfer (R_t, R_c1..R_cm), leaf (R_t, n..)):
+
+up   UX_t[a, j] = sum C_t[a, b_1..b_m] prod_k UX_{c_k}[b_k, j]
+     (leaf: sum_i C_t[a, i] kr(X_mu : mu in t)[i, j]); UK_t likewise with the
+     Y_mu (the Khatri-Rao Y_t of t itself, columns shared).
+down E_{c_k}[b_k, j] = sum C_t[a, b..] E_t[a, j] prod_{k' != k} UX_{c_k'}[b_k', j]
+     (root: no E_t factor).
+Omega_t = UK_t[:, :s_t]^T E_t[:, :r_t];   Psi_leaf = C_t^T E_t;
+Psi_t[a_1..a_m, j] = sum C_t[a, b..] E_t[a, j] prod_k UY_{c_k}[b_k, a_k];
+Psi_root[a_1..a_m] = sum C_root[b..] prod_k UY_{c_k}[b_k, a_k],
+with UY_c = UK_c[:, :s_c], or the raw leaf core C_c for an identity node c.
+
+The DRMs are those of ``ttnn.Drm(..., variant="round")`` (no second rounding
+of KR blocks: nothing here multiplies a dense tensor on tensor cores).
+"""
+import numpy as np
+
+from .ttnn import kr
+
+_B = "bcdefghi"      # child rank letters
+_O = "pqstuvwx"      # child output (sketch) letters
+
+
+def _up(C, mats):
+    """sum_b C[a, b_1..b_m] prod_k mats[k][b_k, j]  ->  (a, j)."""
+    m = len(mats)
+    spec = "a" + _B[:m] + "," + ",".join(_B[k] + "j" for k in range(m)) + "->aj"
+    return np.einsum(spec, C, *mats, optimize=True)
+
+
+def _down(C, k, ux, Et):
+    """E_{c_k}[b_k, j] from the parent's core, E_t (None at the root) and the
+    siblings' UX."""
+    m = len(ux)
+    ins, ops = [], []
+    if Et is None:
+        ins.append(_B[:m])
+        ops.append(C)
+    else:
+        ins += ["a" + _B[:m], "aj"]
+        ops += [C, Et]
+    for i in range(m):
+        if i != k:
+            ins.append(_B[i] + "j")
+            ops.append(ux[i])
+    return np.einsum(",".join(ins) + "->" + _B[k] + "j", *ops, optimize=True)
+
+
+def _psi(C, Et, uy):
+    """sum_{a,b} C[a, b..] E_t[a, j] prod_k uy[k][b_k, o_k] -> (o_1..o_m, j);
+    at the root (Et None) -> (o_1..o_m)."""
+    m = len(uy)
+    ins, ops = [], []
+    if Et is None:
+        ins.append(_B[:m])
+        ops.append(C)
+        out = _O[:m]
+    else:
+        ins += ["a" + _B[:m], "aj"]
+        ops += [C, Et]
+        out = _O[:m] + "j"
+    for k in range(m):
+        ins.append(_B[k] + _O[k])
+        ops.append(uy[k])
+    return np.einsum(",".join(ins) + "->" + out, *ops, optimize=True)
+
+
+def sketch_ttn_input(cores_in, tree, drm):
+    """All sketches of the TTN-format tensor given by cores_in (user-indexed),
+    for the target ranks of `tree` and the DRMs of `drm` (same tree shape).
+    Same return convention as ttnn.sketch_ttnn."""
+    C = {v: np.asarray(c, dtype=np.float64) for v, c in cores_in.items()}
+    UX, UK = {}, {}
+    for v in reversed(tree.lex):               # children before parents
+        if v == tree.root:
+            continue
+        nd = tree.node(v)
+        if nd.is_leaf:
+            C2 = C[v].reshape(C[v].shape[0], -1)
+            UX[v] = C2 @ kr([drm.X[mu] for mu in range(nd.lo, nd.hi)])
+            UK[v] = C2 @ kr([drm.Y[mu] for mu in range(nd.lo, nd.hi)])
+        else:
+            UX[v] = _up(C[v], [UX[c] for c in nd.children])
+            UK[v] = _up(C[v], [UK[c] for c in nd.children])
+
+    def uy(c):
+        nc = tree.node(c)
+        if nc.identity:
+            return C[c].reshape(C[c].shape[0], -1)
+        return UK[c][:, :nc.s]
+
+    E = {}
+    for v in tree.lex:                          # parents before children
+        nd = tree.node(v)
+        if nd.is_leaf:
+            continue
+        ux = [UX[c] for c in nd.children]
+        for k, c in enumerate(nd.children):
+            E[c] = _down(C[v], k, ux, None if v == tree.root else E[v])
+    Om, Ps = {}, {}
+    for v in tree.sketched():
+        nd = tree.node(v)
+        Et = E[v][:, :nd.r]
+        Om[v] = UK[v][:, :nd.s].T @ Et
+        if nd.is_leaf:
+            Ps[v] = C[v].reshape(C[v].shape[0], -1).T @ Et
+        else:
+            Ps[v] = _psi(C[v], Et, [uy(c) for c in nd.children])
+    root = tree.node(tree.root)
+    Pr = _psi(C[tree.root], None, [uy(c) for c in root.children])
+    return Om, Ps, Pr

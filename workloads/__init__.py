@@ -1,0 +1,276 @@
+"""Seeded synthetic inputs shared by the tests, ``bench.py`` and the oracle's
+timing leg.  This module holds input synthesis only (trees, tensors, updates)
+and none of TTNN's arithmetic; it imports neither the oracle nor the CUDA
+library.
+
+Trees are returned as (parent, leaf_modes, identity) lists in the format of
+the library's ``ttnn_tree`` (0-based modes, parent -1 for the root).
+
+Workload recipes (the paper's experiments use formula / synthetic generators,
+Sec. 8; these mirror their shapes):
+* exact_ttn: N(0,1) cores on a tree, contracted to a dense tensor, plus i.i.d.
+  Gaussian noise at a given relative Frobenius norm (order-4, 24^4 case).
+* inv_sum: f(x) = 1 / (x_1 + ... + x_d) on the uniform grid x = 1 + i/(n-1) of
+  [1, 2]^d (fast-decaying multilinear spectrum; the paper's Hilbert tensor
+  1/(1 + i_1 + ... + i_d) of Sec. 8 is the same family).
+* cp_term / box_update: rank-2 CP terms with N(0,1) factors and dense
+  sub-blocks of N(0, 0.01) noise (streamed order-6 case).
+* rounding_input: TTN cores of rank R_dom + R_noise as a block-diagonal direct
+  sum, N(0, 1/R) entries, the dominant block scaled by 100 (order-8 rounding).
+"""
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# trees
+# ---------------------------------------------------------------------------
+def from_nested(spec):
+    """Nested tuples of modes -> (parent, leaf_modes, identity).  An int is a
+    single-mode leaf, a list a multi-mode leaf, a tuple an internal node."""
+    parent, leaf_modes = [], []
+
+    def add(s, p):
+        v = len(parent)
+        parent.append(p)
+        if isinstance(s, int):
+            leaf_modes.append([s])
+        elif isinstance(s, list):
+            leaf_modes.append(list(s))
+        else:
+            leaf_modes.append([])
+            for c in s:
+                add(c, v)
+        return v
+
+    add(spec, -1)
+    return parent, leaf_modes, [False] * len(parent)
+
+
+def balanced_binary(d):
+    """Balanced binary tree: the left child takes ceil(|t|/2) contiguous modes."""
+    def build(lo, hi):
+        if hi - lo == 1:
+            return lo
+        mid = lo + (hi - lo + 1) // 2
+        return (build(lo, mid), build(mid, hi))
+    return from_nested(build(0, d))
+
+
+def tucker(d):
+    """Star tree: root -> {0}, ..., {d-1}."""
+    return from_nested(tuple(range(d)))
+
+
+def tensor_train(d):
+    """Caterpillar {0..k} -> {0..k-1}, {k}; the single-mode leaves {k}, k >= 1,
+    are identity nodes, so the sketched nodes are the prefixes {0..k-1}."""
+    spec = 0
+    for k in range(1, d):
+        spec = (spec, k)
+    parent, leaf_modes, identity = from_nested(spec)
+    identity = [bool(lm) and lm[0] >= 1 for lm in leaf_modes]
+    return parent, leaf_modes, identity
+
+
+def toy_tree():
+    """The paper's 6-mode example index tree (Sec. 3, first figure):
+    {1..6} -> {1,2,3}, {4}, {5,6}; {1,2,3} -> {1,2}, {3}; {1,2} -> {1}, {2};
+    {5,6} -> {5}, {6} (0-based here)."""
+    return from_nested((((0, 1), 2), 3, (4, 5)))
+
+
+def node_modes(parent, leaf_modes):
+    """Sorted mode list of every node (union over its subtree's leaves)."""
+    n = len(parent)
+    modes = [list(leaf_modes[v]) for v in range(n)]
+    order = sorted(range(n), key=lambda v: -depth_of(parent, v))
+    for v in order:
+        if parent[v] >= 0:
+            modes[parent[v]].extend(modes[v])
+    return [sorted(m) for m in modes]
+
+
+def depth_of(parent, v):
+    k = 0
+    while parent[v] >= 0:
+        v = parent[v]
+        k += 1
+    return k
+
+
+def children_of(parent, leaf_modes):
+    modes = node_modes(parent, leaf_modes)
+    ch = [[] for _ in parent]
+    for v, p in enumerate(parent):
+        if p >= 0:
+            ch[p].append(v)
+    for c in ch:
+        c.sort(key=lambda v: modes[v][0])
+    return ch, modes
+
+
+# ---------------------------------------------------------------------------
+# dense tensors
+# ---------------------------------------------------------------------------
+def ttn_cores(tree, dims, ranks, rng, scale=1.0):
+    """Random N(0, scale^2) TTN cores: root (r_c..), transfer (r_t, r_c..),
+    leaf (r_t, n_mu..).  ranks[v] is node v's edge rank (root ignored)."""
+    parent, leaf_modes, _ = tree
+    ch, modes = children_of(parent, leaf_modes)
+    cores = {}
+    for v in range(len(parent)):
+        if not ch[v]:
+            shape = [ranks[v]] + [dims[m] for m in modes[v]]
+        else:
+            shape = ([] if parent[v] < 0 else [ranks[v]]) + [ranks[c] for c in ch[v]]
+        cores[v] = rng.standard_normal(shape) * scale
+    return cores
+
+
+def ttn_dense(tree, cores):
+    """Contract a TTN to its dense tensor (modes in increasing order)."""
+    parent, leaf_modes, _ = tree
+    ch, _ = children_of(parent, leaf_modes)
+    root = parent.index(-1)
+
+    def full(v):
+        out = cores[v]
+        for c in ch[v]:
+            out = np.tensordot(out, full(c), axes=([1], [0]))
+        return out
+
+    out = cores[root]
+    for c in ch[root]:
+        out = np.tensordot(out, full(c), axes=([0], [0]))
+    return out
+
+
+def exact_ttn(tree, dims, ranks, seed, noise=0.0):
+    """Dense tensor with exact TTN ranks <= ranks, plus Gaussian noise of
+    relative Frobenius norm `noise`.  Returns (T, cores)."""
+    rng = np.random.default_rng(seed)
+    cores = ttn_cores(tree, dims, ranks, rng)
+    T = ttn_dense(tree, cores)
+    if noise > 0:
+        E = rng.standard_normal(T.shape)
+        T = T + E * (noise * np.linalg.norm(T) / np.linalg.norm(E))
+    return T, cores
+
+
+def inv_sum(d, n, dtype=np.float64):
+    """A[i_1..i_d] = 1 / sum_mu (1 + i_mu/(n-1)) in binary64, cast to dtype."""
+    x = 1.0 + np.arange(n, dtype=np.float64) / (n - 1)
+    s = np.zeros([n] * d)
+    for mu in range(d):
+        sh = [1] * d
+        sh[mu] = n
+        s = s + x.reshape(sh)
+    return (1.0 / s).astype(dtype)
+
+
+def inv_sum_torch(d, n, device, dtype):
+    """The same tensor as inv_sum, built on a torch device (same operation
+    order: binary64 sum over modes in increasing order, reciprocal, cast)."""
+    import torch
+    x = 1.0 + torch.arange(n, dtype=torch.float64, device=device) / (n - 1)
+    s = torch.zeros([n] * d, dtype=torch.float64, device=device)
+    for mu in range(d):
+        sh = [1] * d
+        sh[mu] = n
+        s = s + x.reshape(sh)
+    return (1.0 / s).to(dtype)
+
+
+def gaussian(shape, seed, scale=1.0):
+    return np.random.default_rng(seed).standard_normal(shape) * scale
+
+
+# ---------------------------------------------------------------------------
+# streamed updates
+# ---------------------------------------------------------------------------
+def cp_term(dims, rank, rng):
+    """Rank-`rank` CP term: weights 1, factors a_mu (n_mu x rank) ~ N(0,1)."""
+    return np.ones(rank), [rng.standard_normal((n, rank)) for n in dims]
+
+
+def cp_dense(weights, factors):
+    d = len(factors)
+    out = 0.0
+    for q in range(len(weights)):
+        t = np.array(weights[q])
+        for mu in range(d):
+            t = np.multiply.outer(t, factors[mu][:, q])
+        out = out + t
+    return out
+
+
+def box_update(dims, varying, extent, rng, sigma=0.1):
+    """Dense sub-block: `varying` modes span `extent` consecutive indices from
+    a uniform offset, the other modes are fixed at a uniform index (extent 1).
+    Returns (offset, extent_per_mode, data)."""
+    d = len(dims)
+    off = [int(rng.integers(0, n)) for n in dims]
+    ext = [1] * d
+    for mu in varying:
+        ext[mu] = extent
+        off[mu] = int(rng.integers(0, dims[mu] - extent + 1))
+    data = rng.standard_normal(ext) * sigma
+    return off, ext, data
+
+
+def embed_box(dims, off, ext, data):
+    T = np.zeros(dims)
+    sl = tuple(slice(o, o + e) for o, e in zip(off, ext))
+    T[sl] = data
+    return T
+
+
+def streaming_updates(dims, n_updates, seed, box_modes=3, box_extent=32, cp_rank=2):
+    """The streamed order-6 workload: each update is one rank-2 CP term
+    (N(0,1) factors) plus one dense box of N(0, 0.01) noise over `box_modes`
+    distinct uniformly chosen modes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    d = len(dims)
+    for _ in range(n_updates):
+        w, f = cp_term(dims, cp_rank, rng)
+        modes = sorted(rng.choice(d, size=box_modes, replace=False).tolist())
+        off, ext, data = box_update(dims, modes, min(box_extent, min(dims)), rng)
+        out.append({"cp_weights": w, "cp_factors": f, "box_offset": off,
+                    "box_extent": ext, "box_data": data})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# TTN rounding input
+# ---------------------------------------------------------------------------
+def rounding_input(tree, dims, r_dom, r_noise, seed, dom_scale=100.0):
+    """TTN with every edge of rank r_dom + r_noise: cores are block-diagonal
+    direct sums of a dominant (rank r_dom) and a noise (rank r_noise) TTN,
+    entries N(0, 1/R); the dominant root block is scaled by dom_scale."""
+    parent, leaf_modes, _ = tree
+    ch, modes = children_of(parent, leaf_modes)
+    rng = np.random.default_rng(seed)
+    R = r_dom + r_noise
+    cores = {}
+    for v in range(len(parent)):
+        is_root = parent[v] < 0
+        blocks = []
+        for b, rb in ((0, r_dom), (1, r_noise)):
+            if not ch[v]:
+                shape = [rb] + [dims[m] for m in modes[v]]
+            else:
+                shape = ([] if is_root else [rb]) + [rb] * len(ch[v])
+            blocks.append(rng.standard_normal(shape) / np.sqrt(R))
+        if not ch[v]:
+            C = np.concatenate(blocks, axis=0)
+        else:
+            shape = ([] if is_root else [R]) + [R] * len(ch[v])
+            C = np.zeros(shape)
+            for b, (lo, rb) in enumerate(((0, r_dom), (r_dom, r_noise))):
+                sl = tuple(slice(lo, lo + rb) for _ in shape)
+                C[sl] = blocks[b]
+            if is_root:
+                C[tuple(slice(0, r_dom) for _ in shape)] *= dom_scale
+        cores[v] = C
+    return cores
