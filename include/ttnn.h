@@ -1,0 +1,254 @@
+/*
+ * ttnn.h -- C ABI of the GB300 (sm_103a) implementation of tree tensor network
+ * Nystrom (TTNN) and its sequential variant STTNN, after Bucci & Verzella,
+ * "Randomized algorithms for streaming low-rank approximation in tree tensor
+ * network format", arXiv:2412.06111.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All pointers are plain host or device pointers as stated per argument; no
+ *   argument is a C++ or framework type.  A "stream" is a cudaStream_t passed
+ *   as void* (NULL = the legacy default stream).
+ * - The caller owns every buffer it passes in; the library never frees one.
+ *   A plan owns its DRM factors and workspace; a state owns its sketch
+ *   accumulators.  Both are freed by their destroy call.
+ * - Dense tensors are row-major over their modes (last mode fastest).
+ * - Errors are returned as ttnn_status; nothing is thrown across the ABI.  A
+ *   call that fails validation leaves plan and state unchanged.  After
+ *   TTNN_ECUDA the state content is unspecified.  ttnn_last_error() returns a
+ *   one-line message for the calling thread's last failure.
+ * - Calls on one plan (and the states made from it) are serialised by the
+ *   caller: they share the plan's device workspace.  Different plans may run
+ *   concurrently on different streams.
+ * - Work is enqueued on the given stream; a call returns once its work is
+ *   enqueued unless stated otherwise.
+ *
+ * Layout of the tree and of the results (paper notation in brackets)
+ * ------------------------------------------------------------------
+ * - Index tree [Sec. 3, Def. "index tree"]: node v has parent parent[v]
+ *   (-1 = root); leaves list their modes (0-based) in the CSR arrays
+ *   leaf_mode_ptr / leaf_modes.  Every node's modes (the union over its
+ *   leaves) must form one contiguous range and children partition their
+ *   parent; children are ordered by first mode.  Internal nodes need >= 2
+ *   children.
+ * - identity[v] != 0 (or r_v >= n_v on a leaf) makes v a dummy-like node
+ *   [Sec. 4: X = Y = P = I on dummy nodes]: its core is the identity.
+ * - Ranks r_v and oversampling p_v are per node (root entries ignored); r_v
+ *   is clipped to min(n_v, n_{D\v}) and p_v to n_v - r_v.  s_v = r_v + p_v.
+ * - Sketches [Sec. 4, sketch phase]: Omega_v is s_v x r_v; Psi of an
+ *   internal node is (s'_c1, ..., s'_cm, r_v) with s'_c = s_c (n_c for an
+ *   identity child); Psi of a leaf is (n_v, r_v); Psi_root is
+ *   (s'_c1, ..., s'_cm).  All row-major.
+ * - Cores [Def. "Tree tensor network format"]: root (r_c1..r_cm); transfer
+ *   (r_v, r_c1..r_cm); leaf (r_v, n_mu1..n_muk); identity leaf (n_v, n_v).
+ *   Binary64, row-major, at the per-node offsets of ttnn_node_info.
+ *
+ * DRMs [Sec. 7, Khatri-Rao sketchings]: per-mode Gaussian factors X_mu
+ * (n_mu x r_max), Y_mu (n_mu x s_max) drawn by Philox4x32-10 + Box-Muller
+ * (bit-identical on host and device, see ttnn_philox_gaussian), rounded to the
+ * plan's sketch number format; X_v / Y_v are their Khatri-Rao products over
+ * the complement / own modes, first r_v / s_v columns.  The Khatri-Rao blocks
+ * that multiply the dense tensor on the first-level pass are stored in the
+ * sketch format and are therefore rounded once more (exact for binary64).
+ */
+#ifndef TTNN_H
+#define TTNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TTNN_OK = 0,
+  TTNN_EINVAL = 1,       /* invalid argument, tree, size or pointer */
+  TTNN_ENOMEM = 2,       /* device or host allocation failed */
+  TTNN_ECUDA = 3,        /* a CUDA call or kernel launch failed */
+  TTNN_ENUMERIC = 4,     /* non-finite values met (e.g. NaN in an update) */
+  TTNN_ETIMEOUT = 5,     /* a bounded device wait ran out */
+  TTNN_EBUSY = 6,        /* resource in use (serving: no free slot) */
+  TTNN_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} ttnn_status;
+
+/* Number formats of the tensor and of the pass-side DRM blocks. */
+typedef enum {
+  TTNN_F64 = 0,   /* binary64 everywhere (accumulators binary64) */
+  TTNN_F32 = 1,   /* binary32 tensor, FP32 FMA pass, FP32 accumulators */
+  TTNN_BF16 = 2,  /* bfloat16 tensor + DRM blocks on tensor cores, FP32 accumulation */
+  TTNN_E4M3 = 3,  /* FP8 E4M3 tensor with one FP32 scale per 128x128 tile, FP32 accumulation */
+  TTNN_BF16X2 = 4 /* FP32 tensor split hi+lo into two bf16 MMAs, FP32 accumulation */
+} ttnn_dtype;
+
+typedef enum { TTNN_VARIANT_TTNN = 0, TTNN_VARIANT_STTNN = 1 } ttnn_variant;
+
+typedef struct {
+  int32_t n_nodes;
+  const int32_t* parent;        /* host [n_nodes]; -1 marks the root */
+  const int32_t* leaf_mode_ptr; /* host [n_nodes + 1]; CSR offsets into leaf_modes */
+  const int32_t* leaf_modes;    /* host; 0-based modes of each leaf */
+  const uint8_t* identity;      /* host [n_nodes] or NULL; nonzero forces P = I on a leaf */
+} ttnn_tree;
+
+typedef struct {
+  int32_t variant;       /* ttnn_variant */
+  int32_t sketch_dtype;  /* ttnn_dtype */
+  double eps_factor;     /* eps = eps_factor * unit_roundoff * ||R_v||_2; paper: 10 */
+  double unit_roundoff;  /* paper's "machine precision" u; default 2^-52 */
+  uint32_t flags;        /* TTNN_FLAG_* */
+} ttnn_opts;
+
+#define TTNN_FLAG_NO_SIDE_CACHE 1u  /* do not cache full-size pass DRM blocks */
+#define TTNN_FLAG_SIMT_PASS 2u      /* use the SIMT pass even for BF16 (testing) */
+
+typedef struct ttnn_plan_s* ttnn_plan_t;
+typedef struct ttnn_state_s* ttnn_state_t;
+
+typedef struct {
+  int32_t user_index;   /* index in the caller's parent[] */
+  int32_t lex_index;    /* position in the (level, position) order */
+  int32_t level, parent, n_children, mode_lo, mode_hi;
+  int32_t is_leaf, identity, r, p, s;
+  int64_t n;            /* n_v = prod of the node's mode sizes */
+  int64_t omega_offset, omega_elems;  /* in the state buffer (elements) */
+  int64_t psi_offset, psi_elems;
+  int32_t psi_ndim;
+  int64_t psi_shape[10];
+  int64_t core_offset, core_elems;    /* in the caller's core buffer (binary64 elements) */
+  int32_t core_ndim;
+  int64_t core_shape[10];
+  int32_t kept_rank;    /* after ttnn_recover: rank kept by the eps-pseudo-inverse (-1 before) */
+} ttnn_node_info;
+
+/* ---------------------------------------------------------------------- */
+/* Status text.  Never NULL.                                               */
+const char* ttnn_status_string(ttnn_status s);
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to n bytes) into buf (host).  Returns TTNN_OK. */
+ttnn_status ttnn_last_error(char* buf, size_t n);
+
+/* ttnn_philox_gaussian -- the DRM generator [Sec. 7 per-mode factors; the
+ * paper draws N(0,1) entries].  Writes rows x cols binary64 N(0,1) values to
+ * dst (device, row-major): element (i, j) is Box-Muller output (j & 1) of
+ * Philox4x32-10 with counter (i, j >> 1, (kind << 24) | ident, 0) and key
+ * (seed mod 2^32, seed >> 32); kind 1 = X_mu, 2 = Y_mu, 3 = STTNN XT_s.  If
+ * round_dtype is TTNN_F32/BF16/E4M3 the values are rounded (nearest-even)
+ * into that format's value set and still stored as binary64.
+ * EINVAL: rows/cols < 0, kind outside 1..5, ident >= 2^24, dst NULL. */
+ttnn_status ttnn_philox_gaussian(uint64_t seed, int32_t kind, int32_t ident, int64_t rows,
+                                 int64_t cols, int32_t round_dtype, double* dst, void* stream);
+
+/* ttnn_plan_create -- A1/A2 of the method [Sec. 4 Algorithm 2, first loop;
+ * Sec. 5 ordering]: validates and normalises the tree, fixes the
+ * lexicographic order, the STTNN reuse sets and the first-level split,
+ * draws the DRM factors on the device and sizes the workspace.
+ * tree, dims (host [d]), ranks and oversample (host [n_nodes]) are read during
+ * the call only.  opts may be NULL (TTNN, F32, eps_factor 10, u = 2^-52).
+ * EINVAL: invalid tree/sizes (see conventions); EUNSUPPORTED: STTNN whose
+ * first root child is an identity leaf; ENOMEM/ECUDA. */
+ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* dims,
+                             const int32_t* ranks, const int32_t* oversample, uint64_t seed,
+                             const ttnn_opts* opts, void* stream, ttnn_plan_t* out);
+void ttnn_plan_destroy(ttnn_plan_t plan);
+
+/* Sizes: state elements (binary64 for TTNN_F64 plans, binary32 otherwise),
+ * bytes per state element, total binary64 elements of all cores, number of
+ * tree nodes.  Any output pointer may be NULL. */
+ttnn_status ttnn_plan_sizes(ttnn_plan_t plan, int64_t* state_elems, int32_t* state_elem_bytes,
+                            int64_t* core_elems, int32_t* n_nodes);
+/* Per-node layout, by the caller's node index. */
+ttnn_status ttnn_plan_node(ttnn_plan_t plan, int32_t user_index, ttnn_node_info* out);
+/* Copies one per-mode DRM factor as stored by the plan (binary64, device dst,
+ * row-major n_mu x cols): which = 1 for X_mu (cols = r_max), 2 for Y_mu
+ * (cols = s_max), 3 for XT of the node with lexicographic index `mode`. */
+ttnn_status ttnn_plan_factor(ttnn_plan_t plan, int32_t which, int32_t mode, double* dst,
+                             int64_t* rows, int64_t* cols, void* stream);
+
+/* States: zeroed device accumulators for all Omega_v, Psi_v, Psi_root. */
+ttnn_status ttnn_state_create(ttnn_plan_t plan, void* stream, ttnn_state_t* out);
+void ttnn_state_destroy(ttnn_state_t state);
+ttnn_status ttnn_state_zero(ttnn_state_t state, void* stream);
+/* Raw accumulator buffer (device) and its element count. */
+ttnn_status ttnn_state_buffer(ttnn_state_t state, void** device_ptr, int64_t* elems);
+/* dst += alpha * src (same plan): sums partial sketches of disjoint parts of
+ * a tensor, e.g. from several GPUs or processes (Sec. 4: the sketch phase is
+ * linear in T). */
+ttnn_status ttnn_state_axpy(ttnn_state_t dst, ttnn_state_t src, double alpha, void* stream);
+/* Checkpoint: copies the accumulators to / from host memory (bytes must be
+ * state_elems * state_elem_bytes); synchronous on the stream. */
+ttnn_status ttnn_state_save(ttnn_state_t state, void* host_buf, size_t bytes, void* stream);
+ttnn_status ttnn_state_load(ttnn_state_t state, const void* host_buf, size_t bytes, void* stream);
+
+/* ttnn_update_dense -- A3-A6 [Sec. 4 sketch phase + "streaming by
+ * linearity"]: adds lambda * sketch(H) to the state, where H is zero outside
+ * the box offset[mu] <= i_mu < offset[mu] + extent[mu] and equals `data` on
+ * it.  data: device, row-major over the extents, in the plan's format
+ * (TTNN_BF16X2 plans take binary32; TTNN_E4M3 plans take the E4M3 bytes with
+ * `tile_scale` (device, one binary32 per 128x128 tile of the pass matrix, see
+ * ttnn_fp8_quantize) ).  offset/extent: host [d], NULL = whole tensor.
+ * EINVAL: box outside the tensor, empty box, NULL data. */
+ttnn_status ttnn_update_dense(ttnn_state_t state, const void* data, const int64_t* offset,
+                              const int64_t* extent, const float* tile_scale, double lambda,
+                              void* stream);
+
+/* ttnn_update_cp -- A5: adds lambda * sum_q w_q a_1q o ... o a_dq (a CP term)
+ * to the sketches without forming it.  weights: host [cp_rank];
+ * factors: host array of d device pointers, factor mu is n_mu x cp_rank
+ * row-major binary64. */
+ttnn_status ttnn_update_cp(ttnn_state_t state, int32_t cp_rank, const double* weights,
+                           const double* const* factors, double lambda, void* stream);
+
+/* ttnn_update_ttn -- A8 [Sec. 7 structured sketchings, TTN rounding]: adds
+ * lambda * sketch(T_in) for a tensor given in TTN format on the same tree.
+ * cores_in: host array (n_nodes) of device pointers to binary64 cores in the
+ * core layout above with input ranks ranks_in (host [n_nodes], root ignored);
+ * identity leaves of the plan still take an (R_v, n_v) input core. */
+ttnn_status ttnn_update_ttn(ttnn_state_t state, const double* const* cores_in,
+                            const int32_t* ranks_in, double lambda, void* stream);
+
+/* ttnn_recover -- A9 [Sec. 4 recovery phase, Algorithm 2, stabilised least
+ * squares with eps = eps_factor * u * ||R_v||_2]: QR of every Omega_v
+ * (diag R >= 0), eps-pseudo-inverse of R_v by one-sided Jacobi SVD, then
+ * B_v = (kron_c Q_c)^T Psi_v R_v,eps^+ (children's Q), leaf B_v = Psi_v
+ * R_v,eps^+, root B = (kron_c Q_c)^T Psi_root; all in binary64.
+ * cores: device, core_elems binary64 values at the per-node offsets.
+ * Synchronises the stream before returning (kept ranks are read back). */
+ttnn_status ttnn_recover(ttnn_state_t state, double* cores, void* stream);
+
+/* sttnn_run -- STTNN end to end on a whole dense tensor [Sec. 5]: a plan made
+ * with variant TTNN_VARIANT_STTNN, one pass over `dense` (plan format), then
+ * recovery into `cores`.  EINVAL if the plan is not an STTNN plan. */
+ttnn_status sttnn_run(ttnn_plan_t plan, const void* dense, const float* tile_scale,
+                      double* cores, void* stream);
+
+/* ttnn_round -- TTN rounding end to end [Sec. 7]: sketches of a TTN-format
+ * input (see ttnn_update_ttn) followed by recovery into `cores`. */
+ttnn_status ttnn_round(ttnn_plan_t plan, const double* const* cores_in, const int32_t* ranks_in,
+                       double* cores, void* stream);
+
+/* ttnn_fp8_quantize -- helper for TTNN_E4M3 plans: quantises a binary32
+ * dense tensor (device, whole tensor or box extents) to E4M3 bytes (device
+ * dst) with one binary32 scale = max|tile| / 448 per 128 x 128 tile of the
+ * pass matrix (rows = first-level left modes, columns = the rest); scales
+ * (device) has ceil(rows/128) * ceil(cols/128) entries. */
+ttnn_status ttnn_fp8_quantize(ttnn_plan_t plan, const float* src, const int64_t* extent,
+                              uint8_t* dst, float* scales, void* stream);
+
+/* Profiling (no counterpart in the paper; this build's instrumentation):
+ * with enable != 0 every later update / recovery on this plan records CUDA
+ * events around its phases on the stream it runs on.  ttnn_profile_read
+ * synchronises those events and returns the summed milliseconds and the
+ * number of recorded intervals of one phase since the last read, then clears
+ * them.  phase 0 = first-level pass kernel(s), 1 = tree walk and
+ * accumulation, 2 = recovery.  At most 4096 intervals are kept per phase. */
+ttnn_status ttnn_profile(ttnn_plan_t plan, int32_t enable);
+ttnn_status ttnn_profile_read(ttnn_plan_t plan, int32_t phase, double* total_ms, int32_t* count);
+/* Number of device kernels this library has launched in this process. */
+ttnn_status ttnn_kernel_launches(int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTNN_H */

@@ -20,7 +20,7 @@ import numpy as np
 FORMATS = {
     "f64": None,
     "f32": (24, -126, float(np.finfo(np.float32).max), "inf"),
-    "bf16": (8, -126, float.fromhex("0x1.fcp127"), "inf"),
+    "bf16": (8, -126, float.fromhex("0x1.fep127"), "inf"),
     "e4m3": (4, -6, 448.0, "sat"),
 }
 

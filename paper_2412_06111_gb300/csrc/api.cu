@@ -1,0 +1,425 @@
+// C ABI entry points (declared in include/ttnn.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "plan.cuh"
+
+namespace ttnn {
+
+long long launches_so_far();
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+const char* last_error() { return g_err; }
+
+static ttnn_status dev_alloc(void** p, int64_t bytes) {
+  *p = nullptr;
+  if (bytes <= 0) return TTNN_OK;
+  cudaError_t e = cudaMalloc(p, (size_t)bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%lld) failed: %s", (long long)bytes, cudaGetErrorString(e));
+    *p = nullptr;
+    return TTNN_ENOMEM;
+  }
+  return TTNN_OK;
+}
+
+static void free_plan(ttnn_plan_s* P) {
+  if (!P) return;
+  for (auto& v : P->prof)
+    for (auto& pr : v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  cudaFree(P->fac64);
+  if (P->facw != (void*)P->fac64) cudaFree(P->facw);
+  cudaFree(P->sideR);
+  cudaFree(P->sideL);
+  cudaFree(P->yW);
+  cudaFree(P->ws);
+  cudaFree(P->jobs_dev);
+  cudaFree(P->kept_dev);
+  delete P;
+}
+
+static int store_bytes(int store) { return store == 0 ? 8 : store == 1 ? 4 : store == 2 ? 2 : 1; }
+
+static Box full_box(const ttnn_plan_s& P) {
+  Box b;
+  b.off.assign(P.d, 0);
+  b.ext = P.dims;
+  b.full = true;
+  return b;
+}
+
+}  // namespace ttnn
+
+using namespace ttnn;
+
+extern "C" {
+
+const char* ttnn_status_string(ttnn_status s) {
+  switch (s) {
+    case TTNN_OK: return "ok";
+    case TTNN_EINVAL: return "invalid argument";
+    case TTNN_ENOMEM: return "out of memory";
+    case TTNN_ECUDA: return "CUDA error";
+    case TTNN_ENUMERIC: return "non-finite values";
+    case TTNN_ETIMEOUT: return "device wait timed out";
+    case TTNN_EBUSY: return "busy";
+    case TTNN_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+ttnn_status ttnn_last_error(char* buf, size_t n) {
+  if (buf && n) {
+    strncpy(buf, last_error(), n - 1);
+    buf[n - 1] = 0;
+  }
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_philox_gaussian(uint64_t seed, int32_t kind, int32_t ident, int64_t rows,
+                                 int64_t cols, int32_t round_dtype, double* dst, void* stream) {
+  TTNN_CHECK_ARG(rows >= 0 && cols >= 0, "negative size");
+  TTNN_CHECK_ARG(kind >= 1 && kind <= 5, "kind must be in 1..5");
+  TTNN_CHECK_ARG(ident >= 0 && ident < (1 << 24), "ident must be in [0, 2^24)");
+  TTNN_CHECK_ARG(round_dtype >= 0 && round_dtype <= 3, "round_dtype must be F64/F32/BF16/E4M3");
+  TTNN_CHECK_ARG(dst || rows * cols == 0, "null dst");
+  return launch_philox(seed, kind, ident, rows, cols, round_dtype, dst, (cudaStream_t)stream);
+}
+
+ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* dims,
+                             const int32_t* ranks, const int32_t* oversample, uint64_t seed,
+                             const ttnn_opts* opts, void* stream, ttnn_plan_t* out) {
+  TTNN_CHECK_ARG(out, "null output");
+  *out = nullptr;
+  std::unique_ptr<ttnn_plan_s> hold(new (std::nothrow) ttnn_plan_s());
+  if (!hold) {
+    set_error("host allocation failed");
+    return TTNN_ENOMEM;
+  }
+  ttnn_plan_s& P = *hold;
+  ttnn_opts def{TTNN_VARIANT_TTNN, TTNN_F32, 10.0, 2.220446049250313e-16, 0};
+  TTNN_TRY(build_plan(P, tree, d, dims, ranks, oversample, seed, opts ? opts : &def));
+  cudaStream_t st = (cudaStream_t)stream;
+  ttnn_status s = TTNN_OK;
+  auto fail = [&](ttnn_status e) {
+    ttnn_plan_s* raw = hold.release();
+    free_plan(raw);
+    return e;
+  };
+  // DRM factors (binary64 master, walk-type copy)
+  if ((s = dev_alloc((void**)&P.fac64, P.fac_elems * 8)) != TTNN_OK) return fail(s);
+  for (int m = 0; m < P.d; ++m) {
+    if ((s = launch_philox(seed, 1, m, P.dims[m], P.rmax, P.round_fmt, P.fac64 + P.x_off[m], st))) return fail(s);
+    if ((s = launch_philox(seed, 2, m, P.dims[m], P.smax, P.round_fmt, P.fac64 + P.y_off[m], st))) return fail(s);
+  }
+  for (int v : P.lex) {
+    const TNode& nd = P.nodes[v];
+    if (!nd.sketched()) continue;
+    if ((s = launch_philox(seed, 3, nd.lex, nd.s, P.rmax, P.round_fmt, P.fac64 + nd.xt_off, st))) return fail(s);
+  }
+  if (P.walk_f64) {
+    P.facw = P.fac64;
+  } else {
+    if ((s = dev_alloc(&P.facw, P.fac_elems * 4)) != TTNN_OK) return fail(s);
+    if ((s = launch_convert_f64_to_f32(P.fac64, (float*)P.facw, P.fac_elems, st))) return fail(s);
+  }
+  // cached full-size pass blocks
+  Box fb = full_box(P);
+  int64_t nL = 1, nR = 1;
+  for (int m = P.Llo; m < P.Lhi; ++m) nL *= P.dims[m];
+  for (int m = P.Rlo; m < P.Rhi; ++m) nR *= P.dims[m];
+  const int sb = store_bytes(P.pass_store);
+  if (!(P.flags & TTNN_FLAG_NO_SIDE_CACHE)) {
+    if (P.wR > 0) {
+      if ((s = dev_alloc(&P.sideR, (int64_t)P.wRpad * nR * sb)) != TTNN_OK) return fail(s);
+      if ((s = make_side(P, fb, 0, P.sideR, nR, st))) return fail(s);
+    }
+    if (P.wL > 0) {
+      if ((s = dev_alloc(&P.sideL, (int64_t)P.wLpad * nL * sb)) != TTNN_OK) return fail(s);
+      if ((s = make_side(P, fb, 1, P.sideL, nL, st))) return fail(s);
+    }
+    const TNode& yc = P.nodes[P.ychild];
+    if (!yc.identity) {
+      if ((s = dev_alloc(&P.yW, (int64_t)yc.s * yc.n * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
+      if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
+    }
+  }
+  // workspace: the larger of a whole-tensor update and a recovery
+  int64_t need_u = 0, need_r = 0;
+  if ((s = run_dense_update(P, nullptr, nullptr, fb, nullptr, 1.0, st, true, &need_u))) return fail(s);
+  if ((s = run_recover(P, nullptr, nullptr, st, true, &need_r))) return fail(s);
+  P.ws_bytes = std::max(need_u, need_r) + 4096;
+  if ((s = dev_alloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
+  if ((s = dev_alloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
+  if ((s = dev_alloc((void**)&P.kept_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error("plan creation: %s", cudaGetErrorString(e));
+    return fail(TTNN_ECUDA);
+  }
+  *out = hold.release();
+  return TTNN_OK;
+}
+
+void ttnn_plan_destroy(ttnn_plan_t plan) { free_plan(plan); }
+
+ttnn_status ttnn_plan_sizes(ttnn_plan_t P, int64_t* state_elems, int32_t* state_elem_bytes,
+                            int64_t* core_elems, int32_t* n_nodes) {
+  TTNN_CHECK_ARG(P, "null plan");
+  if (state_elems) *state_elems = P->state_elems;
+  if (state_elem_bytes) *state_elem_bytes = P->walk_f64 ? 8 : 4;
+  if (core_elems) *core_elems = P->core_elems;
+  if (n_nodes) *n_nodes = (int32_t)P->nodes.size();
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_plan_node(ttnn_plan_t P, int32_t v, ttnn_node_info* o) {
+  TTNN_CHECK_ARG(P && o, "null argument");
+  TTNN_CHECK_ARG(v >= 0 && v < (int)P->nodes.size(), "node index out of range");
+  const TNode& nd = P->nodes[v];
+  memset(o, 0, sizeof(*o));
+  o->user_index = v;
+  o->lex_index = nd.lex;
+  o->level = nd.level;
+  o->parent = nd.parent;
+  o->n_children = (int32_t)nd.ch.size();
+  o->mode_lo = nd.lo;
+  o->mode_hi = nd.hi;
+  o->is_leaf = nd.leaf;
+  o->identity = nd.identity;
+  o->r = nd.r;
+  o->p = nd.p;
+  o->s = nd.s;
+  o->n = nd.n;
+  o->omega_offset = nd.om_off;
+  o->omega_elems = nd.om_el;
+  o->psi_offset = nd.ps_off;
+  o->psi_elems = nd.ps_el;
+  o->psi_ndim = (int32_t)std::min<size_t>(nd.ps_shape.size(), 10);
+  for (int k = 0; k < o->psi_ndim; ++k) o->psi_shape[k] = nd.ps_shape[k];
+  o->core_offset = nd.core_off;
+  o->core_elems = nd.core_el;
+  o->core_ndim = (int32_t)std::min<size_t>(nd.core_shape.size(), 10);
+  for (int k = 0; k < o->core_ndim; ++k) o->core_shape[k] = nd.core_shape[k];
+  o->kept_rank = nd.kept;
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_plan_factor(ttnn_plan_t P, int32_t which, int32_t mode, double* dst, int64_t* rows,
+                             int64_t* cols, void* stream) {
+  TTNN_CHECK_ARG(P, "null plan");
+  int64_t r = 0, c = 0, off = 0;
+  if (which == 1 || which == 2) {
+    TTNN_CHECK_ARG(mode >= 0 && mode < P->d, "mode out of range");
+    r = P->dims[mode];
+    c = which == 1 ? P->rmax : P->smax;
+    off = which == 1 ? P->x_off[mode] : P->y_off[mode];
+  } else if (which == 3) {
+    TTNN_CHECK_ARG(mode >= 0 && mode < (int)P->lex.size(), "lex index out of range");
+    const TNode& nd = P->nodes[P->lex[mode]];
+    TTNN_CHECK_ARG(nd.sketched(), "node has no XT factor");
+    r = nd.s;
+    c = P->rmax;
+    off = nd.xt_off;
+  } else {
+    set_error("which must be 1, 2 or 3");
+    return TTNN_EINVAL;
+  }
+  if (rows) *rows = r;
+  if (cols) *cols = c;
+  if (dst)
+    TTNN_TRY_CUDA(cudaMemcpyAsync(dst, P->fac64 + off, r * c * 8, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream));
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_state_create(ttnn_plan_t P, void* stream, ttnn_state_t* out) {
+  TTNN_CHECK_ARG(P && out, "null argument");
+  *out = nullptr;
+  ttnn_state_s* S = new (std::nothrow) ttnn_state_s();
+  if (!S) {
+    set_error("host allocation failed");
+    return TTNN_ENOMEM;
+  }
+  S->plan = P;
+  S->elems = P->state_elems;
+  ttnn_status s = dev_alloc(&S->acc, S->elems * (P->walk_f64 ? 8 : 4));
+  if (s != TTNN_OK) {
+    delete S;
+    return s;
+  }
+  s = launch_fill_zero(S->acc, S->elems * (P->walk_f64 ? 8 : 4), (cudaStream_t)stream);
+  if (s != TTNN_OK) {
+    cudaFree(S->acc);
+    delete S;
+    return s;
+  }
+  *out = S;
+  return TTNN_OK;
+}
+
+void ttnn_state_destroy(ttnn_state_t S) {
+  if (!S) return;
+  cudaFree(S->acc);
+  delete S;
+}
+
+ttnn_status ttnn_state_zero(ttnn_state_t S, void* stream) {
+  TTNN_CHECK_ARG(S, "null state");
+  return launch_fill_zero(S->acc, S->elems * (S->plan->walk_f64 ? 8 : 4), (cudaStream_t)stream);
+}
+
+ttnn_status ttnn_state_buffer(ttnn_state_t S, void** p, int64_t* elems) {
+  TTNN_CHECK_ARG(S, "null state");
+  if (p) *p = S->acc;
+  if (elems) *elems = S->elems;
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_state_axpy(ttnn_state_t dst, ttnn_state_t src, double alpha, void* stream) {
+  TTNN_CHECK_ARG(dst && src, "null state");
+  TTNN_CHECK_ARG(dst->plan == src->plan || dst->elems == src->elems, "states of different plans");
+  return launch_axpy(dst->acc, src->acc, alpha, dst->elems, dst->plan->walk_f64, (cudaStream_t)stream);
+}
+
+ttnn_status ttnn_state_save(ttnn_state_t S, void* host, size_t bytes, void* stream) {
+  TTNN_CHECK_ARG(S && host, "null argument");
+  const size_t need = (size_t)S->elems * (S->plan->walk_f64 ? 8 : 4);
+  TTNN_CHECK_ARG(bytes == need, "buffer must be %zu bytes", need);
+  TTNN_TRY_CUDA(cudaMemcpyAsync(host, S->acc, need, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  TTNN_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_state_load(ttnn_state_t S, const void* host, size_t bytes, void* stream) {
+  TTNN_CHECK_ARG(S && host, "null argument");
+  const size_t need = (size_t)S->elems * (S->plan->walk_f64 ? 8 : 4);
+  TTNN_CHECK_ARG(bytes == need, "buffer must be %zu bytes", need);
+  TTNN_TRY_CUDA(cudaMemcpyAsync(S->acc, host, need, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  TTNN_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_update_dense(ttnn_state_t S, const void* data, const int64_t* offset,
+                              const int64_t* extent, const float* tile_scale, double lambda,
+                              void* stream) {
+  TTNN_CHECK_ARG(S && data, "null argument");
+  ttnn_plan_s& P = *S->plan;
+  Box b;
+  b.off.assign(P.d, 0);
+  b.ext = P.dims;
+  b.full = true;
+  for (int m = 0; m < P.d; ++m) {
+    if (offset) b.off[m] = offset[m];
+    if (extent) b.ext[m] = extent[m];
+    TTNN_CHECK_ARG(b.ext[m] >= 1 && b.off[m] >= 0 && b.off[m] + b.ext[m] <= P.dims[m],
+                   "box outside the tensor on mode %d", m);
+    if (b.off[m] != 0 || b.ext[m] != P.dims[m]) b.full = false;
+  }
+  TTNN_CHECK_ARG(P.pass_store != 3 || tile_scale, "E4M3 updates need tile scales");
+  return run_dense_update(P, S->acc, data, b, tile_scale, lambda, (cudaStream_t)stream, false,
+                          nullptr);
+}
+
+ttnn_status ttnn_update_cp(ttnn_state_t S, int32_t cp_rank, const double* weights,
+                           const double* const* factors, double lambda, void* stream) {
+  (void)S; (void)cp_rank; (void)weights; (void)factors; (void)lambda; (void)stream;
+  set_error("CP updates are not implemented yet");
+  return TTNN_EUNSUPPORTED;
+}
+
+ttnn_status ttnn_update_ttn(ttnn_state_t S, const double* const* cores_in, const int32_t* ranks_in,
+                            double lambda, void* stream) {
+  (void)S; (void)cores_in; (void)ranks_in; (void)lambda; (void)stream;
+  set_error("TTN-format updates are not implemented yet");
+  return TTNN_EUNSUPPORTED;
+}
+
+ttnn_status ttnn_recover(ttnn_state_t S, double* cores, void* stream) {
+  TTNN_CHECK_ARG(S && cores, "null argument");
+  return run_recover(*S->plan, S->acc, cores, (cudaStream_t)stream, false, nullptr);
+}
+
+ttnn_status sttnn_run(ttnn_plan_t P, const void* dense, const float* tile_scale, double* cores,
+                      void* stream) {
+  TTNN_CHECK_ARG(P && dense && cores, "null argument");
+  TTNN_CHECK_ARG(P->variant == TTNN_VARIANT_STTNN, "sttnn_run needs an STTNN plan");
+  ttnn_state_t S = nullptr;
+  TTNN_TRY(ttnn_state_create(P, stream, &S));
+  ttnn_status s = ttnn_update_dense(S, dense, nullptr, nullptr, tile_scale, 1.0, stream);
+  if (s == TTNN_OK) s = ttnn_recover(S, cores, stream);
+  ttnn_state_destroy(S);
+  return s;
+}
+
+ttnn_status ttnn_round(ttnn_plan_t P, const double* const* cores_in, const int32_t* ranks_in,
+                       double* cores, void* stream) {
+  TTNN_CHECK_ARG(P && cores_in && ranks_in && cores, "null argument");
+  ttnn_state_t S = nullptr;
+  TTNN_TRY(ttnn_state_create(P, stream, &S));
+  ttnn_status s = ttnn_update_ttn(S, cores_in, ranks_in, 1.0, stream);
+  if (s == TTNN_OK) s = ttnn_recover(S, cores, stream);
+  ttnn_state_destroy(S);
+  return s;
+}
+
+ttnn_status ttnn_fp8_quantize(ttnn_plan_t P, const float* src, const int64_t* extent, uint8_t* dst,
+                              float* scales, void* stream) {
+  (void)P; (void)src; (void)extent; (void)dst; (void)scales; (void)stream;
+  set_error("FP8 quantisation is not implemented yet");
+  return TTNN_EUNSUPPORTED;
+}
+
+ttnn_status ttnn_profile(ttnn_plan_t P, int32_t enable) {
+  TTNN_CHECK_ARG(P, "null plan");
+  P->profile = enable != 0;
+  return TTNN_OK;
+}
+
+ttnn_status ttnn_profile_read(ttnn_plan_t P, int32_t phase, double* total_ms, int32_t* count) {
+  TTNN_CHECK_ARG(P && phase >= 0 && phase < 3, "bad argument");
+  double tot = 0.0;
+  int cnt = 0;
+  ttnn_status s = TTNN_OK;
+  for (auto& pr : P->prof[phase]) {
+    float ms = 0.f;
+    if (s == TTNN_OK) {
+      cudaError_t e = cudaEventSynchronize(pr.second);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+      if (e != cudaSuccess) {
+        set_error("profile read: %s", cudaGetErrorString(e));
+        s = TTNN_ECUDA;
+      }
+    }
+    tot += ms;
+    ++cnt;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  P->prof[phase].clear();
+  if (total_ms) *total_ms = tot;
+  if (count) *count = cnt;
+  return s;
+}
+
+ttnn_status ttnn_kernel_launches(int64_t* count) {
+  TTNN_CHECK_ARG(count, "null argument");
+  *count = launches_so_far();
+  return TTNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,496 @@
+// Generic device kernels: DRM generation, pass-side Khatri-Rao blocks, the
+// strided contraction used by the tree walk and the core assembly, the SIMT
+// GEMM of the binary64 / binary32 first-level pass, and small helpers.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "kernels.cuh"
+#include "philox.cuh"
+
+namespace ttnn {
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(); }
+
+ttnn_status check_launch(const char* what) {
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
+    return TTNN_ECUDA;
+  }
+  return TTNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DRM generation
+// ---------------------------------------------------------------------------
+__global__ void philox_kernel(uint64_t seed, uint32_t kind, uint32_t ident, int64_t rows,
+                              int64_t cols, int fmt, double* dst) {
+  const int64_t n = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    dst[e] = round_fmt(philox_gaussian(seed, kind, ident, (uint64_t)i, (uint64_t)j), fmt);
+  }
+}
+
+ttnn_status launch_philox(uint64_t seed, int kind, int ident, int64_t rows, int64_t cols,
+                          int fmt, double* dst, cudaStream_t st) {
+  const int64_t n = rows * cols;
+  if (n == 0) return TTNN_OK;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, threads), 65535);
+  philox_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, (uint32_t)kind, (uint32_t)ident, rows,
+                                                      cols, fmt, dst);
+  return check_launch("philox_kernel");
+}
+
+__global__ void convert_kernel(const double* src, float* dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+
+ttnn_status launch_convert_f64_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), 65535);
+  convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
+  return check_launch("convert_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// pass-side Khatri-Rao blocks
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_fmt(void* out, int64_t idx, double v, int store) {
+  switch (store) {
+    case 0: ((double*)out)[idx] = v; break;
+    case 1: ((float*)out)[idx] = (float)v; break;
+    case 2: {
+      // v is already a bfloat16 value: its binary32 image has 16 zero low bits
+      const uint32_t b = __float_as_uint((float)v);
+      ((uint16_t*)out)[idx] = (uint16_t)(b >> 16);
+      break;
+    }
+    default: {
+      __nv_fp8_e4m3 q((float)v);  // exact: v is an E4M3 value
+      ((uint8_t*)out)[idx] = q.__x;
+      break;
+    }
+  }
+}
+
+__global__ void side_kernel(SideSpec s, void* out) {
+  int64_t rows = 1;
+  for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];
+  const int64_t n = rows * s.total_cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, row = e - c * rows;
+    double v = 0.0;
+    if (c < s.x_cols + s.y_cols) {
+      // decompose the row index (row-major over the side's modes)
+      int64_t idx[8];
+      int64_t rem = row;
+      for (int m = s.nmodes - 1; m >= 0; --m) {
+        idx[m] = rem % s.ext[m];
+        rem /= s.ext[m];
+      }
+      if (c < s.x_cols) {
+        v = s.xf[0][(s.off[0] + idx[0]) * s.rmax + c];
+        for (int m = 1; m < s.nmodes; ++m) v = __dmul_rn(v, s.xf[m][(s.off[m] + idx[m]) * s.rmax + c]);
+      } else if (s.y_kind == 0) {
+        const int64_t cc = c - s.x_cols;
+        v = s.yf[0][(s.off[0] + idx[0]) * s.smax + cc];
+        for (int m = 1; m < s.nmodes; ++m) v = __dmul_rn(v, s.yf[m][(s.off[m] + idx[m]) * s.smax + cc]);
+      } else {
+        int64_t flat = 0;
+        for (int m = 0; m < s.nmodes; ++m) flat = flat * s.full[m] + (s.off[m] + idx[m]);
+        v = (flat == c - s.x_cols) ? 1.0 : 0.0;
+      }
+      v = round_fmt(v, s.round_fmt);
+    }
+    store_fmt(out, c * s.ld + row, v, s.store);
+  }
+}
+
+ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st) {
+  int64_t rows = 1;
+  for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];
+  const int64_t n = rows * s.total_cols;
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), 65535);
+  side_kernel<<<(unsigned)blocks, 256, 0, st>>>(s, out);
+  return check_launch("side_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// strided contraction
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tw, typename Tout, typename Tacc>
+__global__ void contract_kernel(Contract c, int nsplit, int64_t chunk, Tout* partial) {
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  const Tin* in = (const Tin*)c.in;
+  const Tw* w = (const Tw*)c.w;
+  Tout* out = (Tout*)c.out;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total * nsplit;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t split = e / total, o = e - split * total;
+    int64_t t = o;
+    const int64_t j = t % c.J;
+    t /= c.J;
+    const int64_t q = t % c.Q;
+    t /= c.Q;
+    const int64_t b = t % c.NB;
+    const int64_t p = t / c.NB;
+    const int64_t i0 = split * chunk;
+    const int64_t i1 = min(c.NI, i0 + chunk);
+    const Tin* ip = in + p * c.isP + q * c.isQ + j * c.isJ;
+    Tacc acc = 0;
+    if (w) {
+      const Tw* wp = w + b * c.wsB + q * c.wsQ + j * c.wsJ;
+      for (int64_t i = i0; i < i1; ++i) acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
+    } else {
+      for (int64_t i = i0; i < i1; ++i) acc += (Tacc)ip[i * c.isI];
+    }
+    if (nsplit > 1) {
+      partial[split * total + o] = (Tout)acc;
+    } else {
+      const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+      const Tout v = (Tout)((Tacc)c.alpha * acc);
+      out[oi] = c.accumulate ? (Tout)(out[oi] + v) : v;
+    }
+  }
+}
+
+template <typename Tout>
+__global__ void contract_reduce_kernel(Contract c, int nsplit, const Tout* partial) {
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  Tout* out = (Tout*)c.out;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    Tout acc = 0;
+    for (int s = 0; s < nsplit; ++s) acc += partial[s * total + o];
+    int64_t t = o;
+    const int64_t j = t % c.J;
+    t /= c.J;
+    const int64_t q = t % c.Q;
+    t /= c.Q;
+    const int64_t b = t % c.NB;
+    const int64_t p = t / c.NB;
+    const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+    const Tout v = (Tout)(c.alpha * acc);
+    out[oi] = c.accumulate ? (Tout)(out[oi] + v) : v;
+  }
+}
+
+static void contract_split(const Contract& c, int* nsplit, int64_t* chunk) {
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  const int64_t target = (int64_t)num_sms() * 2048;
+  int ns = 1;
+  if (c.NI >= 256 && total < target) {
+    ns = (int)std::min<int64_t>(std::min<int64_t>(ceil_div(target, std::max<int64_t>(total, 1)),
+                                                  c.NI / 64),
+                                256);
+    ns = std::max(ns, 1);
+  }
+  *chunk = ceil_div(c.NI, ns);
+  *nsplit = (int)ceil_div(c.NI, *chunk);
+  if (*nsplit < 1) *nsplit = 1;
+}
+
+int64_t contract_partial_elems(const Contract& c) {
+  int ns;
+  int64_t chunk;
+  contract_split(c, &ns, &chunk);
+  return ns > 1 ? ns * c.P * c.NB * c.Q * c.J : 0;
+}
+
+template <typename Tin, typename Tw, typename Tout, typename Tacc>
+static ttnn_status run_contract(const Contract& c, void* partial, int64_t partial_elems,
+                                cudaStream_t st) {
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  if (total == 0) return TTNN_OK;
+  int ns;
+  int64_t chunk;
+  contract_split(c, &ns, &chunk);
+  if (ns > 1 && (partial == nullptr || partial_elems < ns * total)) {
+    ns = 1;
+    chunk = c.NI;
+  }
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>(ceil_div(total * ns, threads), (int64_t)num_sms() * 32);
+  contract_kernel<Tin, Tw, Tout, Tacc><<<(unsigned)blocks, threads, 0, st>>>(c, ns, chunk, (Tout*)partial);
+  TTNN_TRY(check_launch("contract_kernel"));
+  if (ns > 1) {
+    const int64_t b2 = std::min<int64_t>(ceil_div(total, threads), (int64_t)num_sms() * 32);
+    contract_reduce_kernel<Tout><<<(unsigned)b2, threads, 0, st>>>(c, ns, (const Tout*)partial);
+    TTNN_TRY(check_launch("contract_reduce_kernel"));
+  }
+  return TTNN_OK;
+}
+
+ttnn_status launch_contract(const Contract& c, ElemType tin, ElemType tw, ElemType tout,
+                            void* partial, int64_t partial_elems, cudaStream_t st) {
+  if (tin == ET_F32 && tw == ET_F32 && tout == ET_F32)
+    return run_contract<float, float, float, float>(c, partial, partial_elems, st);
+  if (tin == ET_F64 && tw == ET_F64 && tout == ET_F64)
+    return run_contract<double, double, double, double>(c, partial, partial_elems, st);
+  if (tin == ET_F32 && tw == ET_F64 && tout == ET_F64)
+    return run_contract<float, double, double, double>(c, partial, partial_elems, st);
+  set_error("unsupported contraction type combination");
+  return TTNN_EUNSUPPORTED;
+}
+
+// ---------------------------------------------------------------------------
+// SIMT GEMM (binary64 / binary32 pass, and the BF16 fallback)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float to_f32(T v) { return (float)v; }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename Tin, typename Tacc>
+__device__ __forceinline__ Tacc load_as(const Tin* p) { return (Tacc)to_f32(*p); }
+template <>
+__device__ __forceinline__ double load_as<double, double>(const double* p) { return *p; }
+
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+// 256 threads; each computes a 4 x 4 block of the 64 x 64 output tile.
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t kchunk, Tacc* partial) {
+  __shared__ Tacc As[GB_K][GB_M + 1];
+  __shared__ Tacc Bs[GB_K][GB_N + 1];
+  const Tin* A = (const Tin*)g.A;
+  const Tin* B = (const Tin*)g.B;
+  const int tid = threadIdx.x;
+  const int64_t i0 = blockIdx.x * (int64_t)GB_M;
+  const int64_t j0 = blockIdx.y * (int64_t)GB_N;
+  const int split = blockIdx.z;
+  const int64_t kb = split * kchunk;
+  const int64_t ke = min(g.K, kb + kchunk);
+  const int ty = tid / 16, tx = tid % 16;   // output rows ty*4.., cols tx*4..
+  Tacc acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  const bool a_k_contig = (g.ask == 1);
+  const bool b_k_contig = (g.bsk == 1);
+  for (int64_t k0 = kb; k0 < ke; k0 += GB_K) {
+    // 64 x 16 tiles: 1024 elements, 4 per thread
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = tid + l * 256;
+      int ii, kk;
+      if (a_k_contig) { ii = e / GB_K; kk = e % GB_K; }
+      else { kk = e / GB_M; ii = e % GB_M; }
+      const int64_t gi = i0 + ii, gk = k0 + kk;
+      As[kk][ii] = (gi < g.I && gk < ke) ? load_as<Tin, Tacc>(A + gi * g.asi + gk * g.ask) : (Tacc)0;
+      int jj, kk2;
+      if (b_k_contig) { jj = e / GB_K; kk2 = e % GB_K; }
+      else { kk2 = e / GB_N; jj = e % GB_N; }
+      const int64_t gj = j0 + jj, gk2 = k0 + kk2;
+      Bs[kk2][jj] = (gj < g.Jn && gk2 < ke) ? load_as<Tin, Tacc>(B + gj * g.bsj + gk2 * g.bsk) : (Tacc)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      Tacc a[4], b[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        a[x] = As[kk][ty * 4 + x];
+        b[x] = Bs[kk][tx * 4 + x];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+  Tacc* C = nsplit > 1 ? partial + (int64_t)split * g.I * g.ldc : (Tacc*)g.C;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int64_t gi = i0 + ty * 4 + x;
+    if (gi >= g.I) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int64_t gj = j0 + tx * 4 + y;
+      if (gj < g.Jn) C[gi * g.ldc + gj] = acc[x][y];
+    }
+  }
+}
+
+template <typename Tacc>
+__global__ void gemm_reduce_kernel(Gemm g, int nsplit, const Tacc* partial) {
+  const int64_t n = g.I * g.ldc;
+  Tacc* C = (Tacc*)g.C;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e % g.ldc >= g.Jn) continue;
+    Tacc acc = 0;
+    for (int s = 0; s < nsplit; ++s) acc += partial[(int64_t)s * n + e];
+    C[e] = acc;
+  }
+}
+
+int gemm_choose_split(const Gemm& g) {
+  const int64_t tiles = ceil_div(g.I, GB_M) * ceil_div(g.Jn, GB_N);
+  const int64_t want = (int64_t)num_sms() * 4;
+  if (tiles >= want) return 1;
+  int64_t ns = ceil_div(want, tiles);
+  ns = std::min<int64_t>(ns, ceil_div(g.K, 256));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ns, 512));
+}
+
+template <typename Tin, typename Tacc>
+static ttnn_status run_gemm(const Gemm& g, int nsplit, void* partial, cudaStream_t st) {
+  if (g.I == 0 || g.Jn == 0) return TTNN_OK;
+  int64_t kchunk = round_up(ceil_div(g.K, nsplit), GB_K);
+  nsplit = (int)ceil_div(g.K, kchunk);
+  if (nsplit < 1) nsplit = 1;
+  dim3 grid((unsigned)ceil_div(g.I, GB_M), (unsigned)ceil_div(g.Jn, GB_N), (unsigned)nsplit);
+  if (grid.y > 65535 || grid.z > 65535) {
+    set_error("gemm grid too large");
+    return TTNN_EUNSUPPORTED;
+  }
+  gemm_kernel<Tin, Tacc><<<grid, 256, 0, st>>>(g, nsplit, kchunk, (Tacc*)partial);
+  TTNN_TRY(check_launch("gemm_kernel"));
+  if (nsplit > 1) {
+    const int64_t n = g.I * g.ldc;
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 32);
+    gemm_reduce_kernel<Tacc><<<(unsigned)blocks, 256, 0, st>>>(g, nsplit, (const Tacc*)partial);
+    TTNN_TRY(check_launch("gemm_reduce_kernel"));
+  }
+  return TTNN_OK;
+}
+
+ttnn_status launch_gemm(const Gemm& g, int nsplit, void* partial, cudaStream_t st) {
+  switch (g.in_type) {
+    case 0: return run_gemm<double, double>(g, nsplit, partial, st);
+    case 1: return run_gemm<float, float>(g, nsplit, partial, st);
+    case 2: return run_gemm<__nv_bfloat16, float>(g, nsplit, partial, st);
+    default: set_error("gemm: bad input type"); return TTNN_EINVAL;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st) {
+  if (bytes == 0) return TTNN_OK;
+  TTNN_TRY_CUDA(cudaMemsetAsync(p, 0, (size_t)bytes, st));
+  return TTNN_OK;
+}
+
+template <typename T>
+__global__ void axpy_kernel(T* y, const T* x, double alpha, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (T)(y[e] + (T)alpha * x[e]);
+}
+
+ttnn_status launch_axpy(void* y, const void* x, double alpha, int64_t n, int is_f64, cudaStream_t st) {
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), 65535);
+  if (is_f64) axpy_kernel<double><<<(unsigned)blocks, 256, 0, st>>>((double*)y, (const double*)x, alpha, n);
+  else axpy_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((float*)y, (const float*)x, alpha, n);
+  return check_launch("axpy_kernel");
+}
+
+__global__ void eye_kernel(double* dst, int64_t n) {
+  const int64_t m = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+ttnn_status launch_eye(double* dst, int64_t n, cudaStream_t st) {
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n * n, 256), 65535);
+  eye_kernel<<<(unsigned)blocks, 256, 0, st>>>(dst, n);
+  return check_launch("eye_kernel");
+}
+
+template <typename T>
+__global__ void finite_kernel(const T* x, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = to_f32(x[e]);
+    if (!isfinite(v)) bad = true;
+  }
+  if (bad) atomicOr(flag, 1);
+}
+
+__global__ void finite_kernel_f64(const double* x, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[e])) bad = true;
+  if (bad) atomicOr(flag, 1);
+}
+
+ttnn_status launch_finite_check(const void* data, int64_t n, int type, int* flag, cudaStream_t st) {
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+  switch (type) {
+    case 0: finite_kernel_f64<<<(unsigned)blocks, 256, 0, st>>>((const double*)data, n, flag); break;
+    case 1: finite_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float*)data, n, flag); break;
+    case 2: finite_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>((const __nv_bfloat16*)data, n, flag); break;
+    default: return TTNN_OK;
+  }
+  return check_launch("finite_kernel");
+}
+
+}  // namespace ttnn
+
+namespace ttnn {
+
+template <typename T>
+__global__ void scatter_kernel(Scatter s) {
+  int64_t total = 1;
+  for (int a = 0; a < s.nd; ++a) total *= s.size[a];
+  const T* in = (const T*)s.in;
+  T* out = (T*)s.out;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e, io = 0, oo = 0;
+    for (int a = s.nd - 1; a >= 0; --a) {
+      const int64_t i = rem % s.size[a];
+      rem /= s.size[a];
+      io += i * s.is[a];
+      oo += (s.off[a] + i) * s.os[a];
+    }
+    out[oo] = (T)(out[oo] + (T)s.alpha * in[io]);
+  }
+}
+
+ttnn_status launch_scatter_add(const Scatter& s, int f64, cudaStream_t st) {
+  int64_t total = 1;
+  for (int a = 0; a < s.nd; ++a) total *= s.size[a];
+  if (total == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(total, 256), (int64_t)num_sms() * 16);
+  if (f64) scatter_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(s);
+  else scatter_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(s);
+  return check_launch("scatter_kernel");
+}
+
+}  // namespace ttnn

@@ -1,0 +1,112 @@
+// Launch wrappers of the library's device kernels (defined in *.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace ttnn {
+
+// Generic strided contraction ("walk" op), one output element per thread:
+//   out[p,b,q,j] (+)= alpha * sum_{i<NI} in[p*isP+i*isI+q*isQ+j*isJ]
+//                                  * W[i*wsI+b*wsB+q*wsQ+j*wsJ]
+// with out at p*osP+b*osB+q*osQ+j*osJ.  W == nullptr means W = 1.  When
+// `partial` is given the sum over i is split into nsplit chunks that are
+// reduced in a fixed order (deterministic).
+struct Contract {
+  int64_t P = 1, NI = 1, NB = 1, Q = 1, J = 1;
+  int64_t isP = 0, isI = 0, isQ = 0, isJ = 0;
+  int64_t wsI = 0, wsB = 0, wsQ = 0, wsJ = 0;
+  int64_t osP = 0, osB = 0, osQ = 0, osJ = 0;
+  const void* in = nullptr;
+  const void* w = nullptr;
+  void* out = nullptr;
+  double alpha = 1.0;
+  int accumulate = 0;
+};
+
+// element type codes for the contraction
+enum ElemType { ET_F32 = 0, ET_F64 = 1 };
+
+// Launches the contraction: (in, w, out, accumulation) types
+// (f32,f32,f32,f32), (f64,f64,f64,f64), (f32,f64,f64,f64).
+ttnn_status launch_contract(const Contract& c, ElemType tin, ElemType tw, ElemType tout,
+                            void* partial, int64_t partial_elems, cudaStream_t st);
+// Workspace elements (of the output type) the contraction needs for split-K.
+int64_t contract_partial_elems(const Contract& c);
+
+// SIMT GEMM C[i][j] (+)= alpha * sum_k A(i,k) B(j,k), A(i,k) = A[i*asi+k*ask],
+// B(j,k) = B[j*bsj+k*bsk]; C row-major with leading dimension ldc.
+// Input types: 0 = f64, 1 = f32, 2 = bf16; accumulation f64 for f64 inputs,
+// f32 otherwise; C has the accumulation type.  Split-K over `nsplit` chunks
+// writes partials [nsplit][I][ldc] to `partial` and reduces in order.
+struct Gemm {
+  int64_t I = 0, Jn = 0, K = 0;
+  int64_t asi = 0, ask = 0, bsj = 0, bsk = 0, ldc = 0;
+  const void* A = nullptr;
+  const void* B = nullptr;
+  void* C = nullptr;
+  int in_type = 1;
+};
+ttnn_status launch_gemm(const Gemm& g, int nsplit, void* partial, cudaStream_t st);
+int gemm_choose_split(const Gemm& g);
+
+// DRM kernels
+ttnn_status launch_philox(uint64_t seed, int kind, int ident, int64_t rows, int64_t cols,
+                          int round_fmt, double* dst, cudaStream_t st);
+ttnn_status launch_convert_f64_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+
+// Side (pass DRM) block: out[col][row] for col < w, row < nrows (leading dim
+// ld_out >= nrows), in the pass storage format (0 f64, 1 f32, 2 bf16, 3 e4m3).
+// Column c of the block is described by a SideCol: a Khatri-Rao product of
+// per-mode factor columns (kr), a Kronecker/identity column (ident), or zero.
+struct SideSpec {
+  int nmodes = 0;                 // modes of the side (row index = row-major over them)
+  int64_t ext[8] = {0};           // extents of the box on these modes
+  int64_t off[8] = {0};           // box offsets on these modes
+  int64_t full[8] = {0};          // full mode sizes (identity blocks)
+  const double* xf[8] = {nullptr};   // X factor of each mode (n_mu x rmax, f64)
+  const double* yf[8] = {nullptr};   // Y factor of each mode (n_mu x smax, f64)
+  int rmax = 0, smax = 0;
+  int x_cols = 0;                 // columns [0, x_cols): kr of X
+  int y_cols = 0;                 // next y_cols: kr of Y (y_kind 0) or identity (y_kind 1)
+  int y_kind = 0;
+  int total_cols = 0;             // padded width (zero columns after)
+  int round_fmt = 0;              // rounding of the exact f64 product
+  int store = 1;                  // 0 f64, 1 f32, 2 bf16, 3 e4m3
+  int64_t ld = 0;                 // leading dim (>= rows)
+};
+ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st);
+
+// misc
+ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st);
+ttnn_status launch_axpy(void* y, const void* x, double alpha, int64_t n, int is_f64, cudaStream_t st);
+ttnn_status launch_eye(double* dst, int64_t n, cudaStream_t st);
+ttnn_status launch_finite_check(const void* data, int64_t n, int type, int* flag, cudaStream_t st);
+
+// Recovery (binary64): for each job, QR of Omega (s x r, state type) into
+// Q (s x r) with diag R >= 0, one-sided Jacobi SVD of R and the
+// eps-pseudo-inverse Rp (r x r); kept rank to kept[job].
+struct QrJob {
+  const void* omega;
+  double* q;
+  double* rp;
+  int s, r;
+};
+ttnn_status launch_qr_pinv(const QrJob* jobs_dev, int njobs, int state_f64, double eps_factor,
+                           double u, int* kept_dev, cudaStream_t st);
+constexpr int kMaxRecoverS = 128;
+constexpr int kMaxRecoverR = 64;
+
+}  // namespace ttnn
+
+namespace ttnn {
+// out[sum_a (off_a + i_a) * os_a] += alpha * in[sum_a i_a * is_a] over the
+// box of sizes `size` (up to 12 axes); in/out of the same type (f32 / f64).
+struct Scatter {
+  int nd = 0;
+  int64_t size[12] = {0}, is[12] = {0}, os[12] = {0}, off[12] = {0};
+  const void* in = nullptr;
+  void* out = nullptr;
+  double alpha = 1.0;
+};
+ttnn_status launch_scatter_add(const Scatter& s, int f64, cudaStream_t st);
+}  // namespace ttnn

@@ -1,0 +1,1083 @@
+// Host plan (tree normalisation, first-level split, layouts) and the update /
+// recovery programs: the first-level pass over the dense block, the tree walk
+// that turns its two products into every node's Omega_v and Psi_v, and the
+// binary64 core assembly.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <functional>
+#include <numeric>
+
+#include "plan.cuh"
+
+namespace ttnn {
+
+// tensor-core pass (pass_tc.cu)
+ttnn_status tc_pass_supported(const ttnn_plan_s& P, int64_t nL, int64_t nR);
+ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int64_t nR,
+                           const void* sR, int64_t ldR, const void* sL, int64_t ldL, void* D1,
+                           void* D2, const float* tile_scale, void* ws, int64_t ws_bytes,
+                           cudaStream_t st, bool dry, int64_t* ws_need);
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const int64_t* dims,
+                       const int32_t* ranks, const int32_t* oversample, uint64_t seed,
+                       const ttnn_opts* opts) {
+  TTNN_CHECK_ARG(tree && dims && ranks && oversample, "null argument");
+  TTNN_CHECK_ARG(d >= 1 && d <= 16, "order d must be in 1..16");
+  const int n = tree->n_nodes;
+  TTNN_CHECK_ARG(n >= 1 && tree->parent && tree->leaf_mode_ptr, "empty tree");
+  P.d = d;
+  P.dims.assign(dims, dims + d);
+  P.N = 1;
+  for (int m = 0; m < d; ++m) {
+    TTNN_CHECK_ARG(dims[m] >= 1, "mode size %d must be >= 1", m);
+    TTNN_CHECK_ARG(P.N <= (int64_t(1) << 46) / dims[m], "tensor too large");
+    P.N *= dims[m];
+  }
+  if (opts) {
+    P.variant = opts->variant;
+    P.dtype = opts->sketch_dtype;
+    P.eps_factor = opts->eps_factor;
+    P.u = opts->unit_roundoff;
+    P.flags = opts->flags;
+  }
+  TTNN_CHECK_ARG(P.variant == 0 || P.variant == 1, "bad variant");
+  TTNN_CHECK_ARG(P.dtype >= 0 && P.dtype <= 4, "bad sketch dtype");
+  TTNN_CHECK_ARG(P.eps_factor >= 0 && P.u >= 0, "eps_factor and unit_roundoff must be >= 0");
+  P.seed = seed;
+  P.nodes.assign(n, TNode());
+  int root = -1;
+  for (int v = 0; v < n; ++v) {
+    const int p = tree->parent[v];
+    TTNN_CHECK_ARG(p >= -1 && p < n && p != v, "bad parent index of node %d", v);
+    if (p == -1) {
+      TTNN_CHECK_ARG(root < 0, "more than one root");
+      root = v;
+    }
+    P.nodes[v].user = v;
+    P.nodes[v].parent = p;
+  }
+  TTNN_CHECK_ARG(root >= 0, "no root");
+  P.root = root;
+  for (int v = 0; v < n; ++v)
+    if (P.nodes[v].parent >= 0) P.nodes[P.nodes[v].parent].ch.push_back(v);
+  // reachability / acyclicity
+  {
+    std::vector<char> seen(n, 0);
+    std::vector<int> stack{root};
+    int cnt = 0;
+    while (!stack.empty()) {
+      const int v = stack.back();
+      stack.pop_back();
+      TTNN_CHECK_ARG(!seen[v], "cycle in tree");
+      seen[v] = 1;
+      ++cnt;
+      for (int c : P.nodes[v].ch) stack.push_back(c);
+    }
+    TTNN_CHECK_ARG(cnt == n, "tree is not connected");
+  }
+  // mode ranges, bottom-up
+  std::vector<int> mode_owner(d, -1);
+  std::function<ttnn_status(int)> visit = [&](int v) -> ttnn_status {
+    TNode& nd = P.nodes[v];
+    const int b = tree->leaf_mode_ptr[v], e = tree->leaf_mode_ptr[v + 1];
+    TTNN_CHECK_ARG(e >= b, "bad leaf_mode_ptr");
+    const bool ident = tree->identity && tree->identity[v];
+    if (nd.ch.empty()) {
+      TTNN_CHECK_ARG(e > b && tree->leaf_modes, "leaf %d without modes", v);
+      std::vector<int> lm(tree->leaf_modes + b, tree->leaf_modes + e);
+      std::sort(lm.begin(), lm.end());
+      for (size_t k = 0; k < lm.size(); ++k) {
+        TTNN_CHECK_ARG(lm[k] >= 0 && lm[k] < d, "leaf mode out of range");
+        TTNN_CHECK_ARG(lm[k] == lm[0] + (int)k, "leaf modes must be contiguous");
+        TTNN_CHECK_ARG(mode_owner[lm[k]] < 0, "leaf modes must partition 0..d-1");
+        mode_owner[lm[k]] = v;
+      }
+      nd.lo = lm.front();
+      nd.hi = lm.back() + 1;
+      nd.leaf = true;
+      return TTNN_OK;
+    }
+    TTNN_CHECK_ARG(e == b, "internal node %d with own modes", v);
+    TTNN_CHECK_ARG(nd.ch.size() >= 2, "internal node %d needs >= 2 children", v);
+    TTNN_CHECK_ARG(!ident, "identity flag only on leaves");
+    for (int c : nd.ch) TTNN_TRY(visit(c));
+    std::sort(nd.ch.begin(), nd.ch.end(), [&](int x, int y) { return P.nodes[x].lo < P.nodes[y].lo; });
+    for (size_t k = 0; k + 1 < nd.ch.size(); ++k)
+      TTNN_CHECK_ARG(P.nodes[nd.ch[k]].hi == P.nodes[nd.ch[k + 1]].lo, "node modes must be contiguous");
+    nd.lo = P.nodes[nd.ch.front()].lo;
+    nd.hi = P.nodes[nd.ch.back()].hi;
+    nd.leaf = false;
+    return TTNN_OK;
+  };
+  TTNN_TRY(visit(root));
+  for (int m = 0; m < d; ++m) TTNN_CHECK_ARG(mode_owner[m] >= 0, "leaf modes must partition 0..d-1");
+  // lexicographic order
+  {
+    std::vector<int> level{root};
+    int lvl = 0;
+    while (!level.empty()) {
+      for (size_t k = 0; k < level.size(); ++k) {
+        P.nodes[level[k]].level = lvl;
+        P.nodes[level[k]].pos = (int)k;
+        P.nodes[level[k]].lex = (int)P.lex.size();
+        P.lex.push_back(level[k]);
+      }
+      std::vector<int> next;
+      for (int v : level)
+        for (int c : P.nodes[v].ch) next.push_back(c);
+      level.swap(next);
+      ++lvl;
+    }
+  }
+  // ranks
+  for (int v = 0; v < n; ++v) {
+    TNode& nd = P.nodes[v];
+    nd.n = 1;
+    for (int m = nd.lo; m < nd.hi; ++m) nd.n *= P.dims[m];
+    if (v == root) continue;
+    const bool ident = tree->identity && tree->identity[v];
+    if (nd.leaf && ident) {
+      nd.identity = true;
+      nd.r = (int)std::min<int64_t>(nd.n, 1 << 30);
+      nd.p = 0;
+      nd.s = nd.r;
+      continue;
+    }
+    int r = ranks[v], p = oversample[v];
+    TTNN_CHECK_ARG(r >= 1 && p >= 0, "ranks must be >= 1 and oversample >= 0 (node %d)", v);
+    const int64_t nc = P.N / nd.n;
+    if (nd.leaf && r >= nd.n) {
+      nd.identity = true;
+      nd.r = nd.s = (int)nd.n;
+      nd.p = 0;
+      continue;
+    }
+    r = (int)std::min<int64_t>(std::min<int64_t>(r, nd.n), nc);
+    p = (int)std::min<int64_t>(p, nd.n - r);
+    nd.r = r;
+    nd.p = p;
+    nd.s = r + p;
+  }
+  // rsub (post-order) and r_max / s_max
+  P.rmax = P.smax = 1;
+  std::function<int(int)> rs = [&](int v) -> int {
+    TNode& nd = P.nodes[v];
+    int m = nd.sketched() ? nd.r : 0;
+    for (int c : nd.ch) m = std::max(m, rs(c));
+    nd.rsub = m;
+    return m;
+  };
+  rs(root);
+  P.n_sketched = 0;
+  for (auto& nd : P.nodes)
+    if (nd.sketched()) {
+      P.rmax = std::max(P.rmax, nd.r);
+      P.smax = std::max(P.smax, nd.s);
+      TTNN_CHECK_ARG(nd.r <= kMaxRecoverR && nd.s <= kMaxRecoverS,
+                     "rank %d / sketch size %d above the recovery limits (%d, %d)", nd.r, nd.s,
+                     kMaxRecoverR, kMaxRecoverS);
+      ++P.n_sketched;
+    }
+  // STTNN reuse sets
+  for (int v = 0; v < n; ++v) {
+    if (v == root) continue;
+    std::vector<int> S;
+    int u = v;
+    while (P.nodes[u].parent >= 0) {
+      const TNode& par = P.nodes[P.nodes[u].parent];
+      for (int c : par.ch) {
+        if (c == u) break;
+        if (!P.nodes[c].identity) S.push_back(c);
+      }
+      u = P.nodes[u].parent;
+      if (u == root) break;
+    }
+    std::sort(S.begin(), S.end(), [&](int x, int y) { return P.nodes[x].lo < P.nodes[y].lo; });
+    P.nodes[v].reuse = S;
+  }
+  // number formats
+  P.walk_f64 = (P.dtype == TTNN_F64);
+  switch (P.dtype) {
+    case TTNN_F64: P.pass_store = 0; P.round_fmt = RF_F64; break;
+    case TTNN_F32: P.pass_store = 1; P.round_fmt = RF_F32; break;
+    case TTNN_BF16: P.pass_store = 2; P.round_fmt = RF_BF16; break;
+    case TTNN_E4M3: P.pass_store = 3; P.round_fmt = RF_E4M3; break;
+    default: P.pass_store = 2; P.round_fmt = RF_BF16; break;   // BF16X2: bf16 DRM blocks
+  }
+  // first-level split
+  const TNode& R0 = P.nodes[root];
+  const int m = (int)R0.ch.size();
+  if (R0.ch.empty()) {
+    set_error("the root must have children (d >= 2)");
+    return TTNN_EINVAL;
+  }
+  auto sprime = [&](int c) { return P.nodes[c].identity ? (int64_t)P.nodes[c].n : (int64_t)P.nodes[c].s; };
+  if (P.variant == TTNN_VARIANT_STTNN) {
+    P.a = 1;
+    P.yside = 1;
+    if (P.nodes[R0.ch[0]].identity) {
+      set_error("STTNN with an identity first root child is not supported");
+      return TTNN_EUNSUPPORTED;
+    }
+  } else if (m == 2) {
+    P.a = 1;
+    P.yside = (sprime(R0.ch[1]) <= sprime(R0.ch[0])) ? 0 : 1;
+  } else {
+    P.a = m - 1;
+    P.yside = 0;
+  }
+  P.Lch.assign(R0.ch.begin(), R0.ch.begin() + P.a);
+  P.Rch.assign(R0.ch.begin() + P.a, R0.ch.end());
+  P.Llo = P.nodes[P.Lch.front()].lo;
+  P.Lhi = P.nodes[P.Lch.back()].hi;
+  P.Rlo = P.nodes[P.Rch.front()].lo;
+  P.Rhi = P.nodes[P.Rch.back()].hi;
+  P.ychild = (P.yside == 0) ? P.Rch[0] : P.Lch[0];
+  if (P.yside == 0 && P.Rch.size() != 1) P.ychild = -1;
+  if (P.yside == 1 && P.Lch.size() != 1) P.ychild = -1;
+  if (P.ychild < 0) {
+    set_error("internal: pass Y side must be a single root child");
+    return TTNN_EUNSUPPORTED;
+  }
+  P.rXL = 0;
+  for (int c : P.Lch) P.rXL = std::max(P.rXL, P.nodes[c].rsub);
+  P.rXR = 0;
+  if (P.variant == TTNN_VARIANT_TTNN)
+    for (int c : P.Rch) P.rXR = std::max(P.rXR, P.nodes[c].rsub);
+  const int64_t wy = sprime(P.ychild);
+  TTNN_CHECK_ARG(wy <= 4096, "pass Y block too wide (%lld columns)", (long long)wy);
+  P.wYR = P.yside == 0 ? (int)wy : 0;
+  P.wYL = P.yside == 1 ? (int)wy : 0;
+  P.yR_ident = P.yside == 0 && P.nodes[P.ychild].identity;
+  P.yL_ident = P.yside == 1 && P.nodes[P.ychild].identity;
+  P.wR = P.rXL + P.wYR;
+  P.wL = P.rXR + P.wYL;
+  P.wRpad = (int)round_up(P.wR, 16);
+  P.wLpad = (int)round_up(P.wL, 16);
+  // state layout (lex order): Omega_v then Psi_v; root: Psi_root
+  int64_t off = 0;
+  for (int v : P.lex) {
+    TNode& nd = P.nodes[v];
+    nd.ps_shape.clear();
+    if (v == root) {
+      nd.ps_el = 1;
+      for (int c : nd.ch) {
+        nd.ps_shape.push_back(sprime(c));
+        nd.ps_el *= sprime(c);
+      }
+      TTNN_CHECK_ARG(nd.ps_el <= (int64_t(1) << 33), "root sketch too large");
+      nd.ps_off = off;
+      off += nd.ps_el;
+      continue;
+    }
+    if (!nd.sketched()) continue;
+    nd.om_off = off;
+    nd.om_el = (int64_t)nd.s * nd.r;
+    off += nd.om_el;
+    if (nd.leaf) {
+      nd.ps_shape = {nd.n, (int64_t)nd.r};
+      nd.ps_el = nd.n * nd.r;
+    } else {
+      nd.ps_el = nd.r;
+      for (int c : nd.ch) {
+        nd.ps_shape.push_back(sprime(c));
+        nd.ps_el *= sprime(c);
+      }
+      nd.ps_shape.push_back(nd.r);
+    }
+    nd.ps_off = off;
+    off += nd.ps_el;
+  }
+  P.state_elems = off;
+  // core layout (lex order)
+  off = 0;
+  for (int v : P.lex) {
+    TNode& nd = P.nodes[v];
+    nd.core_shape.clear();
+    if (v == root) {
+      for (int c : nd.ch) nd.core_shape.push_back(P.nodes[c].r);
+    } else if (nd.identity) {
+      nd.core_shape = {nd.n};
+      for (int mm = nd.lo; mm < nd.hi; ++mm) nd.core_shape.push_back(P.dims[mm]);
+    } else if (nd.leaf) {
+      nd.core_shape = {(int64_t)nd.r};
+      for (int mm = nd.lo; mm < nd.hi; ++mm) nd.core_shape.push_back(P.dims[mm]);
+    } else {
+      nd.core_shape = {(int64_t)nd.r};
+      for (int c : nd.ch) nd.core_shape.push_back(P.nodes[c].r);
+    }
+    nd.core_el = 1;
+    for (int64_t x : nd.core_shape) nd.core_el *= x;
+    nd.core_off = off;
+    off += nd.core_el;
+  }
+  P.core_elems = off;
+  // factor layout: X_mu, Y_mu, then XT_v of sketched nodes
+  off = 0;
+  P.x_off.assign(d, 0);
+  P.y_off.assign(d, 0);
+  for (int mm = 0; mm < d; ++mm) {
+    P.x_off[mm] = off;
+    off += P.dims[mm] * P.rmax;
+    P.y_off[mm] = off;
+    off += P.dims[mm] * P.smax;
+  }
+  for (int v : P.lex) {
+    TNode& nd = P.nodes[v];
+    if (!nd.sketched()) continue;
+    nd.xt_off = off;
+    off += (int64_t)nd.s * P.rmax;
+  }
+  P.fac_elems = off;
+  return TTNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace stack and tensor views
+// ---------------------------------------------------------------------------
+struct Ws {
+  char* base;
+  int64_t cap, top = 0, peak = 0;
+  bool dry;
+  Ws(char* b, int64_t c, bool d) : base(b), cap(c), dry(d) {}
+  char* alloc(int64_t bytes) {
+    const int64_t o = round_up(top, 256);
+    top = o + std::max<int64_t>(bytes, 0);
+    peak = std::max(peak, top);
+    if (dry) return base + 0;   // never dereferenced in a dry run
+    return base + o;
+  }
+  bool ok() const { return dry || top <= cap; }
+};
+
+enum AxKind { AX_MODE = 0, AX_SK = 1, AX_J = 2 };
+struct Ax {
+  int kind;
+  int id;          // mode (AX_MODE) or child node (AX_SK)
+  int64_t size;
+  int64_t off;     // box offset (AX_MODE)
+};
+struct View {
+  char* ptr;
+  std::vector<Ax> ax;
+  int64_t ld;      // stride of the next-to-last axis
+};
+
+static int64_t vstride(const View& v, int k) {
+  const int L = (int)v.ax.size() - 1;
+  if (k == L) return 1;
+  if (k == L - 1) return v.ld;
+  return vstride(v, k + 1) * v.ax[k + 1].size;
+}
+static int64_t vsize(const View& v) {
+  int64_t s = 1;
+  for (auto& a : v.ax) s *= a.size;
+  return s;
+}
+
+struct Ctx {
+  ttnn_plan_s& P;
+  Ws& ws;
+  cudaStream_t st;
+  bool dry;
+  int eb;               // walk element bytes
+  ElemType et;
+  const Box& box;
+  const char* facw;     // walk-type factors
+  const char* yw;       // walk-type copy of the pass Y block (rows of the Y child, box)
+  int64_t yw_ld;
+};
+
+static int find_ax(const View& v, int kind, int id) {
+  for (int k = 0; k < (int)v.ax.size(); ++k)
+    if (v.ax[k].kind == kind && v.ax[k].id == id) return k;
+  return -1;
+}
+
+// Contract axis k of `in` against W.  shared < 0: mode product creating a new
+// axis `nax` at position k, W(i, b) = W[i*wsI + b*wsX].  shared == last or
+// shared == k + 1: the reduction shares that axis' index x with W,
+// W(i, x) = W[i*wsI + x*wsX]; the axis stays.  The output is contiguous.
+static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, int64_t wsI,
+                                 int64_t wsX, int shared, const Ax* nax, View* out) {
+  const int L = (int)in.ax.size() - 1;
+  Contract c;
+  c.P = 1;
+  for (int a = 0; a < k; ++a) c.P *= in.ax[a].size;
+  c.isP = k > 0 ? vstride(in, k - 1) : 0;
+  c.NI = in.ax[k].size;
+  c.isI = vstride(in, k);
+  c.w = W;
+  c.wsI = wsI;
+  std::vector<Ax> oax;
+  if (shared < 0) {
+    c.NB = nax->size;
+    c.wsB = wsX;
+    if (k < L) {
+      c.Q = 1;
+      for (int a = k + 1; a < L; ++a) c.Q *= in.ax[a].size;
+      c.isQ = (k < L - 1) ? vstride(in, L - 1) : 0;
+      c.J = in.ax[L].size;
+      c.isJ = 1;
+    }
+    oax.assign(in.ax.begin(), in.ax.begin() + k);
+    oax.push_back(*nax);
+    oax.insert(oax.end(), in.ax.begin() + k + 1, in.ax.end());
+  } else if (shared == L) {
+    if (k >= L) { set_error("internal: bad shared-column contraction"); return TTNN_EUNSUPPORTED; }
+    c.Q = 1;
+    for (int a = k + 1; a < L; ++a) c.Q *= in.ax[a].size;
+    c.isQ = (k < L - 1) ? vstride(in, L - 1) : 0;
+    c.J = in.ax[L].size;
+    c.isJ = 1;
+    c.wsJ = wsX;
+    oax = in.ax;
+    oax.erase(oax.begin() + k);
+  } else if (shared == k + 1) {
+    c.Q = in.ax[k + 1].size;
+    c.isQ = vstride(in, k + 1);
+    c.J = 1;
+    for (int a = k + 2; a <= L; ++a) c.J *= in.ax[a].size;
+    c.isJ = 1;
+    if (k + 2 <= L - 1 && in.ld != in.ax[L].size) {
+      set_error("internal: non-contiguous column group");
+      return TTNN_EUNSUPPORTED;
+    }
+    c.wsQ = wsX;
+    oax = in.ax;
+    oax.erase(oax.begin() + k);
+  } else {
+    set_error("internal: unsupported shared axis");
+    return TTNN_EUNSUPPORTED;
+  }
+  View o;
+  o.ax = oax;
+  o.ld = o.ax.back().size;
+  const int64_t total = vsize(o);
+  o.ptr = C.ws.alloc(total * C.eb);
+  c.out = o.ptr;
+  c.osJ = 1;
+  c.osQ = c.J;
+  c.osB = c.Q * c.J;
+  c.osP = c.NB * c.Q * c.J;
+  c.in = in.ptr;
+  const int64_t pe = contract_partial_elems(c);
+  const int64_t mark = C.ws.top;
+  char* partial = pe ? C.ws.alloc(pe * C.eb) : nullptr;
+  if (!C.dry) TTNN_TRY(launch_contract(c, C.et, C.et, C.et, partial, pe, C.st));
+  C.ws.top = mark;    // partial buffer is free again once the launch is queued
+  *out = o;
+  return TTNN_OK;
+}
+
+static const char* facX(Ctx& C, int mode) { return C.facw + (C.P.x_off[mode] + C.box.off[mode] * C.P.rmax) * C.eb; }
+static const char* facY(Ctx& C, int mode) { return C.facw + (C.P.y_off[mode] + C.box.off[mode] * C.P.smax) * C.eb; }
+
+// Khatri-Rao contraction of the modes [lo, hi) of `in` with the Y factors,
+// producing one sketch axis (kind AX_SK, id = node) of size s at the place of
+// the modes (Sec. 7: Y_t = kr of its modes' Y_mu, columns shared).
+static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int s, View* out) {
+  View cur = in;
+  for (int mode = hi - 1; mode >= lo; --mode) {
+    const int k = find_ax(cur, AX_MODE, mode);
+    if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
+    View nx;
+    if (mode == hi - 1) {
+      Ax nax{AX_SK, node, s, 0};
+      TTNN_TRY(contract_view(C, cur, k, facY(C, mode), C.P.smax, 1, -1, &nax, &nx));
+    } else {
+      TTNN_TRY(contract_view(C, cur, k, facY(C, mode), C.P.smax, 1, k + 1, nullptr, &nx));
+    }
+    cur = nx;
+  }
+  *out = cur;
+  return TTNN_OK;
+}
+
+// Contraction of one mode with X_mu sharing the column axis (last axis).
+static ttnn_status x_mode(Ctx& C, const View& in, int mode, View* out) {
+  const int k = find_ax(in, AX_MODE, mode);
+  if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
+  return contract_view(C, in, k, facX(C, mode), C.P.rmax, 1, (int)in.ax.size() - 1, nullptr, out);
+}
+
+// STTNN: contraction of group s with E_s = Y_s XT_s (Y chain, then XT_s on
+// the new sketch axis sharing the column axis).
+static ttnn_status e_group(Ctx& C, const View& in, int s, View* out) {
+  const TNode& ns = C.P.nodes[s];
+  View y;
+  TTNN_TRY(y_chain(C, in, s, ns.lo, ns.hi, ns.s, &y));
+  const int k = find_ax(y, AX_SK, s);
+  const char* xt = C.facw + ns.xt_off * C.eb;
+  return contract_view(C, y, k, xt, C.P.rmax, 1, (int)y.ax.size() - 1, nullptr, out);
+}
+
+// Adds alpha * view into the state at `base` with per-axis output strides.
+static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::vector<int64_t>& os,
+                                double alpha) {
+  Scatter s;
+  s.nd = (int)v.ax.size();
+  if (s.nd > 12) { set_error("internal: too many axes"); return TTNN_EUNSUPPORTED; }
+  for (int a = 0; a < s.nd; ++a) {
+    s.size[a] = v.ax[a].size;
+    s.is[a] = vstride(v, a);
+    s.os[a] = os[a];
+    s.off[a] = v.ax[a].kind == AX_MODE ? v.ax[a].off : 0;
+  }
+  s.in = v.ptr;
+  s.out = base;
+  s.alpha = alpha;
+  if (C.dry) return TTNN_OK;
+  return launch_scatter_add(s, C.P.walk_f64, C.st);
+}
+
+// Output strides of a Psi-shaped target: children axes (sketch or raw modes of
+// identity children) then optionally the column axis.
+static std::vector<int64_t> psi_strides(Ctx& C, const View& v, const TNode& nd, bool with_j) {
+  const int m = (int)nd.ch.size();
+  std::vector<int64_t> cs(m);
+  int64_t acc = with_j ? nd.r : 1;
+  for (int k = m - 1; k >= 0; --k) {
+    cs[k] = acc;
+    const TNode& c = C.P.nodes[nd.ch[k]];
+    acc *= c.identity ? c.n : c.s;
+  }
+  std::vector<int64_t> os(v.ax.size(), 0);
+  for (size_t a = 0; a < v.ax.size(); ++a) {
+    const Ax& x = v.ax[a];
+    if (x.kind == AX_J) { os[a] = 1; continue; }
+    for (int k = 0; k < m; ++k) {
+      const TNode& c = C.P.nodes[nd.ch[k]];
+      if (x.kind == AX_SK && x.id == nd.ch[k]) os[a] = cs[k];
+      if (x.kind == AX_MODE && x.id >= c.lo && x.id < c.hi) {
+        int64_t sub = 1;
+        for (int mm = x.id + 1; mm < c.hi; ++mm) sub *= C.P.dims[mm];
+        os[a] = cs[k] * sub;
+      }
+    }
+  }
+  return os;
+}
+
+static View truncate_j(const View& v, int64_t j) {
+  View o = v;
+  o.ax.back().size = std::min<int64_t>(o.ax.back().size, j);
+  return o;
+}
+
+static char* state_at(Ctx& C, void* acc, int64_t elem_off) { return (char*)acc + elem_off * C.eb; }
+
+// Node v with G_v = T^(v) X_v over the box (axes: v's modes, then columns).
+static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) {
+  ttnn_plan_s& P = C.P;
+  const TNode& nd = P.nodes[v];
+  if (nd.rsub == 0) return TTNN_OK;
+  if (nd.sketched()) {
+    const View Gt = truncate_j(G, nd.r);
+    const int64_t mark = C.ws.top;
+    View om;
+    if (v == P.ychild) {
+      // Y of the pass-side root child is the stored (rounded) block
+      View mg = Gt;
+      int64_t nb = 1;
+      for (int a = 0; a + 1 < (int)Gt.ax.size(); ++a) nb *= Gt.ax[a].size;
+      mg.ax = {Ax{AX_MODE, nd.lo, nb, 0}, Gt.ax.back()};
+      Ax nax{AX_SK, v, nd.s, 0};
+      TTNN_TRY(contract_view(C, mg, 0, C.yw, 1, C.yw_ld, -1, &nax, &om));
+    } else {
+      TTNN_TRY(y_chain(C, Gt, v, nd.lo, nd.hi, nd.s, &om));
+    }
+    TTNN_TRY(scatter_into(C, om, state_at(C, acc, nd.om_off), {(int64_t)nd.r, 1}, lambda));
+    C.ws.top = mark;
+    if (nd.leaf) {
+      std::vector<int64_t> os(Gt.ax.size(), 1);
+      for (int a = 0; a + 1 < (int)Gt.ax.size(); ++a) {
+        int64_t sub = nd.r;
+        for (int mm = Gt.ax[a].id + 1; mm < nd.hi; ++mm) sub *= P.dims[mm];
+        os[a] = sub;
+      }
+      TTNN_TRY(scatter_into(C, Gt, state_at(C, acc, nd.ps_off), os, lambda));
+    } else {
+      View cur = Gt;
+      for (int k = (int)nd.ch.size() - 1; k >= 0; --k) {
+        const TNode& c = P.nodes[nd.ch[k]];
+        if (c.identity) continue;
+        View nx;
+        TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+        cur = nx;
+      }
+      TTNN_TRY(scatter_into(C, cur, state_at(C, acc, nd.ps_off), psi_strides(C, cur, nd, true), lambda));
+      C.ws.top = mark;
+    }
+  }
+  // children
+  for (size_t k = 0; k < nd.ch.size(); ++k) {
+    const TNode& c = P.nodes[nd.ch[k]];
+    if (c.rsub == 0) continue;
+    const int64_t mark = C.ws.top;
+    View cur = truncate_j(G, c.rsub);
+    for (size_t k2 = 0; k2 < nd.ch.size(); ++k2) {
+      if (k2 == k) continue;
+      const TNode& sib = P.nodes[nd.ch[k2]];
+      View nx;
+      if (P.variant == TTNN_VARIANT_STTNN && k2 < k && !sib.identity) {
+        TTNN_TRY(e_group(C, cur, sib.user, &nx));
+        cur = nx;
+      } else {
+        for (int mm = sib.hi - 1; mm >= sib.lo; --mm) {
+          TTNN_TRY(x_mode(C, cur, mm, &nx));
+          cur = nx;
+        }
+      }
+    }
+    TTNN_TRY(walk(C, acc, c.user, cur, lambda));
+    C.ws.top = mark;
+  }
+  return TTNN_OK;
+}
+
+static void side_spec_common(ttnn_plan_s& P, const Box& box, int lo, int hi, SideSpec& s) {
+  s.nmodes = hi - lo;
+  for (int k = 0; k < s.nmodes; ++k) {
+    s.ext[k] = box.ext[lo + k];
+    s.off[k] = box.off[lo + k];
+    s.full[k] = P.dims[lo + k];
+    s.xf[k] = P.fac64 + P.x_off[lo + k];
+    s.yf[k] = P.fac64 + P.y_off[lo + k];
+  }
+  s.rmax = P.rmax;
+  s.smax = P.smax;
+  s.round_fmt = P.round_fmt;
+  s.store = P.pass_store;
+}
+
+static int store_bytes(int store) { return store == 0 ? 8 : store == 1 ? 4 : store == 2 ? 2 : 1; }
+
+ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
+                      cudaStream_t st) {
+  SideSpec s;
+  if (which == 0) {   // B_R: rows over R modes
+    side_spec_common(P, box, P.Rlo, P.Rhi, s);
+    s.x_cols = P.rXL;
+    s.y_cols = P.wYR;
+    s.y_kind = P.yR_ident;
+    s.total_cols = P.wRpad;
+    if (P.yside == 0 && P.wYR && !P.yR_ident) {
+      // Y block of the single R child = Khatri-Rao over its modes (all R modes)
+    }
+  } else {
+    side_spec_common(P, box, P.Llo, P.Lhi, s);
+    s.x_cols = P.rXR;
+    s.y_cols = P.wYL;
+    s.y_kind = P.yL_ident;
+    s.total_cols = P.wLpad;
+  }
+  s.ld = ld;
+  return launch_side(s, out, st);
+}
+
+// Walk-type copy of the pass Y block (rows over the Y child's box modes).
+ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st) {
+  SideSpec s;
+  const TNode& c = P.nodes[P.ychild];
+  side_spec_common(P, box, c.lo, c.hi, s);
+  s.x_cols = 0;
+  s.y_cols = c.s;
+  s.y_kind = 0;
+  s.total_cols = c.s;
+  s.store = P.walk_f64 ? 0 : 1;
+  s.ld = ld;
+  return launch_side(s, out, st);
+}
+
+ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
+                             const float* tile_scale, double lambda, cudaStream_t st, bool dry,
+                             int64_t* peak) {
+  Ws ws(P.ws, P.ws_bytes, dry);
+  const int eb = P.walk_f64 ? 8 : 4;
+  Ctx C{P, ws, st, dry, eb, P.walk_f64 ? ET_F64 : ET_F32, box, (const char*)P.facw, nullptr, 0};
+  int64_t nL = 1, nR = 1;
+  for (int m = P.Llo; m < P.Lhi; ++m) nL *= box.ext[m];
+  for (int m = P.Rlo; m < P.Rhi; ++m) nR *= box.ext[m];
+  const int sb = store_bytes(P.pass_store);
+  // side blocks of the box
+  const void* sR = nullptr;
+  const void* sL = nullptr;
+  if (box.full && P.sideR) sR = P.sideR;
+  if (box.full && P.sideL) sL = P.sideL;
+  if (P.wR > 0 && !sR) {
+    char* b = ws.alloc((int64_t)P.wRpad * nR * sb);
+    if (!dry) TTNN_TRY(make_side(P, box, 0, b, nR, st));
+    sR = b;
+  }
+  if (P.wL > 0 && !sL) {
+    char* b = ws.alloc((int64_t)P.wLpad * nL * sb);
+    if (!dry) TTNN_TRY(make_side(P, box, 1, b, nL, st));
+    sL = b;
+  }
+  if (!P.nodes[P.ychild].identity) {
+    const TNode& yc = P.nodes[P.ychild];
+    int64_t ny = 1;
+    for (int m = yc.lo; m < yc.hi; ++m) ny *= box.ext[m];
+    C.yw_ld = ny;
+    if (box.full && P.yW) {
+      C.yw = (const char*)P.yW;
+    } else {
+      char* b = ws.alloc((int64_t)yc.s * ny * eb);
+      if (!dry) TTNN_TRY(make_side_yw(P, box, b, ny, st));
+      C.yw = b;
+    }
+  }
+  // first-level pass: D1 = M B_R^T (nL x wRpad), D2 = M^T B_L^T (nR x wLpad)
+  char* D1 = ws.alloc(nL * P.wRpad * eb);
+  char* D2 = ws.alloc(nR * P.wLpad * eb);
+  cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
+  const bool use_tc = P.tc_ok && !(P.flags & TTNN_FLAG_SIMT_PASS) &&
+                      tc_pass_supported(P, nL, nR) == TTNN_OK;
+  if (use_tc) {
+    const int64_t mark = ws.top;
+    int64_t need = 0;
+    TTNN_TRY(launch_tc_pass(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, nullptr, 0, st,
+                            true, &need));
+    char* tw = ws.alloc(need);
+    if (!dry)
+      TTNN_TRY(launch_tc_pass(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, st,
+                              false, nullptr));
+    ws.top = mark;
+  } else {
+    if (P.pass_store == 3 || P.dtype == TTNN_BF16X2) {
+      set_error("this number format needs the tensor-core pass (unsupported shape)");
+      return TTNN_EUNSUPPORTED;
+    }
+    const int in_type = P.pass_store == 0 ? 0 : P.pass_store == 1 ? 1 : 2;
+    if (P.wR > 0) {
+      Gemm g;
+      g.I = nL; g.Jn = P.wR; g.K = nR;
+      g.A = data; g.asi = nR; g.ask = 1;
+      g.B = sR; g.bsj = nR; g.bsk = 1;
+      g.C = D1; g.ldc = P.wRpad; g.in_type = in_type;
+      const int ns = gemm_choose_split(g);
+      const int64_t mark = ws.top;
+      char* part = ns > 1 ? ws.alloc((int64_t)ns * nL * P.wRpad * eb) : nullptr;
+      if (!dry) TTNN_TRY(launch_gemm(g, ns, part, st));
+      ws.top = mark;
+    }
+    if (P.wL > 0) {
+      Gemm g;
+      g.I = nR; g.Jn = P.wL; g.K = nL;
+      g.A = data; g.asi = 1; g.ask = nR;
+      g.B = sL; g.bsj = nL; g.bsk = 1;
+      g.C = D2; g.ldc = P.wLpad; g.in_type = in_type;
+      const int ns = gemm_choose_split(g);
+      const int64_t mark = ws.top;
+      char* part = ns > 1 ? ws.alloc((int64_t)ns * nR * P.wLpad * eb) : nullptr;
+      if (!dry) TTNN_TRY(launch_gemm(g, ns, part, st));
+      ws.top = mark;
+    }
+  }
+  cudaEvent_t ev1 = dry ? nullptr : prof_event(P, st);
+  prof_push(P, 0, ev0, ev1);
+  // views of the pass products
+  auto mode_axes = [&](int lo, int hi) {
+    std::vector<Ax> ax;
+    for (int m = lo; m < hi; ++m) ax.push_back(Ax{AX_MODE, m, box.ext[m], box.off[m]});
+    return ax;
+  };
+  const TNode& root = P.nodes[P.root];
+  // L side (both variants): G over L modes from D1's X part
+  if (P.rXL > 0) {
+    View GL{D1, mode_axes(P.Llo, P.Lhi), P.wRpad};
+    GL.ax.push_back(Ax{AX_J, -1, P.rXL, 0});
+    for (size_t k = 0; k < P.Lch.size(); ++k) {
+      const TNode& c = P.nodes[P.Lch[k]];
+      if (c.rsub == 0) continue;
+      const int64_t mark = ws.top;
+      View cur = truncate_j(GL, c.rsub);
+      for (size_t k2 = 0; k2 < P.Lch.size(); ++k2) {
+        if (k2 == k) continue;
+        const TNode& sib = P.nodes[P.Lch[k2]];
+        for (int mm = sib.hi - 1; mm >= sib.lo; --mm) {
+          View nx;
+          TTNN_TRY(x_mode(C, cur, mm, &nx));
+          cur = nx;
+        }
+      }
+      TTNN_TRY(walk(C, acc, c.user, cur, lambda));
+      ws.top = mark;
+    }
+  }
+  if (P.variant == TTNN_VARIANT_TTNN) {
+    if (P.rXR > 0) {
+      View GR{D2, mode_axes(P.Rlo, P.Rhi), P.wLpad};
+      GR.ax.push_back(Ax{AX_J, -1, P.rXR, 0});
+      for (size_t k = 0; k < P.Rch.size(); ++k) {
+        const TNode& c = P.nodes[P.Rch[k]];
+        if (c.rsub == 0) continue;
+        const int64_t mark = ws.top;
+        View cur = truncate_j(GR, c.rsub);
+        for (size_t k2 = 0; k2 < P.Rch.size(); ++k2) {
+          if (k2 == k) continue;
+          const TNode& sib = P.nodes[P.Rch[k2]];
+          for (int mm = sib.hi - 1; mm >= sib.lo; --mm) {
+            View nx;
+            TTNN_TRY(x_mode(C, cur, mm, &nx));
+            cur = nx;
+          }
+        }
+        TTNN_TRY(walk(C, acc, c.user, cur, lambda));
+        ws.top = mark;
+      }
+    }
+    // root Psi
+    const int64_t mark = ws.top;
+    if (P.yside == 0) {
+      View H{D1 + (int64_t)P.rXL * eb, mode_axes(P.Llo, P.Lhi), P.wRpad};
+      H.ax.push_back(Ax{AX_SK, P.ychild, P.wYR, 0});
+      View cur = H;
+      for (int k = (int)P.Lch.size() - 1; k >= 0; --k) {
+        const TNode& c = P.nodes[P.Lch[k]];
+        if (c.identity) continue;
+        View nx;
+        TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+        cur = nx;
+      }
+      std::vector<int64_t> os = psi_strides(C, cur, root, false);
+      // the last axis is the R child's pass-side sketch (or its full raw index)
+      os.back() = 1;
+      TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
+    } else {
+      View H{D2 + (int64_t)P.rXR * eb, mode_axes(P.Rlo, P.Rhi), P.wLpad};
+      H.ax.push_back(Ax{AX_SK, P.ychild, P.wYL, 0});
+      View cur = H;
+      for (int k = (int)P.Rch.size() - 1; k >= 0; --k) {
+        const TNode& c = P.nodes[P.Rch[k]];
+        if (c.identity) continue;
+        View nx;
+        TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+        cur = nx;
+      }
+      std::vector<int64_t> os = psi_strides(C, cur, root, false);
+      int64_t rest = 1;
+      for (size_t k = 1; k < root.ch.size(); ++k) {
+        const TNode& c = P.nodes[root.ch[k]];
+        rest *= c.identity ? c.n : c.s;
+      }
+      os.back() = rest;
+      TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
+    }
+    ws.top = mark;
+  } else {
+    // STTNN: D2 = M^T Y_c1 (nR x s'_c1): R children and the root
+    View H{D2, mode_axes(P.Rlo, P.Rhi), P.wLpad};
+    H.ax.push_back(Ax{AX_SK, P.ychild, P.wYL, 0});
+    const TNode& c1 = P.nodes[P.ychild];
+    for (size_t k = 0; k < P.Rch.size(); ++k) {
+      const TNode& c = P.nodes[P.Rch[k]];
+      if (c.rsub == 0) continue;
+      const int64_t mark = ws.top;
+      // contract the c1 sketch axis with XT_c1: creates the column axis
+      View cur;
+      Ax jax{AX_J, -1, c.rsub, 0};
+      TTNN_TRY(contract_view(C, H, (int)H.ax.size() - 1, C.facw + c1.xt_off * eb, P.rmax, 1, -1,
+                             &jax, &cur));
+      for (size_t k2 = 0; k2 < P.Rch.size(); ++k2) {
+        if (k2 == k) continue;
+        const TNode& sib = P.nodes[P.Rch[k2]];
+        View nx;
+        if (k2 < k && !sib.identity) {
+          TTNN_TRY(e_group(C, cur, sib.user, &nx));
+          cur = nx;
+        } else {
+          for (int mm = sib.hi - 1; mm >= sib.lo; --mm) {
+            TTNN_TRY(x_mode(C, cur, mm, &nx));
+            cur = nx;
+          }
+        }
+      }
+      TTNN_TRY(walk(C, acc, c.user, cur, lambda));
+      ws.top = mark;
+    }
+    const int64_t mark = ws.top;
+    View cur = H;
+    for (int k = (int)P.Rch.size() - 1; k >= 0; --k) {
+      const TNode& c = P.nodes[P.Rch[k]];
+      if (c.identity) continue;
+      View nx;
+      TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+      cur = nx;
+    }
+    std::vector<int64_t> os = psi_strides(C, cur, root, false);
+    int64_t rest = 1;
+    for (size_t k = 1; k < root.ch.size(); ++k) {
+      const TNode& c = P.nodes[root.ch[k]];
+      rest *= c.identity ? c.n : c.s;
+    }
+    os.back() = rest;
+    TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
+    ws.top = mark;
+  }
+  cudaEvent_t ev2 = dry ? nullptr : prof_event(P, st);
+  prof_push(P, 1, ev1, ev2);
+  if (peak) *peak = ws.peak;
+  if (!ws.ok()) {
+    set_error("internal: workspace overflow (%lld > %lld)", (long long)ws.peak, (long long)ws.cap);
+    return TTNN_ENOMEM;
+  }
+  return TTNN_OK;
+}
+
+cudaEvent_t prof_event(ttnn_plan_s& P, cudaStream_t st) {
+  if (!P.profile) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, st);
+  return e;
+}
+
+void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b) {
+  if (!a || !b) return;
+  auto& v = P.prof[phase];
+  if (v.size() >= 4096) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return;
+  }
+  v.emplace_back(a, b);
+}
+
+// ---------------------------------------------------------------------------
+// recovery: QR / eps-pseudo-inverse, then core assembly in binary64
+// ---------------------------------------------------------------------------
+ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
+                        int64_t* peak) {
+  Ws ws(P.ws, P.ws_bytes, dry);
+  cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
+  const int seb = P.walk_f64 ? 8 : 4;
+  const ElemType set = P.walk_f64 ? ET_F64 : ET_F32;
+  std::vector<QrJob> jobs;
+  std::vector<int> job_node;
+  std::vector<double*> Qp(P.nodes.size(), nullptr), Rp(P.nodes.size(), nullptr);
+  for (int v : P.lex) {
+    TNode& nd = P.nodes[v];
+    if (!nd.sketched()) continue;
+    double* q = (double*)ws.alloc((int64_t)nd.s * nd.r * 8);
+    double* rp = (double*)ws.alloc((int64_t)nd.r * nd.r * 8);
+    Qp[v] = q;
+    Rp[v] = rp;
+    jobs.push_back(QrJob{(const char*)acc + nd.om_off * seb, q, rp, nd.s, nd.r});
+    job_node.push_back(v);
+  }
+  if (!dry && !jobs.empty()) {
+    TTNN_TRY_CUDA(cudaMemcpyAsync(P.jobs_dev, jobs.data(), jobs.size() * sizeof(QrJob),
+                                  cudaMemcpyHostToDevice, st));
+    TTNN_TRY(launch_qr_pinv(P.jobs_dev, (int)jobs.size(), P.walk_f64, P.eps_factor, P.u,
+                            P.kept_dev, st));
+  }
+  // a generic f64 contraction on a contiguous tensor with dims `dims`:
+  // contract axis k with W (i, b) = W[i*wsI + b*wsB] into a new axis of nb.
+  auto mp = [&](const void* in, bool in_state, const std::vector<int64_t>& dims, int k,
+                const double* W, int64_t wsI, int64_t wsB, int64_t nb, double* out,
+                int64_t osP, int64_t osB, int64_t osQ) -> ttnn_status {
+    Contract c;
+    c.P = 1;
+    for (int a = 0; a < k; ++a) c.P *= dims[a];
+    c.NI = dims[k];
+    c.Q = 1;
+    for (size_t a = k + 1; a < dims.size(); ++a) c.Q *= dims[a];
+    c.isP = c.NI * c.Q;
+    c.isI = c.Q;
+    c.isQ = 1;
+    c.NB = nb;
+    c.w = W;
+    c.wsI = wsI;
+    c.wsB = wsB;
+    c.in = in;
+    c.out = out;
+    c.osP = osP;
+    c.osB = osB;
+    c.osQ = osQ;
+    c.osJ = 0;
+    const int64_t pe = contract_partial_elems(c);
+    const int64_t mark = ws.top;
+    char* part = pe ? ws.alloc(pe * 8) : nullptr;
+    if (!dry)
+      TTNN_TRY(launch_contract(c, in_state ? set : ET_F64, ET_F64, ET_F64, part, pe, st));
+    ws.top = mark;
+    return TTNN_OK;
+  };
+  for (int v : P.lex) {
+    TNode& nd = P.nodes[v];
+    double* core = cores + nd.core_off;
+    const int64_t mark = ws.top;
+    if (v != P.root && nd.identity) {
+      if (!dry) TTNN_TRY(launch_eye(core, nd.n, st));
+      continue;
+    }
+    if (v != P.root && nd.leaf) {
+      // core[j][i] = sum_k Psi[i][k] Rp[k][j]
+      TTNN_TRY(mp((const char*)acc + nd.ps_off * seb, true, {nd.n, (int64_t)nd.r}, 1, Rp[v], nd.r,
+                  1, nd.r, core, 1, nd.n, 0));
+      continue;
+    }
+    // transfer tensor or root: Q_c^T on each non-identity child axis, then
+    // R_eps^+ on the column axis and the permutation (r_v, r_c1, ...)
+    std::vector<int64_t> dims = nd.ps_shape;
+    const void* cur = (const char*)acc + nd.ps_off * seb;
+    bool in_state = true;
+    const int m = (int)nd.ch.size();
+    for (int k = 0; k < m; ++k) {
+      const TNode& c = P.nodes[nd.ch[k]];
+      if (c.identity) continue;
+      std::vector<int64_t> od = dims;
+      od[k] = c.r;
+      int64_t tot = 1;
+      for (auto x : od) tot *= x;
+      double* o = (double*)ws.alloc(tot * 8);
+      int64_t Q = 1;
+      for (size_t a = k + 1; a < od.size(); ++a) Q *= od[a];
+      TTNN_TRY(mp(cur, in_state, dims, k, Qp[c.user], c.r, 1, c.r, o, (int64_t)c.r * Q, Q, 1));
+      cur = o;
+      in_state = false;
+      dims = od;
+    }
+    if (v == P.root) {
+      int64_t tot = 1;
+      for (auto x : dims) tot *= x;
+      // copy (identity W via a 1-long contraction)
+      Contract c;
+      c.P = tot;
+      c.NI = 1;
+      c.isP = 1;
+      c.in = cur;
+      c.out = core;
+      c.osP = 1;
+      if (!dry) TTNN_TRY(launch_contract(c, in_state ? set : ET_F64, ET_F64, ET_F64, nullptr, 0, st));
+    } else {
+      int64_t rest = 1;
+      for (int k = 0; k < m; ++k) rest *= dims[k];
+      // out[b][p] = sum_k cur[p][k] Rp[k][b]
+      TTNN_TRY(mp(cur, in_state, {rest, (int64_t)nd.r}, 1, Rp[v], nd.r, 1, nd.r, core, 1, rest, 0));
+    }
+    ws.top = mark;
+  }
+  if (peak) *peak = ws.peak;
+  if (!ws.ok()) {
+    set_error("internal: workspace overflow in recovery");
+    return TTNN_ENOMEM;
+  }
+  if (!dry) prof_push(P, 2, ev0, prof_event(P, st));
+  if (!dry && !jobs.empty()) {
+    std::vector<int> kept(jobs.size());
+    TTNN_TRY_CUDA(cudaMemcpyAsync(kept.data(), P.kept_dev, kept.size() * sizeof(int),
+                                  cudaMemcpyDeviceToHost, st));
+    TTNN_TRY_CUDA(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < jobs.size(); ++k) P.nodes[job_node[k]].kept = kept[k];
+  }
+  return TTNN_OK;
+}
+
+}  // namespace ttnn

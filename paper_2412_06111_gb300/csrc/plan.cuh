@@ -1,0 +1,106 @@
+// Host-side plan and state structures.
+#pragma once
+
+#include <array>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct TNode {
+  int user = -1, lex = -1, level = 0, parent = -1, pos = 0;
+  int lo = 0, hi = 0;
+  bool leaf = false, identity = false;
+  int r = 0, p = 0, s = 0;
+  int64_t n = 1;
+  int rsub = 0;                 // max r over sketched nodes of the subtree
+  std::vector<int> ch;          // children (user indices), ordered by first mode
+  std::vector<int> reuse;       // STTNN reuse set S_v (user indices), by first mode
+  int64_t om_off = -1, om_el = 0, ps_off = -1, ps_el = 0;
+  std::vector<int64_t> ps_shape;
+  int64_t core_off = 0, core_el = 0;
+  std::vector<int64_t> core_shape;
+  int64_t xt_off = -1;          // STTNN XT_v factor offset (elements) in the factor arrays
+  int kept = -1;
+  bool sketched() const { return parent >= 0 && !identity; }
+};
+
+struct ttnn_plan_s {
+  int d = 0;
+  std::vector<int64_t> dims;
+  int64_t N = 1;
+  std::vector<TNode> nodes;
+  int root = -1;
+  std::vector<int> lex;         // lex position -> user index
+  int variant = 0, dtype = 1;
+  double eps_factor = 10.0, u = 2.220446049250313e-16;
+  uint64_t seed = 0;
+  uint32_t flags = 0;
+  int rmax = 1, smax = 1;
+  // first-level split: L = root children [0, a), R = [a, m)
+  int a = 1;
+  int yside = 0;                // 0: root's Y applied on the R side (in D1), 1: on the L side (D2)
+  int ychild = -1;              // the single root child whose Y is a pass-side block
+  std::vector<int> Lch, Rch;
+  int Llo = 0, Lhi = 0, Rlo = 0, Rhi = 0;
+  int rXL = 0, rXR = 0;         // X-part widths of the side blocks B_R / B_L
+  int wYR = 0, wYL = 0;         // Y-part widths
+  int yR_ident = 0, yL_ident = 0;
+  int wR = 0, wL = 0, wRpad = 0, wLpad = 0;
+  // number formats
+  int walk_f64 = 0;             // tree walk / accumulators in binary64
+  int pass_store = 1;           // storage of the tensor and side blocks: 0 f64 1 f32 2 bf16 3 e4m3
+  int round_fmt = 1;            // DRM rounding (RoundFmt)
+  // device memory
+  double* fac64 = nullptr;      // X_mu, Y_mu, XT_v (binary64)
+  void* facw = nullptr;         // the same in the walk type
+  std::vector<int64_t> x_off, y_off;
+  int64_t fac_elems = 0;
+  void* sideR = nullptr;        // cached full-size side blocks (pass storage)
+  void* sideL = nullptr;
+  void* yW = nullptr;           // walk-type copy of the pass Y block (full box)
+  char* ws = nullptr;
+  int64_t ws_bytes = 0;
+  ttnn::QrJob* jobs_dev = nullptr;
+  int* kept_dev = nullptr;
+  int n_sketched = 0;
+  int64_t state_elems = 0;
+  int64_t core_elems = 0;
+  int tc_ok = 0;                // tensor-core pass usable for this plan
+  // profiling: event pairs per phase (0 pass, 1 walk, 2 recovery)
+  int profile = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[3];
+};
+
+struct ttnn_state_s {
+  ttnn_plan_s* plan = nullptr;
+  void* acc = nullptr;
+  int64_t elems = 0;
+};
+
+namespace ttnn {
+
+struct Box {
+  std::vector<int64_t> off, ext;
+  bool full = true;
+};
+
+ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const int64_t* dims,
+                       const int32_t* ranks, const int32_t* oversample, uint64_t seed,
+                       const ttnn_opts* opts);
+
+// Runs (or, with dry = true, sizes) one dense update.  Returns the peak
+// workspace bytes through *peak when dry.
+ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
+                             const float* tile_scale, double lambda, cudaStream_t st, bool dry,
+                             int64_t* peak);
+ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
+                      cudaStream_t st);
+ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st);
+// records an event on `st` if profiling is on (returns nullptr otherwise)
+cudaEvent_t prof_event(ttnn_plan_s& P, cudaStream_t st);
+void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b);
+ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
+                        int64_t* peak);
+
+}  // namespace ttnn

@@ -1,0 +1,195 @@
+"""GPU path against the FP64 oracle, element by element, on seeded inputs
+(ragged sizes, several tree shapes, both variants, every number format the
+SIMT path runs).  All calls go through the C ABI (libttnn.so)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import philox
+from oracle import sttnn as OS
+from oracle import ttnn as O
+from oracle.tree import Tree
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from paper_2412_06111_gb300 import api  # noqa: E402
+
+from _lib_util import Run, rel  # noqa: E402
+
+FMT = {api.F64: "f64", api.F32: "f32", api.BF16: "bf16", api.E4M3: "e4m3"}
+
+CASES = {
+    "binary4": (W.balanced_binary(4), [7, 5, 6, 4], 3, 2),
+    "toy6": (W.toy_tree(), [3, 4, 3, 5, 4, 3], 2, 2),
+    "tt5": (W.tensor_train(5), [4, 3, 5, 3, 4], 2, 1),
+    "tucker4": (W.tucker(4), [5, 4, 6, 3], 2, 2),
+    "binary5": (W.balanced_binary(5), [6, 7, 5, 8, 6], 4, 2),
+}
+
+
+def _otree(tr, dims, r, p):
+    n = len(tr[0])
+    return Tree(tr[0], tr[1], dims, [r] * n, [p] * n, tr[2])
+
+
+def _dev(T, dtype):
+    t = torch.from_numpy(np.ascontiguousarray(T)).cuda()
+    if dtype == api.F64:
+        return t.double(), T
+    if dtype == api.F32:
+        t = t.float()
+    else:
+        t = t.float().to(torch.bfloat16)
+    return t, t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2 ** 40 + 3])
+@pytest.mark.parametrize("fmt", [0, 1, 2, 3])
+def test_philox_generator_bitwise(seed, fmt):
+    for kind, ident, rows, cols in [(1, 0, 37, 24), (2, 5, 129, 48), (3, 77, 8, 5), (1, 3, 1000, 1)]:
+        dst = torch.empty(rows * cols, dtype=torch.float64, device="cuda")
+        api.ttnn_philox_gaussian(seed, kind, ident, rows, cols, fmt, dst)
+        got = dst.cpu().numpy().reshape(rows, cols)
+        want = philox.gaussian_matrix(seed, kind, ident, rows, cols)
+        from oracle.quant import round_to
+        want = round_to(want, FMT[fmt])
+        assert np.array_equal(got, want), (seed, fmt, kind, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize("dtype", [api.F64, api.F32, api.BF16])
+def test_plan_factors_bitwise(dtype):
+    tr, dims, r, p = CASES["toy6"]
+    run = Run(tr, dims, [r] * len(tr[0]), [p] * len(tr[0]), 1234, dtype=dtype)
+    try:
+        t = _otree(tr, dims, r, p)
+        drm = O.Drm(t, 1234, FMT[dtype])
+        for mu in range(len(dims)):
+            for which, want in ((1, drm.X[mu]), (2, drm.Y[mu])):
+                rows, cols = api.ttnn_plan_factor(run.plan, which, mu)
+                dst = torch.empty(rows * cols, dtype=torch.float64, device="cuda")
+                api.ttnn_plan_factor(run.plan, which, mu, dst)
+                assert np.array_equal(dst.cpu().numpy().reshape(rows, cols), want)
+        for v in t.sketched():
+            lex = t.node(v).lex
+            rows, cols = api.ttnn_plan_factor(run.plan, 3, lex)
+            dst = torch.empty(rows * cols, dtype=torch.float64, device="cuda")
+            api.ttnn_plan_factor(run.plan, 3, lex, dst)
+            assert np.array_equal(dst.cpu().numpy().reshape(rows, cols), drm.XT[v])
+    finally:
+        run.close()
+
+
+def _compare_sketches(run, t, T, drm, variant, tol):
+    Om, Ps, Pr = (O.sketch_ttnn if variant == api.VARIANT_TTNN else OS.sketch_sttnn)(T, t, drm)
+    gOm, gPs, gPr = run.sketches()
+    worst = 0.0
+    for v in t.sketched():
+        worst = max(worst, rel(gOm[v], Om[v]), rel(gPs[v], Ps[v]))
+    worst = max(worst, rel(gPr, Pr))
+    assert worst <= tol, worst
+    return worst
+
+
+@pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("dtype,tol", [(api.F64, 1e-12), (api.F32, 1e-5), (api.BF16, 1e-5)])
+def test_sketches_match_oracle(case, variant, dtype, tol):
+    tr, dims, r, p = CASES[case]
+    n = len(tr[0])
+    T = W.gaussian(dims, 17)
+    dev, Tq = _dev(T, dtype)
+    run = Run(tr, dims, [r] * n, [p] * n, 99, dtype=dtype, variant=variant)
+    try:
+        api.ttnn_update_dense(run.state, dev)
+        t = _otree(tr, dims, r, p)
+        drm = O.Drm(t, 99, FMT[dtype], "sttnn" if variant else "ttnn")
+        _compare_sketches(run, t, Tq, drm, variant, tol)
+    finally:
+        run.close()
+
+
+@pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_recovery_matches_oracle_f64(case, variant):
+    tr, dims, r, p = CASES[case]
+    n = len(tr[0])
+    T, _ = W.exact_ttn(tr, dims, [max(1, r - 1)] * n, 5, noise=1e-3)
+    run = Run(tr, dims, [r] * n, [p] * n, 7, dtype=api.F64, variant=variant)
+    try:
+        api.ttnn_update_dense(run.state, torch.from_numpy(T).cuda())
+        cores = run.recover()
+        t = _otree(tr, dims, r, p)
+        drm = O.Drm(t, 7, "f64", "sttnn" if variant else "ttnn")
+        sk = (O.sketch_ttnn if variant == 0 else OS.sketch_sttnn)(T, t, drm)
+        ocores, kept = O.recover(t, *sk)
+        rg, ro = O.reconstruct(t, cores), O.reconstruct(t, ocores)
+        assert rel(rg, ro) <= 1e-10
+        for v in t.sketched():
+            assert run.nodes[v]["kept_rank"] == kept[v]
+    finally:
+        run.close()
+
+
+@pytest.mark.parametrize("noise,tol", [(0.0, 1e-12), (1e-8, 1e-6)])
+def test_exact_recovery_order4_24(noise, tol):
+    """Order-4 24^4 exact TTN, ranks 5, l = 5, FP64, one update."""
+    tr = W.balanced_binary(4)
+    dims = [24] * 4
+    T, _ = W.exact_ttn(tr, dims, [5] * 7, 1000, noise=noise)
+    run = Run(tr, dims, [5] * 7, [5] * 7, 2000, dtype=api.F64)
+    try:
+        api.ttnn_update_dense(run.state, torch.from_numpy(T).cuda())
+        t = _otree(tr, dims, 5, 5)
+        R = O.reconstruct(t, run.recover())
+        assert rel(R, T) <= tol
+    finally:
+        run.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [(api.F64, 1e-12), (api.F32, 1e-5)])
+def test_box_updates_are_linear(dtype, tol):
+    """Sketch of a sum of sub-block updates = sum of their sketches (Sec. 4
+    streaming) = sketch of the whole tensor."""
+    tr, dims, r, p = CASES["toy6"]
+    n = len(tr[0])
+    rng = np.random.default_rng(3)
+    T = np.zeros(dims)
+    run = Run(tr, dims, [r] * n, [p] * n, 5, dtype=dtype)
+    try:
+        for k in range(6):
+            off = [int(rng.integers(0, d)) for d in dims]
+            ext = [int(rng.integers(1, d - o + 1)) for d, o in zip(dims, off)]
+            data = rng.standard_normal(ext)
+            lam = float(rng.uniform(-2, 2))
+            dev, dq = _dev(data, dtype)
+            api.ttnn_update_dense(run.state, dev, offset=off, extent=ext, lam=lam)
+            T[tuple(slice(o, o + e) for o, e in zip(off, ext))] += lam * dq
+        t = _otree(tr, dims, r, p)
+        drm = O.Drm(t, 5, FMT[dtype])
+        _compare_sketches(run, t, T, drm, 0, tol)
+    finally:
+        run.close()
+
+
+def test_state_checkpoint_resume_and_axpy():
+    tr, dims, r, p = CASES["binary4"]
+    n = len(tr[0])
+    T1, T2 = W.gaussian(dims, 1), W.gaussian(dims, 2)
+    a = Run(tr, dims, [r] * n, [p] * n, 9, dtype=api.F64)
+    b = Run(tr, dims, [r] * n, [p] * n, 9, dtype=api.F64)
+    try:
+        api.ttnn_update_dense(a.state, torch.from_numpy(T1).cuda())
+        snap = a.state_host()
+        api.ttnn_update_dense(a.state, torch.from_numpy(T2).cuda())
+        full = a.state_host()
+        api.ttnn_state_load(b.state, snap.copy())
+        api.ttnn_update_dense(b.state, torch.from_numpy(T2).cuda())
+        assert np.array_equal(b.state_host(), full)          # bitwise resume
+        api.ttnn_state_zero(b.state)
+        api.ttnn_update_dense(b.state, torch.from_numpy(T2).cuda(), lam=-1.0)
+        api.ttnn_state_axpy(a.state, b.state, 1.0)           # a = S(T1) + S(T2) - S(T2)
+        assert np.allclose(a.state_host(), snap, rtol=0, atol=1e-12 * np.abs(snap).max())
+    finally:
+        a.close()
+        b.close()

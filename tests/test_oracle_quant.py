@@ -11,11 +11,15 @@ def test_f32_is_ieee_cast():
 
 
 def test_bf16_hand_values():
+    import torch
+    assert float.fromhex("0x1.fep127") == torch.finfo(torch.bfloat16).max
     u = 2.0 ** -8
     x = np.array([1 + u, 1 + 3 * u, 1 + 2 * u, -(1 + 1.5 * u), 2.0 ** -133, 2.0 ** -134,
-                  3 * 2.0 ** -134, 2.0 ** 128, float.fromhex("0x1.fcp127"), 0.0, -0.0])
+                  3 * 2.0 ** -134, 2.0 ** 128, float.fromhex("0x1.fep127"),
+                  float.fromhex("0x1.ffp127"), float.fromhex("0x1.fefffp127"), 0.0, -0.0])
     want = np.array([1.0, 1 + 4 * u, 1 + 2 * u, -(1 + 2 * u), 2.0 ** -133, 0.0,
-                     2.0 ** -132, np.inf, float.fromhex("0x1.fcp127"), 0.0, -0.0])
+                     2.0 ** -132, np.inf, float.fromhex("0x1.fep127"), np.inf,
+                     float.fromhex("0x1.fep127"), 0.0, -0.0])
     got = round_to(x, "bf16")
     assert np.array_equal(got, want)
     assert np.signbit(got[-1])
