@@ -112,8 +112,13 @@ def _max_over_ranks(x, ws):
     return float(t.item())
 
 
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
 def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
     """Times `steps` whole-path steps on device-resident data.  Returns a dict."""
+    log("form dtype", dtype, "variant", variant)
     tr = W.balanced_binary(D)
     n = len(tr[0])
     dims = [NMODE] * D
@@ -123,11 +128,13 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
     ce = api.ttnn_plan_sizes(plan)[2]
     cores = torch.zeros(ce, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    log("plan and state ready")
     for _ in range(warmup):
         api.ttnn_state_zero(state)
         api.ttnn_update_dense(state, data)
         api.ttnn_recover(state, cores)
     torch.cuda.synchronize()
+    log("warm-up done")
     api.ttnn_profile(plan, True)
     for ph in range(3):
         api.ttnn_profile_read(plan, ph)
@@ -230,13 +237,16 @@ def cpu_oracle_sample(max_seconds=25.0):
 
 
 def main():
+    global NMODE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nmode", type=int, default=NMODE, help="mode size (64 = the stated workload)")
     args = ap.parse_args()
+    NMODE = args.nmode
     warmup = max(3, args.warmup)
 
     if args.impl == "reference":
@@ -270,6 +280,7 @@ def main():
     N = NMODE ** D
     a32 = W.inv_sum_torch(D, NMODE, "cuda", torch.float32)
     a16 = a32.to(torch.bfloat16)
+    log("tensor ready", N)
     with Clocks(dev) as clk:
         bf = run_form(api, W, api.BF16, api.VARIANT_TTNN, args.steps, warmup, ws, torch, a16)
     f32 = run_form(api, W, api.F32, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch, a32)

@@ -779,8 +779,9 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       ws.top = mark;
     }
   }
+  // each interval owns its two events (an event is destroyed with its interval)
+  prof_push(P, 0, ev0, dry ? nullptr : prof_event(P, st));
   cudaEvent_t ev1 = dry ? nullptr : prof_event(P, st);
-  prof_push(P, 0, ev0, ev1);
   // views of the pass products
   auto mode_axes = [&](int lo, int hi) {
     std::vector<Ax> ax;
@@ -939,7 +940,11 @@ cudaEvent_t prof_event(ttnn_plan_s& P, cudaStream_t st) {
 }
 
 void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b) {
-  if (!a || !b) return;
+  if (!a || !b) {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return;
+  }
   auto& v = P.prof[phase];
   if (v.size() >= 4096) {
     cudaEventDestroy(a);

@@ -193,3 +193,24 @@ def test_state_checkpoint_resume_and_axpy():
     finally:
         a.close()
         b.close()
+
+
+def test_profiling_intervals_and_launch_counter():
+    tr, dims, r, p = CASES["binary4"]
+    n = len(tr[0])
+    run = Run(tr, dims, [r] * n, [p] * n, 3, dtype=api.F32)
+    try:
+        T = torch.from_numpy(W.gaussian(dims, 4)).float().cuda()
+        api.ttnn_profile(run.plan, True)
+        l0 = api.ttnn_kernel_launches()
+        for _ in range(2):
+            api.ttnn_update_dense(run.state, T)
+            run.recover()
+        assert api.ttnn_kernel_launches() > l0
+        for ph in range(3):
+            ms, cnt = api.ttnn_profile_read(run.plan, ph)
+            assert cnt == 2 and ms > 0
+        assert api.ttnn_profile_read(run.plan, 0) == (0.0, 0)
+        api.ttnn_profile(run.plan, False)
+    finally:
+        run.close()
