@@ -155,12 +155,13 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
     _barrier(ws)
     ms = e0.elapsed_time(e1) / steps
     launches = api.ttnn_kernel_launches() - l0
+    passes = api.ttnn_plan_pass_counts(plan)
     api.ttnn_profile(plan, False)
     prof = [api.ttnn_profile_read(plan, ph) for ph in range(3)]
     api.ttnn_state_destroy(state)
     api.ttnn_plan_destroy(plan)
     lat.sort()
-    return {"ms_per_step": ms, "launches": launches,
+    return {"ms_per_step": ms, "launches": launches, "tc_passes": passes[0], "simt_passes": passes[1],
             "pass_ms": prof[0][0] / max(prof[0][1], 1), "walk_ms": prof[1][0] / max(prof[1][1], 1),
             "recover_ms": prof[2][0] / max(prof[2][1], 1),
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
@@ -308,6 +309,7 @@ def main():
         "clocks": clk.summary(),
         "latency_ms": {"p50": bf["p50_ms"], "p99": bf["p99_ms"]},
         "phases_ms": {"pass": bf["pass_ms"], "walk": bf["walk_ms"], "recover": bf["recover_ms"]},
+        "pass_path": {"tensor_core": bf["tc_passes"], "simt": bf["simt_passes"]},
         "fp32_plain": {"value": N * 4 / (f32["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",
                        "ms_per_step": f32["ms_per_step"], "pass_ms": f32["pass_ms"]},
         "sttnn_bf16": {"value": N * 2 / (st["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",

@@ -244,6 +244,10 @@ ttnn_status ttnn_fp8_quantize(ttnn_plan_t plan, const float* src, const int64_t*
  * accumulation, 2 = recovery.  At most 4096 intervals are kept per phase. */
 ttnn_status ttnn_profile(ttnn_plan_t plan, int32_t enable);
 ttnn_status ttnn_profile_read(ttnn_plan_t plan, int32_t phase, double* total_ms, int32_t* count);
+/* Counts of first-level passes this plan has run on the tensor cores
+ * (tcgen05) and on the SIMT path (FP64 / FP32 plans, or shapes the
+ * tensor-core pass does not take). */
+ttnn_status ttnn_plan_pass_counts(ttnn_plan_t plan, int64_t* tensor_core, int64_t* simt);
 /* Number of device kernels this library has launched in this process. */
 ttnn_status ttnn_kernel_launches(int64_t* count);
 

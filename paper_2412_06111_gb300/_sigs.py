@@ -53,6 +53,7 @@ SIGS = {
     "ttnn_profile": (c_i32, [c_vp, c_i32]),
     "ttnn_profile_read": (c_i32, [c_vp, c_i32, C.POINTER(c_dbl), C.POINTER(c_i32)]),
     "ttnn_kernel_launches": (c_i32, [C.POINTER(c_i64)]),
+    "ttnn_plan_pass_counts": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
 }
 
 

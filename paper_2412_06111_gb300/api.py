@@ -203,3 +203,10 @@ def ttnn_kernel_launches():
     n = C.c_int64()
     _check(_lib().ttnn_kernel_launches(C.byref(n)))
     return n.value
+
+
+def ttnn_plan_pass_counts(plan):
+    """(tensor-core passes, SIMT passes) run by this plan."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(_lib().ttnn_plan_pass_counts(plan, C.byref(a), C.byref(b)))
+    return a.value, b.value

@@ -49,6 +49,7 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->ws);
   cudaFree(P->jobs_dev);
   cudaFree(P->kept_dev);
+  cudaFree(P->err_dev);
   delete P;
 }
 
@@ -158,6 +159,7 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
       if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
     }
   }
+  P.tc_ok = (P.dtype == TTNN_BF16);
   // workspace: the larger of a whole-tensor update and a recovery
   int64_t need_u = 0, need_r = 0;
   if ((s = run_dense_update(P, nullptr, nullptr, fb, nullptr, 1.0, st, true, &need_u))) return fail(s);
@@ -166,6 +168,8 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   if ((s = dev_alloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
   if ((s = dev_alloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
   if ((s = dev_alloc((void**)&P.kept_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
+  if ((s = dev_alloc((void**)&P.err_dev, sizeof(int))) != TTNN_OK) return fail(s);
+  if ((s = launch_fill_zero(P.err_dev, sizeof(int), st)) != TTNN_OK) return fail(s);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_error("plan creation: %s", cudaGetErrorString(e));
@@ -414,6 +418,13 @@ ttnn_status ttnn_profile_read(ttnn_plan_t P, int32_t phase, double* total_ms, in
   if (total_ms) *total_ms = tot;
   if (count) *count = cnt;
   return s;
+}
+
+ttnn_status ttnn_plan_pass_counts(ttnn_plan_t P, int64_t* tensor_core, int64_t* simt) {
+  TTNN_CHECK_ARG(P, "null plan");
+  if (tensor_core) *tensor_core = P->n_tc_pass;
+  if (simt) *simt = P->n_simt_pass;
+  return TTNN_OK;
 }
 
 ttnn_status ttnn_kernel_launches(int64_t* count) {

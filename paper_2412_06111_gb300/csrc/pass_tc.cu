@@ -1,22 +1,553 @@
-// Tensor-core (tcgen05) first-level pass: placeholder until the kernel lands.
+// First-level pass on the 5th-generation tensor cores (sm_103a, tcgen05).
+//
+// The dense block is viewed as M (nL x nR, row-major: rows = the root's
+// left-group modes, columns = the right-group modes).  One pass over M forms
+// both products of the sketch phase (Sec. 4) that touch the tensor:
+//   D1 = M  B_R^T   (nL x wR)  contraction over the right modes
+//   D2 = M^T B_L^T  (nR x wL)  contraction over the left modes
+// with B_R / B_L the Khatri-Rao DRM blocks stored [w][n] in bf16.
+//
+// Each 128 x 128 tile of M is staged into shared memory once by TMA (128-byte
+// swizzle) and read by two tcgen05.mma streams: as a K-major A operand for D1
+// (M = 128 rows) and as an MN-major A operand for D2 (M = 128 columns).  D1
+// of the current row block and D2 of the CTA's column chunk accumulate in
+// TMEM in FP32.  Persistent CTAs, one per SM: CTA (chunk c, group g) owns the
+// columns [c*CW, (c+1)*CW) and a contiguous range of row blocks; D1 partials
+// per chunk and D2 partials per group are summed by two small reductions.
+//
+// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM owner + MMA
+// issuer, warps 2-5 epilogue (TMEM lane quarter = warp % 4).  Every mbarrier
+// wait is bounded by a %globaltimer deadline; on expiry the kernel records
+// an error flag, drains its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "plan.cuh"
 
 namespace ttnn {
 
+namespace tc {
+
+constexpr int kThreads = 192;
+constexpr int kTileM = 128;           // rows of M per tile (MMA M for D1)
+constexpr int kTileN = 128;           // columns of M per tile (MMA M for D2)
+constexpr int kMaxTiles = 8;          // column tiles per chunk
+constexpr int kSmemBudget = 232448 - 2048;   // 227 KB opt-in minus static shared memory
+constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s per wait
+
+struct Params {
+  int64_t nL, nR;
+  int C, G, nb, tiles, stages;
+  int wRpad, wLpad;
+  float* D1p;      // [C][nb*128][wRpad]
+  float* D2p;      // [G][C*tiles*128][wLpad]
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (gtimer() - t0 > kTimeoutNs) return false;
+  }
+}
+// Bounded wait that ignores the abort flag (used to drain own work).
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kTimeoutNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                       uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+// tcgen05 shared-memory descriptor: start, leading / stride byte offsets,
+// fixed version bits 46-48 = 0b001, 128-byte swizzle (mode 2, bits 61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D f32, A/B bf16, A K- or MN-major,
+// B K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBR,
+                const __grid_constant__ CUtensorMap mapBL, const Params p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[8], bar_empty[8];
+  __shared__ __align__(8) uint64_t bar_blfull[2], bar_blempty[2], bar_d1full[2], bar_d1empty[2];
+  __shared__ __align__(8) uint64_t bar_d2full;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = p.stages;
+  const uint32_t a_bytes = kTileM * 128 * 2;                   // two 64-column boxes
+  const uint32_t br_bytes = (uint32_t)p.wRpad * 128 * 2;
+  const uint32_t bl_bytes = (uint32_t)p.wLpad * 128 * 2;
+  const uint32_t stage_bytes = a_bytes + br_bytes;
+  const uint32_t base = smem_u32(smem);
+  const uint32_t bl_base = base + S * stage_bytes;
+
+  const int c = blockIdx.x % p.C, g = blockIdx.x / p.C;
+  const int b0 = (int)((int64_t)g * p.nb / p.G), b1 = (int)((int64_t)(g + 1) * p.nb / p.G);
+  const int nu = b1 - b0;
+  const int64_t cw = (int64_t)p.tiles * kTileN;
+  const int64_t col0 = c * cw;
+  const int64_t left_tiles = (p.nR - col0 + kTileN - 1) / kTileN;
+  const int nt = left_tiles < p.tiles ? (int)left_tiles : p.tiles;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_u32(&bar_blfull[k]), 1);
+      mbar_init(smem_u32(&bar_blempty[k]), 1);
+      mbar_init(smem_u32(&bar_d1full[k]), 1);
+      mbar_init(smem_u32(&bar_d1empty[k]), 4);
+    }
+    mbar_init(smem_u32(&bar_d2full), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(512u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t d1_col = 0, d2_col = 2 * p.wRpad;
+
+  if (warp == 0) {
+    if (lane == 0 && nu > 0) {
+      // ---------------- TMA producer ----------------
+      uint64_t pol_stream, pol_keep;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_stream));
+      asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_keep));
+      int stage = 0;
+      uint32_t ph = 0;
+      int last_ph[8];
+      for (int s = 0; s < 8; ++s) last_ph[s] = -1;
+      int bl_last[2] = {-1, -1};
+      bool ok = true;
+      for (int u = 0; u < nu && ok; ++u) {
+        const int b = b0 + u, ub = u & 1;
+        const int row = b * kTileM;
+        ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag);
+        if (!ok) break;
+        const uint32_t blb = bl_base + ub * bl_bytes;
+        mbar_expect_tx(smem_u32(&bar_blfull[ub]), bl_bytes);
+        tma_2d(blb, &mapBL, row, 0, smem_u32(&bar_blfull[ub]), pol_keep);
+        tma_2d(blb + bl_bytes / 2, &mapBL, row + 64, 0, smem_u32(&bar_blfull[ub]), pol_keep);
+        bl_last[ub] = (u >> 1) & 1;
+        for (int t = 0; t < nt; ++t) {
+          ok = mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1, &abort_flag);
+          if (!ok) break;
+          const uint32_t sb = base + stage * stage_bytes;
+          const int col = (int)(col0 + t * kTileN);
+          mbar_expect_tx(smem_u32(&bar_full[stage]), stage_bytes);
+          tma_2d(sb, &mapA, col, row, smem_u32(&bar_full[stage]), pol_stream);
+          tma_2d(sb + a_bytes / 2, &mapA, col + 64, row, smem_u32(&bar_full[stage]), pol_stream);
+          tma_2d(sb + a_bytes, &mapBR, col, 0, smem_u32(&bar_full[stage]), pol_keep);
+          tma_2d(sb + a_bytes + br_bytes / 2, &mapBR, col + 64, 0, smem_u32(&bar_full[stage]),
+                 pol_keep);
+          last_ph[stage] = (int)ph;
+          if (++stage == S) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(p.err, 1);
+      }
+      // the copies this thread issued must land before the CTA may exit
+      for (int s = 0; s < S; ++s)
+        if (last_ph[s] >= 0 && !mbar_drain(smem_u32(&bar_full[s]), (uint32_t)last_ph[s]))
+          atomicOr(p.err, 2);
+      for (int k = 0; k < 2; ++k)
+        if (bl_last[k] >= 0 && !mbar_drain(smem_u32(&bar_blfull[k]), (uint32_t)bl_last[k]))
+          atomicOr(p.err, 2);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nu > 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t id1 = idesc_bf16(kTileM, p.wRpad, false);
+      const uint32_t id2 = idesc_bf16(kTileN, p.wLpad, true);
+      int stage = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int u = 0; u < nu && ok; ++u) {
+        const int buf = u & 1;
+        if (u >= 2) ok = mbar_wait(smem_u32(&bar_d1empty[buf]), ((u >> 1) - 1) & 1, &abort_flag);
+        if (ok) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag);
+        if (!ok) break;
+        fence_after();
+        const uint32_t blb = bl_base + buf * bl_bytes;
+        const uint32_t d1 = tmem + d1_col + buf * p.wRpad;
+        for (int t = 0; t < nt; ++t) {
+          ok = mbar_wait(smem_u32(&bar_full[stage]), ph, &abort_flag);
+          if (!ok) break;
+          fence_after();
+          const uint32_t sa = base + stage * stage_bytes;
+          const uint32_t sbr = sa + a_bytes;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t da = sdesc(sa + (kk >> 2) * (a_bytes / 2) + (kk & 3) * 32, 16, 1024);
+            const uint64_t db = sdesc(sbr + (kk >> 2) * (br_bytes / 2) + (kk & 3) * 32, 16, 1024);
+            mma_bf16(d1, da, db, id1, (t | kk) != 0);
+          }
+          const uint32_t d2 = tmem + d2_col + t * p.wLpad;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t da = sdesc(sa + kk * 2048, a_bytes / 2, 1024);
+            const uint64_t db = sdesc(blb + (kk >> 2) * (bl_bytes / 2) + (kk & 3) * 32, 16, 1024);
+            mma_bf16(d2, da, db, id2, (u | kk) != 0);
+          }
+          mma_commit(smem_u32(&bar_empty[stage]));
+          if (++stage == S) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bar_blempty[buf]));
+        mma_commit(smem_u32(&bar_d1full[buf]));
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(p.err, 4);
+      }
+      // completion of every MMA issued here (also on the abort path)
+      mma_commit(smem_u32(&bar_d2full));
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;
+    const int r_in = 32 * q + lane;
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    bool ok = true;
+    for (int u = 0; u < nu && ok; ++u) {
+      const int buf = u & 1;
+      ok = mbar_wait(smem_u32(&bar_d1full[buf]), (u >> 1) & 1, &abort_flag);
+      if (!ok) break;
+      fence_after();
+      const int64_t row = (int64_t)(b0 + u) * kTileM + r_in;
+      float* dst = p.D1p + ((int64_t)c * p.nb * kTileM + row) * p.wRpad;
+      for (int cg = 0; cg < p.wRpad; cg += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + lane_off + d1_col + buf * p.wRpad + cg, v);
+        tmem_wait_ld();
+        if (row < p.nL) {
+          float4* d4 = reinterpret_cast<float4*>(dst + cg);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
+    }
+    if (!ok) {
+      abort_flag = 1;
+      atomicOr(p.err, 8);
+    }
+    // D2 of the column chunk
+    if (nu == 0) {
+      for (int t = 0; t < p.tiles; ++t) {
+        const int64_t col = col0 + t * kTileN + r_in;
+        if (col >= p.nR) continue;
+        float* dst = p.D2p + ((int64_t)g * p.C * cw + col) * p.wLpad;
+        for (int k = 0; k < p.wLpad; ++k) dst[k] = 0.f;
+      }
+    } else if (ok && mbar_wait(smem_u32(&bar_d2full), 0, &abort_flag)) {
+      fence_after();
+      for (int t = 0; t < nt; ++t) {
+        const int64_t col = col0 + t * kTileN + r_in;
+        float* dst = p.D2p + ((int64_t)g * p.C * cw + col) * p.wLpad;
+        for (int cg = 0; cg < p.wLpad; cg += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + lane_off + d2_col + t * p.wLpad + cg, v);
+          tmem_wait_ld();
+          if (col < p.nR) {
+            float4* d4 = reinterpret_cast<float4*>(dst + cg);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                  __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+          }
+        }
+      }
+    } else {
+      atomicOr(p.err, 16);
+    }
+  }
+  // all MMAs must be complete before TMEM is released
+  if (warp == 1 && lane == 0 && nu > 0) {
+    if (!mbar_drain(smem_u32(&bar_d2full), 0)) atomicOr(p.err, 32);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+  }
+}
+
+// D[i][w] = sum_k P[k][i][w] for w < wpad (rows i < rows).
+__global__ void reduce_partials(const float* P, int K, int64_t stride_k, int64_t rows, int wpad,
+                                float* D) {
+  const int64_t n4 = rows * wpad / 4;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float4 acc = reinterpret_cast<const float4*>(P)[e];
+    for (int k = 1; k < K; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(P + k * stride_k)[e];
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    reinterpret_cast<float4*>(D)[e] = acc;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)ptr;
+  }
+  return fn;
+}
+
+// 2-D bf16 map over a row-major (outer x inner) array, 64 x box_outer boxes.
+static ttnn_status make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer,
+                            int box_outer) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return TTNN_ECUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
+  cuuint32_t es[2] = {1u, 1u};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TTNN_ECUDA;
+  }
+  return TTNN_OK;
+}
+
+struct Geometry {
+  int C, G, nb, tiles, stages, grid;
+  int64_t d1p_elems, d2p_elems;
+  size_t smem;
+};
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+static bool geometry(const ttnn_plan_s& P, int64_t nL, int64_t nR, Geometry* g) {
+  if (P.wRpad < 16 || P.wLpad < 16 || P.wRpad > 256 || P.wLpad > 256) return false;
+  int tiles = (512 - 2 * P.wRpad) / P.wLpad;
+  tiles = std::min(tiles, kMaxTiles);
+  tiles = (int)std::min<int64_t>(tiles, (nR + kTileN - 1) / kTileN);
+  if (tiles < 1) return false;
+  const int64_t stage_bytes = kTileM * 128 * 2 + (int64_t)P.wRpad * 256;
+  const int64_t bl = 2 * (int64_t)P.wLpad * 256;
+  const int stages = (int)std::min<int64_t>(8, (kSmemBudget - 1024 - bl) / stage_bytes);
+  if (stages < 2) return false;
+  g->tiles = tiles;
+  g->stages = stages;
+  g->C = (int)((nR + tiles * kTileN - 1) / (tiles * kTileN));
+  g->nb = (int)((nL + kTileM - 1) / kTileM);
+  const int sms = sm_count();
+  g->G = std::max(1, std::min(sms / g->C, g->nb));
+  if (sms < g->C) g->G = 1;
+  g->grid = g->C * g->G;
+  g->d1p_elems = (int64_t)g->C * g->nb * kTileM * P.wRpad;
+  g->d2p_elems = (int64_t)g->G * g->C * tiles * kTileN * P.wLpad;
+  g->smem = (size_t)(1024 + stages * stage_bytes + bl);
+  return true;
+}
+
+}  // namespace tc
+
 ttnn_status tc_pass_supported(const ttnn_plan_s& P, int64_t nL, int64_t nR) {
-  (void)P; (void)nL; (void)nR;
-  return TTNN_EUNSUPPORTED;
+  if (P.dtype != TTNN_BF16 || P.pass_store != 2) return TTNN_EUNSUPPORTED;
+  if (P.wR <= 0 || P.wL <= 0) return TTNN_EUNSUPPORTED;
+  if (nL % 8 != 0 || nR % 8 != 0) return TTNN_EUNSUPPORTED;   // 16-byte TMA row strides
+  if (nL >= (int64_t(1) << 31) || nR >= (int64_t(1) << 31)) return TTNN_EUNSUPPORTED;
+  tc::Geometry g;
+  if (!tc::geometry(P, nL, nR, &g)) return TTNN_EUNSUPPORTED;
+  return TTNN_OK;
 }
 
 ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int64_t nR,
                            const void* sR, int64_t ldR, const void* sL, int64_t ldL, void* D1,
                            void* D2, const float* tile_scale, void* ws, int64_t ws_bytes,
                            cudaStream_t st, bool dry, int64_t* ws_need) {
-  (void)P; (void)A; (void)nL; (void)nR; (void)sR; (void)ldR; (void)sL; (void)ldL; (void)D1;
-  (void)D2; (void)tile_scale; (void)ws; (void)ws_bytes; (void)st; (void)dry;
-  if (ws_need) *ws_need = 0;
-  set_error("tensor-core pass not available");
-  return TTNN_EUNSUPPORTED;
+  (void)tile_scale;
+  tc::Geometry g;
+  if (!tc::geometry(P, nL, nR, &g)) {
+    set_error("tensor-core pass: unsupported geometry");
+    return TTNN_EUNSUPPORTED;
+  }
+  const int64_t need = (g.d1p_elems + g.d2p_elems) * 4 + 512;
+  if (dry) {
+    if (ws_need) *ws_need = need;
+    return TTNN_OK;
+  }
+  if (ws_bytes < need) {
+    set_error("tensor-core pass: workspace too small");
+    return TTNN_ENOMEM;
+  }
+  if (((uintptr_t)A & 15) || ldR != nR || ldL != nL) {
+    set_error("tensor-core pass: operands must be 16-byte aligned and dense");
+    return TTNN_EUNSUPPORTED;
+  }
+  CUtensorMap mA, mBR, mBL;
+  TTNN_TRY(tc::make_map(&mA, A, nR, nL, tc::kTileM));
+  TTNN_TRY(tc::make_map(&mBR, sR, nR, P.wRpad, P.wRpad));
+  TTNN_TRY(tc::make_map(&mBL, sL, nL, P.wLpad, P.wLpad));
+  tc::Params prm;
+  prm.nL = nL;
+  prm.nR = nR;
+  prm.C = g.C;
+  prm.G = g.G;
+  prm.nb = g.nb;
+  prm.tiles = g.tiles;
+  prm.stages = g.stages;
+  prm.wRpad = P.wRpad;
+  prm.wLpad = P.wLpad;
+  prm.D1p = (float*)ws;
+  prm.D2p = prm.D1p + g.d1p_elems;
+  prm.err = P.err_dev;
+  TTNN_TRY_CUDA(cudaFuncSetAttribute(tc::pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g.smem));
+  tc::pass_kernel<<<g.grid, tc::kThreads, g.smem, st>>>(mA, mBR, mBL, prm);
+  TTNN_TRY(check_launch("tc pass_kernel"));
+  const int sms = tc::sm_count();
+  tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D1p, g.C, (int64_t)g.nb * tc::kTileM * P.wRpad,
+                                               nL, P.wRpad, (float*)D1);
+  TTNN_TRY(check_launch("reduce_partials(D1)"));
+  tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
+                                               nR, P.wLpad, (float*)D2);
+  TTNN_TRY(check_launch("reduce_partials(D2)"));
+  return TTNN_OK;
 }
 
 }  // namespace ttnn

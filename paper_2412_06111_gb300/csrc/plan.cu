@@ -744,9 +744,11 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     TTNN_TRY(launch_tc_pass(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, nullptr, 0, st,
                             true, &need));
     char* tw = ws.alloc(need);
-    if (!dry)
+    if (!dry) {
       TTNN_TRY(launch_tc_pass(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, st,
                               false, nullptr));
+      ++P.n_tc_pass;
+    }
     ws.top = mark;
   } else {
     if (P.pass_store == 3 || P.dtype == TTNN_BF16X2) {
@@ -754,6 +756,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       return TTNN_EUNSUPPORTED;
     }
     const int in_type = P.pass_store == 0 ? 0 : P.pass_store == 1 ? 1 : 2;
+    if (!dry) ++P.n_simt_pass;
     if (P.wR > 0) {
       Gemm g;
       g.I = nL; g.Jn = P.wR; g.K = nR;
@@ -1081,6 +1084,16 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
                                   cudaMemcpyDeviceToHost, st));
     TTNN_TRY_CUDA(cudaStreamSynchronize(st));
     for (size_t k = 0; k < jobs.size(); ++k) P.nodes[job_node[k]].kept = kept[k];
+  }
+  if (!dry && P.err_dev) {
+    int err = 0;
+    TTNN_TRY_CUDA(cudaMemcpyAsync(&err, P.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TTNN_TRY_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+      TTNN_TRY_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
+      set_error("a bounded device wait ran out in an earlier update (code %d)", err);
+      return TTNN_ETIMEOUT;
+    }
   }
   return TTNN_OK;
 }

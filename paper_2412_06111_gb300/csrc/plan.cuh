@@ -63,10 +63,12 @@ struct ttnn_plan_s {
   int64_t ws_bytes = 0;
   ttnn::QrJob* jobs_dev = nullptr;
   int* kept_dev = nullptr;
+  int* err_dev = nullptr;       // device error word of bounded waits (tensor-core pass)
   int n_sketched = 0;
   int64_t state_elems = 0;
   int64_t core_elems = 0;
   int tc_ok = 0;                // tensor-core pass usable for this plan
+  int64_t n_tc_pass = 0, n_simt_pass = 0;
   // profiling: event pairs per phase (0 pass, 1 walk, 2 recovery)
   int profile = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[3];

@@ -214,3 +214,41 @@ def test_profiling_intervals_and_launch_counter():
         api.ttnn_profile(run.plan, False)
     finally:
         run.close()
+
+
+TC_CASES = {
+    # (tree, dims, r, p): pass-matrix sizes nL x nR are multiples of 8 so the
+    # BF16 plans take the tensor-core pass; several 128-row blocks, ragged tails
+    "bin5_960x960": (W.balanced_binary(5), [8, 12, 10, 24, 40], 4, 2),
+    "bin5_512x1600": (W.balanced_binary(5), [8, 8, 8, 40, 40], 5, 3),
+    "tt4_4096x24": (W.tensor_train(4), [16, 16, 16, 24], 6, 3),
+    "bin4_r20": (W.balanced_binary(4), [16, 16, 32, 32], 20, 10),
+}
+
+
+@pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
+@pytest.mark.parametrize("case", sorted(TC_CASES))
+def test_tensor_core_pass_matches_oracle_and_simt(case, variant):
+    tr, dims, r, p = TC_CASES[case]
+    n = len(tr[0])
+    T = W.gaussian(dims, 23)
+    dev, Tq = _dev(T, api.BF16)
+    tc = Run(tr, dims, [r] * n, [p] * n, 77, dtype=api.BF16, variant=variant)
+    simt = Run(tr, dims, [r] * n, [p] * n, 77, dtype=api.BF16, variant=variant,
+               flags=api.FLAG_SIMT_PASS)
+    try:
+        api.ttnn_profile(tc.plan, True)
+        api.ttnn_update_dense(tc.state, dev)
+        api.ttnn_update_dense(simt.state, dev)
+        t = _otree(tr, dims, r, p)
+        drm = O.Drm(t, 77, "bf16", "sttnn" if variant else "ttnn")
+        assert api.ttnn_plan_pass_counts(tc.plan) == (1, 0)
+        assert api.ttnn_plan_pass_counts(simt.plan) == (0, 1)
+        _compare_sketches(tc, t, Tq, drm, variant, 1e-5)
+        a, b = tc.state_host(), simt.state_host()
+        assert rel(a, b) <= 1e-5
+        # recovery reports no device-side timeout from the pass
+        tc.recover()
+    finally:
+        tc.close()
+        simt.close()
