@@ -119,6 +119,7 @@ typedef struct {
   int32_t core_ndim;
   int64_t core_shape[10];
   int32_t kept_rank;    /* after ttnn_recover: rank kept by the eps-pseudo-inverse (-1 before) */
+  int32_t jacobi_sweeps; /* after ttnn_recover: sweeps of the one-sided Jacobi SVD of R_v */
 } ttnn_node_info;
 
 /* ---------------------------------------------------------------------- */

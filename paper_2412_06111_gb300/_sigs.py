@@ -22,7 +22,8 @@ class TtnnNodeInfo(C.Structure):
                 ("omega_offset", c_i64), ("omega_elems", c_i64), ("psi_offset", c_i64),
                 ("psi_elems", c_i64), ("psi_ndim", c_i32), ("psi_shape", c_i64 * 10),
                 ("core_offset", c_i64), ("core_elems", c_i64), ("core_ndim", c_i32),
-                ("core_shape", c_i64 * 10), ("kept_rank", c_i32)]
+                ("core_shape", c_i64 * 10), ("kept_rank", c_i32),
+                ("jacobi_sweeps", c_i32)]
 
 
 SIGS = {

@@ -167,7 +167,7 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   P.ws_bytes = std::max(need_u, need_r) + 4096;
   if ((s = dev_alloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
   if ((s = dev_alloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
-  if ((s = dev_alloc((void**)&P.kept_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
+  if ((s = dev_alloc((void**)&P.kept_dev, 2 * std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
   if ((s = dev_alloc((void**)&P.err_dev, sizeof(int))) != TTNN_OK) return fail(s);
   if ((s = launch_fill_zero(P.err_dev, sizeof(int), st)) != TTNN_OK) return fail(s);
   cudaError_t e = cudaStreamSynchronize(st);
@@ -220,6 +220,7 @@ ttnn_status ttnn_plan_node(ttnn_plan_t P, int32_t v, ttnn_node_info* o) {
   o->core_ndim = (int32_t)std::min<size_t>(nd.core_shape.size(), 10);
   for (int k = 0; k < o->core_ndim; ++k) o->core_shape[k] = nd.core_shape[k];
   o->kept_rank = nd.kept;
+  o->jacobi_sweeps = nd.sweeps;
   return TTNN_OK;
 }
 

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "philox.cuh"
@@ -221,11 +222,119 @@ int64_t contract_partial_elems(const Contract& c) {
   return ns > 1 ? ns * c.P * c.NB * c.Q * c.J : 0;
 }
 
+// Mode product as a batched small GEMM: for every batch item (p, q),
+// out[p,b,q,j] (+)= alpha * sum_i W[i*wsI + b*wsB] * in[p,i,q,j].  W is staged
+// in shared memory once per K chunk; each thread owns a 4 x 4 tile of
+// (b, column) outputs, where the columns are the (item, j) pairs of CH items.
+constexpr int kMpKC = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) mp_kernel(Contract c, int BG, int CG, int CH) {
+  extern __shared__ __align__(16) unsigned char mp_smem[];
+  T* Ws = (T*)mp_smem;                 // [kMpKC][4*BG]
+  T* Is = Ws + kMpKC * 4 * BG;         // [kMpKC][4*CG]
+  const T* in = (const T*)c.in;
+  const T* w = (const T*)c.w;
+  T* out = (T*)c.out;
+  const int tid = threadIdx.x;
+  const int bg = tid / CG, cg = tid % CG;
+  const int ncol = CH * (int)c.J;
+  const int64_t items = c.P * c.Q;
+  const int WB = 4 * BG, WC = 4 * CG;
+  for (int64_t it0 = (int64_t)blockIdx.x * CH; it0 < items; it0 += (int64_t)gridDim.x * CH) {
+    T acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0;
+    for (int64_t i0 = 0; i0 < c.NI; i0 += kMpKC) {
+      const int kc = (int)min((int64_t)kMpKC, c.NI - i0);
+      __syncthreads();
+      for (int e = tid; e < kc * WB; e += 256) {
+        const int ii = e / WB, b = e % WB;
+        Ws[ii * WB + b] = (b < c.NB) ? w[(i0 + ii) * c.wsI + b * c.wsB] : (T)0;
+      }
+      for (int e = tid; e < kc * WC; e += 256) {
+        const int ii = e / WC, col = e % WC;
+        T v = 0;
+        if (col < ncol) {
+          const int64_t item = it0 + col / c.J;
+          if (item < items) {
+            const int64_t j = col % c.J;
+            const int64_t p = item / c.Q, q = item % c.Q;
+            v = in[p * c.isP + (i0 + ii) * c.isI + q * c.isQ + j * c.isJ];
+          }
+        }
+        Is[ii * WC + col] = v;
+      }
+      __syncthreads();
+      if (bg < BG) {
+        for (int ii = 0; ii < kc; ++ii) {
+          T a[4], b[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            a[x] = Ws[ii * WB + 4 * bg + x];
+            b[x] = Is[ii * WC + 4 * cg + x];
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+        }
+      }
+    }
+    if (bg < BG) {
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int col = 4 * cg + y;
+        if (col >= ncol) continue;
+        const int64_t item = it0 + col / c.J;
+        if (item >= items) continue;
+        const int64_t j = col % c.J;
+        const int64_t p = item / c.Q, q = item % c.Q;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int b = 4 * bg + x;
+          if (b >= c.NB) continue;
+          const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+          const T v = (T)c.alpha * acc[x][y];
+          out[oi] = c.accumulate ? out[oi] + v : v;
+        }
+      }
+    }
+  }
+}
+
+// Shapes the batched kernel takes: W independent of q and j, enough work.
+static bool mp_shape(const Contract& c, int elem_bytes, int* BG, int* CG, int* CH) {
+  if (!c.w || c.wsQ != 0 || c.wsJ != 0 || c.NI < 8 || c.NB > 64) return false;
+  int bg = (int)((c.NB + 3) / 4);
+  int p2 = 1;
+  while (p2 < bg) p2 <<= 1;
+  // shared memory kMpKC * 4 * (BG + CG) elements stays within 48 KB
+  const int cg = std::min(256 / p2, elem_bytes == 8 ? 32 : 64);
+  if (c.J > 4 * cg) return false;
+  const int ch = (int)(4 * cg / c.J);
+  if (c.P * c.Q * c.NB * c.J < 4096) return false;
+  *BG = p2;
+  *CG = cg;
+  *CH = ch;
+  return true;
+}
+
 template <typename Tin, typename Tw, typename Tout, typename Tacc>
 static ttnn_status run_contract(const Contract& c, void* partial, int64_t partial_elems,
                                 cudaStream_t st) {
   const int64_t total = c.P * c.NB * c.Q * c.J;
   if (total == 0) return TTNN_OK;
+  int BG, CG, CH;
+  if (std::is_same<Tin, Tw>::value && std::is_same<Tin, Tout>::value && mp_shape(c, (int)sizeof(Tin), &BG, &CG, &CH)) {
+    const size_t smem = (size_t)kMpKC * 4 * (BG + CG) * sizeof(Tin);
+    const int64_t items = c.P * c.Q;
+    const int64_t blocks = std::min<int64_t>(ceil_div(items, CH), (int64_t)num_sms() * 8);
+    mp_kernel<Tin><<<(unsigned)blocks, 256, smem, st>>>(c, BG, CG, CH);
+    return check_launch("mp_kernel");
+  }
   int ns;
   int64_t chunk;
   contract_split(c, &ns, &chunk);

@@ -9,6 +9,7 @@
 #include <numeric>
 
 #include "plan.cuh"
+#include "program.cuh"
 
 namespace ttnn {
 
@@ -339,17 +340,21 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
 // ---------------------------------------------------------------------------
 // workspace stack and tensor views
 // ---------------------------------------------------------------------------
+// Workspace of one update or recovery: a bump allocator.  Nothing is reused
+// inside a program, so the executor may reorder independent ops freely.
 struct Ws {
   char* base;
   int64_t cap, top = 0, peak = 0;
   bool dry;
+  Program* prog = nullptr;
   Ws(char* b, int64_t c, bool d) : base(b), cap(c), dry(d) {}
   char* alloc(int64_t bytes) {
     const int64_t o = round_up(top, 256);
     top = o + std::max<int64_t>(bytes, 0);
     peak = std::max(peak, top);
-    if (dry) return base + 0;   // never dereferenced in a dry run
-    return base + o;
+    char* p = dry ? base : base + o;
+    if (prog && !dry) prog->buffer(p, std::max<int64_t>(bytes, 1));
+    return p;
   }
   bool ok() const { return dry || top <= cap; }
 };
@@ -390,6 +395,7 @@ struct Ctx {
   const char* facw;     // walk-type factors
   const char* yw;       // walk-type copy of the pass Y block (rows of the Y child, box)
   int64_t yw_ld;
+  Program* prog;
 };
 
 static int find_ax(const View& v, int kind, int id) {
@@ -465,11 +471,12 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
   c.osB = c.Q * c.J;
   c.osP = c.NB * c.Q * c.J;
   c.in = in.ptr;
-  const int64_t pe = contract_partial_elems(c);
-  const int64_t mark = C.ws.top;
-  char* partial = pe ? C.ws.alloc(pe * C.eb) : nullptr;
-  if (!C.dry) TTNN_TRY(launch_contract(c, C.et, C.et, C.et, partial, pe, C.st));
-  C.ws.top = mark;    // partial buffer is free again once the launch is queued
+  Op op;
+  op.tin = op.tw = op.tout = C.et;
+  op.c = c;
+  const int64_t pe = plan_contract(op);
+  op.partial = pe ? C.ws.alloc(pe * C.eb) : nullptr;
+  if (!C.dry) C.prog->add(op, in.ptr, W);
   *out = o;
   return TTNN_OK;
 }
@@ -480,9 +487,13 @@ static const char* facY(Ctx& C, int mode) { return C.facw + (C.P.y_off[mode] + C
 // Khatri-Rao contraction of the modes [lo, hi) of `in` with the Y factors,
 // producing one sketch axis (kind AX_SK, id = node) of size s at the place of
 // the modes (Sec. 7: Y_t = kr of its modes' Y_mu, columns shared).
-static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int s, View* out) {
+// With first_done the sketch axis already replaces mode hi - 1 (a shared
+// first mode product) and only the Khatri-Rao steps remain.
+static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int s, View* out,
+                           bool first_done = false) {
   View cur = in;
   for (int mode = hi - 1; mode >= lo; --mode) {
+    if (first_done && mode == hi - 1) continue;
     const int k = find_ax(cur, AX_MODE, mode);
     if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
     View nx;
@@ -532,7 +543,13 @@ static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::ve
   s.out = base;
   s.alpha = alpha;
   if (C.dry) return TTNN_OK;
-  return launch_scatter_add(s, C.P.walk_f64, C.st);
+  Op op;
+  op.kind = OP_SCATTER;
+  op.tin = op.tw = op.tout = C.et;
+  op.s = s;
+  plan_simple(op);
+  C.prog->add(op, v.ptr);
+  return TTNN_OK;
 }
 
 // Output strides of a Psi-shaped target: children axes (sketch or raw modes of
@@ -578,8 +595,17 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
   if (nd.rsub == 0) return TTNN_OK;
   if (nd.sketched()) {
     const View Gt = truncate_j(G, nd.r);
-    const int64_t mark = C.ws.top;
     View om;
+    // Omega_t and Psi_t both start by contracting t's last mode with the same
+    // Y columns when the last child's sketch size equals s_t: do it once.
+    const TNode* lastc = nd.leaf ? nullptr : &P.nodes[nd.ch.back()];
+    const bool share = v != P.ychild && lastc && !lastc->identity && lastc->s == nd.s;
+    View z;
+    if (share) {
+      const int k = find_ax(Gt, AX_MODE, nd.hi - 1);
+      Ax nax{AX_SK, v, nd.s, 0};
+      TTNN_TRY(contract_view(C, Gt, k, facY(C, nd.hi - 1), P.smax, 1, -1, &nax, &z));
+    }
     if (v == P.ychild) {
       // Y of the pass-side root child is the stored (rounded) block
       View mg = Gt;
@@ -588,11 +614,12 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
       mg.ax = {Ax{AX_MODE, nd.lo, nb, 0}, Gt.ax.back()};
       Ax nax{AX_SK, v, nd.s, 0};
       TTNN_TRY(contract_view(C, mg, 0, C.yw, 1, C.yw_ld, -1, &nax, &om));
+    } else if (share) {
+      TTNN_TRY(y_chain(C, z, v, nd.lo, nd.hi, nd.s, &om, true));
     } else {
       TTNN_TRY(y_chain(C, Gt, v, nd.lo, nd.hi, nd.s, &om));
     }
     TTNN_TRY(scatter_into(C, om, state_at(C, acc, nd.om_off), {(int64_t)nd.r, 1}, lambda));
-    C.ws.top = mark;
     if (nd.leaf) {
       std::vector<int64_t> os(Gt.ax.size(), 1);
       for (int a = 0; a + 1 < (int)Gt.ax.size(); ++a) {
@@ -607,18 +634,23 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
         const TNode& c = P.nodes[nd.ch[k]];
         if (c.identity) continue;
         View nx;
-        TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+        if (share && k == (int)nd.ch.size() - 1) {
+          View zc = z;
+          for (auto& a : zc.ax)
+            if (a.kind == AX_SK && a.id == v) a.id = c.user;
+          TTNN_TRY(y_chain(C, zc, c.user, c.lo, c.hi, c.s, &nx, true));
+        } else {
+          TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+        }
         cur = nx;
       }
       TTNN_TRY(scatter_into(C, cur, state_at(C, acc, nd.ps_off), psi_strides(C, cur, nd, true), lambda));
-      C.ws.top = mark;
     }
   }
   // children
   for (size_t k = 0; k < nd.ch.size(); ++k) {
     const TNode& c = P.nodes[nd.ch[k]];
     if (c.rsub == 0) continue;
-    const int64_t mark = C.ws.top;
     View cur = truncate_j(G, c.rsub);
     for (size_t k2 = 0; k2 < nd.ch.size(); ++k2) {
       if (k2 == k) continue;
@@ -635,7 +667,6 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
       }
     }
     TTNN_TRY(walk(C, acc, c.user, cur, lambda));
-    C.ws.top = mark;
   }
   return TTNN_OK;
 }
@@ -698,8 +729,11 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
                              int64_t* peak) {
   Ws ws(P.ws, P.ws_bytes, dry);
+  Program prog;
+  ws.prog = &prog;
   const int eb = P.walk_f64 ? 8 : 4;
-  Ctx C{P, ws, st, dry, eb, P.walk_f64 ? ET_F64 : ET_F32, box, (const char*)P.facw, nullptr, 0};
+  Ctx C{P, ws, st, dry, eb, P.walk_f64 ? ET_F64 : ET_F32, box, (const char*)P.facw, nullptr, 0,
+        &prog};
   int64_t nL = 1, nR = 1;
   for (int m = P.Llo; m < P.Lhi; ++m) nL *= box.ext[m];
   for (int m = P.Rlo; m < P.Rhi; ++m) nR *= box.ext[m];
@@ -799,7 +833,6 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     for (size_t k = 0; k < P.Lch.size(); ++k) {
       const TNode& c = P.nodes[P.Lch[k]];
       if (c.rsub == 0) continue;
-      const int64_t mark = ws.top;
       View cur = truncate_j(GL, c.rsub);
       for (size_t k2 = 0; k2 < P.Lch.size(); ++k2) {
         if (k2 == k) continue;
@@ -811,7 +844,6 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
         }
       }
       TTNN_TRY(walk(C, acc, c.user, cur, lambda));
-      ws.top = mark;
     }
   }
   if (P.variant == TTNN_VARIANT_TTNN) {
@@ -821,7 +853,6 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       for (size_t k = 0; k < P.Rch.size(); ++k) {
         const TNode& c = P.nodes[P.Rch[k]];
         if (c.rsub == 0) continue;
-        const int64_t mark = ws.top;
         View cur = truncate_j(GR, c.rsub);
         for (size_t k2 = 0; k2 < P.Rch.size(); ++k2) {
           if (k2 == k) continue;
@@ -833,11 +864,9 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
           }
         }
         TTNN_TRY(walk(C, acc, c.user, cur, lambda));
-        ws.top = mark;
       }
     }
     // root Psi
-    const int64_t mark = ws.top;
     if (P.yside == 0) {
       View H{D1 + (int64_t)P.rXL * eb, mode_axes(P.Llo, P.Lhi), P.wRpad};
       H.ax.push_back(Ax{AX_SK, P.ychild, P.wYR, 0});
@@ -873,7 +902,6 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       os.back() = rest;
       TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
     }
-    ws.top = mark;
   } else {
     // STTNN: D2 = M^T Y_c1 (nR x s'_c1): R children and the root
     View H{D2, mode_axes(P.Rlo, P.Rhi), P.wLpad};
@@ -882,7 +910,6 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     for (size_t k = 0; k < P.Rch.size(); ++k) {
       const TNode& c = P.nodes[P.Rch[k]];
       if (c.rsub == 0) continue;
-      const int64_t mark = ws.top;
       // contract the c1 sketch axis with XT_c1: creates the column axis
       View cur;
       Ax jax{AX_J, -1, c.rsub, 0};
@@ -903,9 +930,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
         }
       }
       TTNN_TRY(walk(C, acc, c.user, cur, lambda));
-      ws.top = mark;
     }
-    const int64_t mark = ws.top;
     View cur = H;
     for (int k = (int)P.Rch.size() - 1; k >= 0; --k) {
       const TNode& c = P.nodes[P.Rch[k]];
@@ -922,8 +947,8 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     }
     os.back() = rest;
     TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
-    ws.top = mark;
   }
+  if (!dry) TTNN_TRY(prog.run(st));
   cudaEvent_t ev2 = dry ? nullptr : prof_event(P, st);
   prof_push(P, 1, ev1, ev2);
   if (peak) *peak = ws.peak;
@@ -963,6 +988,7 @@ void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b) {
 ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
                         int64_t* peak) {
   Ws ws(P.ws, P.ws_bytes, dry);
+  Program prog;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
   const int seb = P.walk_f64 ? 8 : 4;
   const ElemType set = P.walk_f64 ? ET_F64 : ET_F32;
@@ -985,12 +1011,14 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
     TTNN_TRY(launch_qr_pinv(P.jobs_dev, (int)jobs.size(), P.walk_f64, P.eps_factor, P.u,
                             P.kept_dev, st));
   }
-  // a generic f64 contraction on a contiguous tensor with dims `dims`:
-  // contract axis k with W (i, b) = W[i*wsI + b*wsB] into a new axis of nb.
+  ws.prog = &prog;   // Q and R_eps^+ above are produced before the program (level 0)
+  // contraction of axis k of a contiguous tensor `dims` with W(i, b) =
+  // W[i*wsI + b*wsB] into a new axis of nb, written with strides (osP, osB, osQ)
   auto mp = [&](const void* in, bool in_state, const std::vector<int64_t>& dims, int k,
-                const double* W, int64_t wsI, int64_t wsB, int64_t nb, double* out,
-                int64_t osP, int64_t osB, int64_t osQ) -> ttnn_status {
-    Contract c;
+                const double* W, int64_t wsI, int64_t wsB, int64_t nb, double* out, int64_t osP,
+                int64_t osB, int64_t osQ) -> ttnn_status {
+    Op op;
+    Contract& c = op.c;
     c.P = 1;
     for (int a = 0; a < k; ++a) c.P *= dims[a];
     c.NI = dims[k];
@@ -1008,21 +1036,25 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
     c.osP = osP;
     c.osB = osB;
     c.osQ = osQ;
-    c.osJ = 0;
-    const int64_t pe = contract_partial_elems(c);
-    const int64_t mark = ws.top;
-    char* part = pe ? ws.alloc(pe * 8) : nullptr;
-    if (!dry)
-      TTNN_TRY(launch_contract(c, in_state ? set : ET_F64, ET_F64, ET_F64, part, pe, st));
-    ws.top = mark;
+    op.tin = in_state ? set : ET_F64;
+    op.tw = ET_F64;
+    op.tout = ET_F64;
+    const int64_t pe = plan_contract(op);
+    op.partial = pe ? ws.alloc(pe * 8) : nullptr;
+    if (!dry) prog.add(op, in, W);
     return TTNN_OK;
   };
   for (int v : P.lex) {
     TNode& nd = P.nodes[v];
     double* core = cores + nd.core_off;
-    const int64_t mark = ws.top;
     if (v != P.root && nd.identity) {
-      if (!dry) TTNN_TRY(launch_eye(core, nd.n, st));
+      Op op;
+      op.kind = OP_EYE;
+      op.tout = ET_F64;
+      op.eye_n = nd.n;
+      op.c.out = core;
+      plan_simple(op);
+      if (!dry) prog.add(op, nullptr);
       continue;
     }
     if (v != P.root && nd.leaf) {
@@ -1055,35 +1087,41 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
     if (v == P.root) {
       int64_t tot = 1;
       for (auto x : dims) tot *= x;
-      // copy (identity W via a 1-long contraction)
-      Contract c;
-      c.P = tot;
-      c.NI = 1;
-      c.isP = 1;
-      c.in = cur;
-      c.out = core;
-      c.osP = 1;
-      if (!dry) TTNN_TRY(launch_contract(c, in_state ? set : ET_F64, ET_F64, ET_F64, nullptr, 0, st));
+      Op op;
+      op.c.P = tot;
+      op.c.NI = 1;
+      op.c.isP = 1;
+      op.c.in = cur;
+      op.c.out = core;
+      op.c.osP = 1;
+      op.tin = in_state ? set : ET_F64;
+      op.tw = ET_F64;
+      op.tout = ET_F64;
+      plan_contract(op);
+      if (!dry) prog.add(op, cur);
     } else {
       int64_t rest = 1;
       for (int k = 0; k < m; ++k) rest *= dims[k];
       // out[b][p] = sum_k cur[p][k] Rp[k][b]
       TTNN_TRY(mp(cur, in_state, {rest, (int64_t)nd.r}, 1, Rp[v], nd.r, 1, nd.r, core, 1, rest, 0));
     }
-    ws.top = mark;
   }
   if (peak) *peak = ws.peak;
   if (!ws.ok()) {
     set_error("internal: workspace overflow in recovery");
     return TTNN_ENOMEM;
   }
+  if (!dry) TTNN_TRY(prog.run(st));
   if (!dry) prof_push(P, 2, ev0, prof_event(P, st));
   if (!dry && !jobs.empty()) {
-    std::vector<int> kept(jobs.size());
+    std::vector<int> kept(2 * jobs.size());
     TTNN_TRY_CUDA(cudaMemcpyAsync(kept.data(), P.kept_dev, kept.size() * sizeof(int),
                                   cudaMemcpyDeviceToHost, st));
     TTNN_TRY_CUDA(cudaStreamSynchronize(st));
-    for (size_t k = 0; k < jobs.size(); ++k) P.nodes[job_node[k]].kept = kept[k];
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      P.nodes[job_node[k]].kept = kept[k];
+      P.nodes[job_node[k]].sweeps = kept[jobs.size() + k];
+    }
   }
   if (!dry && P.err_dev) {
     int err = 0;

@@ -22,6 +22,7 @@ struct TNode {
   std::vector<int64_t> core_shape;
   int64_t xt_off = -1;          // STTNN XT_v factor offset (elements) in the factor arrays
   int kept = -1;
+  int sweeps = 0;
   bool sketched() const { return parent >= 0 && !identity; }
 };
 

@@ -1,0 +1,391 @@
+// Batched executor of small-contraction programs (see program.cuh).
+#include <algorithm>
+#include <type_traits>
+
+#include "program.cuh"
+
+namespace ttnn {
+
+constexpr int kExecThreads = 256;
+static_assert(sizeof(LevelBatch) <= 32000, "level batch must fit the kernel parameter space");
+constexpr int kMpKC2 = 32;
+constexpr size_t kExecSmem = 48 * 1024;
+
+static int exec_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// device parts
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tw, typename Tout, typename Tacc>
+__device__ void dev_contract(const DevOp& op, int64_t blk) {
+  const Contract& c = op.c;
+  const int g = op.g;
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  const int64_t vo = blk * (kExecThreads / g) + threadIdx.x / g;
+  const int lg = threadIdx.x % g;
+  const bool valid = vo < total * op.nsplit;
+  Tacc acc = 0;
+  int64_t split = 0, o = 0, p = 0, b = 0, q = 0, j = 0;
+  if (valid) {
+    split = vo / total;
+    o = vo - split * total;
+    int64_t t = o;
+    j = t % c.J;
+    t /= c.J;
+    q = t % c.Q;
+    t /= c.Q;
+    b = t % c.NB;
+    p = t / c.NB;
+    const int64_t i0 = split * op.chunk;
+    const int64_t i1 = min(c.NI, i0 + op.chunk);
+    const Tin* ip = (const Tin*)c.in + p * c.isP + q * c.isQ + j * c.isJ;
+    if (c.w) {
+      const Tw* wp = (const Tw*)c.w + b * c.wsB + q * c.wsQ + j * c.wsJ;
+#pragma unroll 4
+      for (int64_t i = i0 + lg; i < i1; i += g) acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
+    } else {
+#pragma unroll 4
+      for (int64_t i = i0 + lg; i < i1; i += g) acc += (Tacc)ip[i * c.isI];
+    }
+  }
+  for (int off = g >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (valid && lg == 0) {
+    if (op.nsplit > 1) {
+      ((Tout*)op.partial)[split * total + o] = (Tout)acc;
+    } else {
+      Tout* out = (Tout*)c.out;
+      const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+      const Tout v = (Tout)((Tacc)c.alpha * acc);
+      out[oi] = c.accumulate ? (Tout)(out[oi] + v) : v;
+    }
+  }
+}
+
+template <typename T>
+__device__ void dev_reduce(const DevOp& op, int64_t blk) {
+  const Contract& c = op.c;
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  const int64_t o = blk * kExecThreads + threadIdx.x;
+  if (o >= total) return;
+  const T* part = (const T*)op.partial;
+  T acc = 0;
+  for (int s = 0; s < op.nsplit; ++s) acc += part[s * total + o];
+  int64_t t = o;
+  const int64_t j = t % c.J;
+  t /= c.J;
+  const int64_t q = t % c.Q;
+  t /= c.Q;
+  const int64_t b = t % c.NB;
+  const int64_t p = t / c.NB;
+  T* out = (T*)c.out;
+  const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+  const T v = (T)c.alpha * acc;
+  out[oi] = c.accumulate ? out[oi] + v : v;
+}
+
+// Mode product as a batched small GEMM over one chunk of CH batch items:
+// out[p,b,q,j] (+)= alpha * sum_i W[i*wsI + b*wsB] * in[p,i,q,j].
+template <typename T>
+__device__ void dev_mp(const DevOp& op, int64_t blk, unsigned char* smem) {
+  const Contract& c = op.c;
+  const int BG = op.BG, CG = op.CG, CH = op.CH;
+  const int WB = 4 * BG, WC = 4 * CG;
+  T* Ws = (T*)smem;                   // [kMpKC2][WB]
+  T* Is = Ws + kMpKC2 * WB;           // [kMpKC2][WC]
+  const int tid = threadIdx.x;
+  const int bg = tid / CG, cg = tid % CG;
+  const int J = (int)c.J;
+  const int ncol = CH * J;
+  const int64_t items = c.P * c.Q;
+  const int64_t it0 = blk * CH;
+  // fixed load column of this thread (WC divides the block size)
+  const int lcol = tid % WC, lrow0 = tid / WC, lstep = kExecThreads / WC;
+  bool lvalid = false;
+  int64_t lbase = 0;
+  if (lcol < ncol) {
+    const int64_t item = it0 + lcol / J;
+    if (item < items) {
+      const int64_t p = item / c.Q, q = item - (item / c.Q) * c.Q;
+      lbase = p * c.isP + q * c.isQ + (int64_t)(lcol % J) * c.isJ;
+      lvalid = true;
+    }
+  }
+  const int wcol = tid % WB, wrow0 = tid / WB, wstep = kExecThreads / WB;
+  const T* in = (const T*)c.in;
+  const T* w = (const T*)c.w;
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0;
+  for (int64_t i0 = 0; i0 < c.NI; i0 += kMpKC2) {
+    const int kc = (int)min((int64_t)kMpKC2, c.NI - i0);
+    __syncthreads();
+    for (int ii = wrow0; ii < kc; ii += wstep)
+      Ws[ii * WB + wcol] = (wcol < c.NB) ? w[(i0 + ii) * c.wsI + wcol * c.wsB] : (T)0;
+    for (int ii = lrow0; ii < kc; ii += lstep)
+      Is[ii * WC + lcol] = lvalid ? in[lbase + (i0 + ii) * c.isI] : (T)0;
+    __syncthreads();
+    if (bg < BG) {
+      for (int ii = 0; ii < kc; ++ii) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          a[x] = Ws[ii * WB + 4 * bg + x];
+          bb[x] = Is[ii * WC + 4 * cg + x];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * bb[y];
+      }
+    }
+  }
+  if (bg >= BG) return;
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    const int col = 4 * cg + y;
+    if (col >= ncol) continue;
+    const int64_t item = it0 + col / J;
+    if (item >= items) continue;
+    const int64_t j = col % J;
+    const int64_t p = item / c.Q, q = item - (item / c.Q) * c.Q;
+    T* out = (T*)c.out;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int b = 4 * bg + x;
+      if (b >= c.NB) continue;
+      const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+      const T v = (T)c.alpha * acc[x][y];
+      out[oi] = c.accumulate ? out[oi] + v : v;
+    }
+  }
+}
+
+template <typename T>
+__device__ void dev_scatter(const DevOp& op, int64_t blk) {
+  const Scatter& s = op.s;
+  int64_t total = 1;
+  for (int a = 0; a < s.nd; ++a) total *= s.size[a];
+  const int64_t e = blk * kExecThreads + threadIdx.x;
+  if (e >= total) return;
+  int64_t rem = e, io = 0, oo = 0;
+  for (int a = s.nd - 1; a >= 0; --a) {
+    const int64_t i = rem % s.size[a];
+    rem /= s.size[a];
+    io += i * s.is[a];
+    oo += (s.off[a] + i) * s.os[a];
+  }
+  T* out = (T*)s.out;
+  out[oo] = out[oo] + (T)s.alpha * ((const T*)s.in)[io];
+}
+
+__device__ void dev_eye(const DevOp& op, int64_t blk) {
+  const int64_t n = op.eye_n;
+  const int64_t e = blk * kExecThreads + threadIdx.x;
+  if (e < n * n) ((double*)op.c.out)[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(kExecThreads) level_kernel(const __grid_constant__ LevelBatch lb) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = lb.nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (lb.start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const DevOp& op = lb.ops[lo];
+  const int64_t blk = b - lb.start[lo];
+  switch (op.kind) {
+    case OP_CONTRACT:
+      if (op.tin == ET_F32 && op.tw == ET_F32 && op.tout == ET_F32)
+        dev_contract<float, float, float, float>(op, blk);
+      else if (op.tin == ET_F64 && op.tout == ET_F64 && op.tw == ET_F64)
+        dev_contract<double, double, double, double>(op, blk);
+      else
+        dev_contract<float, double, double, double>(op, blk);
+      break;
+    case OP_MP:
+      if (op.tout == ET_F64) dev_mp<double>(op, blk, dsm);
+      else dev_mp<float>(op, blk, dsm);
+      break;
+    case OP_SCATTER:
+      if (op.tout == ET_F64) dev_scatter<double>(op, blk);
+      else dev_scatter<float>(op, blk);
+      break;
+    case OP_REDUCE:
+      if (op.tout == ET_F64) dev_reduce<double>(op, blk);
+      else dev_reduce<float>(op, blk);
+      break;
+    case OP_EYE:
+      dev_eye(op, blk);
+      break;
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host parts
+// ---------------------------------------------------------------------------
+static bool mp_tiling(Op& op) {
+  const Contract& c = op.c;
+  if (!c.w || c.wsQ != 0 || c.wsJ != 0 || c.NI < 8 || c.NB > 64) return false;
+  if (!(op.tin == op.tw && op.tw == op.tout)) return false;
+  if (op.tout == ET_F64) return false;    // few FP64 units per SM: spread FP64 work thin instead
+  if (c.P * c.Q * c.NB * c.J < 8192) return false;
+  int bg = (int)((c.NB + 3) / 4), p2 = 1;
+  while (p2 < bg) p2 <<= 1;
+  const int cg = std::min(kExecThreads / p2, 64);   // smem kMpKC2*4*(BG+CG)*4 <= 48 KB
+  if (c.J > 4 * cg) return false;
+  op.BG = p2;
+  op.CG = cg;
+  op.CH = (int)(4 * cg / c.J);
+  const int64_t items = c.P * c.Q;
+  op.blocks = ceil_div(items, op.CH);
+  op.kind = OP_MP;
+  return true;
+}
+
+int64_t plan_contract(Op& op) {
+  op.kind = OP_CONTRACT;
+  const Contract& c = op.c;
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+  if (total == 0) {
+    op.blocks = 0;
+    return 0;
+  }
+  if (mp_tiling(op)) return 0;
+  const int64_t want = (int64_t)exec_sms() * 1024;   // threads that keep the GPU busy
+  int g = 1;
+  while (g < 32 && total * g < want && c.NI >= 8 * g) g <<= 1;
+  op.g = g;
+  op.nsplit = 1;
+  op.chunk = c.NI;
+  if (c.NI >= 2048 && total * g < want) {
+    int64_t ns = std::min<int64_t>(ceil_div(want, total * g), c.NI / 512);
+    ns = std::max<int64_t>(1, std::min<int64_t>(ns, 256));
+    op.chunk = ceil_div(c.NI, ns);
+    op.nsplit = (int)ceil_div(c.NI, op.chunk);
+  }
+  op.blocks = ceil_div(total * op.nsplit, kExecThreads / g);
+  return op.nsplit > 1 ? total * op.nsplit : 0;
+}
+
+void plan_simple(Op& op) {
+  int64_t total = 0;
+  if (op.kind == OP_SCATTER) {
+    total = 1;
+    for (int a = 0; a < op.s.nd; ++a) total *= op.s.size[a];
+  } else if (op.kind == OP_EYE) {
+    total = op.eye_n * op.eye_n;
+  } else if (op.kind == OP_REDUCE) {
+    total = op.c.P * op.c.NB * op.c.Q * op.c.J;
+  }
+  op.blocks = ceil_div(total, kExecThreads);
+}
+
+void Program::buffer(const void* p, int64_t bytes, int level) {
+  if (!p || bytes <= 0) return;
+  bufs_.push_back(Buf{(const char*)p, (const char*)p + bytes, level});
+}
+
+int Program::level_of(const void* p) const {
+  if (!p) return 0;
+  const char* c = (const char*)p;
+  int lvl = 0;
+  for (const Buf& b : bufs_)
+    if (c >= b.lo && c < b.hi) lvl = std::max(lvl, b.level);
+  return lvl;
+}
+
+void Program::add(Op op, const void* in1, const void* in2) {
+  const int lvl = 1 + std::max(level_of(in1), level_of(in2));
+  const void* out = op.kind == OP_SCATTER ? op.s.out : op.c.out;
+  if (op.kind == OP_CONTRACT && op.nsplit > 1) {
+    Op part = op;
+    part.level = lvl;
+    ops_.push_back(part);
+    Op red = op;
+    red.kind = OP_REDUCE;
+    red.level = lvl + 1;
+    plan_simple(red);
+    ops_.push_back(red);
+    for (Buf& b : bufs_)
+      if ((const char*)out >= b.lo && (const char*)out < b.hi) b.level = std::max(b.level, lvl + 1);
+    return;
+  }
+  op.level = lvl;
+  ops_.push_back(op);
+  for (Buf& b : bufs_)
+    if ((const char*)out >= b.lo && (const char*)out < b.hi) b.level = std::max(b.level, lvl);
+}
+
+int Program::levels() const {
+  int m = 0;
+  for (const Op& o : ops_) m = std::max(m, o.level);
+  return m;
+}
+
+static DevOp to_dev(const Op& o) {
+  DevOp d;
+  d.kind = o.kind;
+  d.tin = o.tin;
+  d.tw = o.tw;
+  d.tout = o.tout;
+  d.c = o.c;
+  d.s = o.s;
+  d.g = o.g;
+  d.nsplit = o.nsplit;
+  d.chunk = o.chunk;
+  d.partial = o.partial;
+  d.BG = o.BG;
+  d.CG = o.CG;
+  d.CH = o.CH;
+  d.eye_n = o.eye_n;
+  return d;
+}
+
+ttnn_status Program::run(cudaStream_t st) {
+  const int L = levels();
+  for (int lvl = 1; lvl <= L; ++lvl) {
+    LevelBatch lb;
+    lb.nops = 0;
+    lb.start[0] = 0;
+    auto flush = [&]() -> ttnn_status {
+      if (lb.nops == 0) return TTNN_OK;
+      const int64_t blocks = lb.start[lb.nops];
+      if (blocks > 0) {
+        if (blocks >= (int64_t(1) << 31)) {
+          set_error("program level too large");
+          return TTNN_EUNSUPPORTED;
+        }
+        level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(lb);
+        TTNN_TRY(check_launch("level_kernel"));
+      }
+      lb.nops = 0;
+      return TTNN_OK;
+    };
+    for (const Op& o : ops_) {
+      if (o.level != lvl || o.blocks == 0) continue;
+      if (lb.nops == kMaxLevelOps) TTNN_TRY(flush());
+      lb.ops[lb.nops] = to_dev(o);
+      lb.start[lb.nops + 1] = lb.start[lb.nops] + o.blocks;
+      ++lb.nops;
+    }
+    TTNN_TRY(flush());
+  }
+  return TTNN_OK;
+}
+
+}  // namespace ttnn

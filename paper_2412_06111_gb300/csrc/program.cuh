@@ -1,0 +1,84 @@
+// Small-contraction programs: the tree walk of an update and the core
+// assembly of a recovery are recorded as lists of ops with buffer
+// dependencies, grouped by dependency level, and each level runs as one
+// batched launch of a kernel that dispatches per block on the op kind.
+#pragma once
+
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace ttnn {
+
+enum OpKind { OP_CONTRACT = 0, OP_MP = 1, OP_SCATTER = 2, OP_REDUCE = 3, OP_EYE = 4 };
+
+// One recorded op.  Types: tin / tw / tout are ElemType (f32 or f64).
+struct Op {
+  int kind = OP_CONTRACT;
+  int tin = ET_F32, tw = ET_F32, tout = ET_F32;
+  Contract c;
+  Scatter s;
+  // contraction details
+  int g = 1;            // lanes cooperating on one output (power of two <= 32)
+  int nsplit = 1;       // split of the reduction index (partials + OP_REDUCE)
+  int64_t chunk = 0;
+  void* partial = nullptr;
+  int BG = 0, CG = 0, CH = 0;   // OP_MP tiling
+  int64_t eye_n = 0;            // OP_EYE: n x n identity at c.out (f64)
+  int64_t blocks = 0;
+  int level = 0;
+};
+
+// Device-side copy of an op (plain data, fits the kernel parameter space).
+struct DevOp {
+  int kind, tin, tw, tout;
+  Contract c;
+  Scatter s;
+  int g, nsplit;
+  int64_t chunk;
+  void* partial;
+  int BG, CG, CH;
+  int64_t eye_n;
+};
+
+constexpr int kMaxLevelOps = 40;   // ops per batched launch (parameter space)
+
+struct LevelBatch {
+  int nops;
+  int64_t start[kMaxLevelOps + 1];   // prefix sums of blocks
+  DevOp ops[kMaxLevelOps];
+};
+
+class Program {
+ public:
+  // Registers a buffer written by the program (or produced before it, level 0).
+  void buffer(const void* p, int64_t bytes, int level = 0);
+  // Records an op; its level follows the buffers it reads.
+  void add(Op op, const void* in1, const void* in2 = nullptr);
+  // Launches every level in order on `st`.
+  ttnn_status run(cudaStream_t st);
+  void clear() {
+    ops_.clear();
+    bufs_.clear();
+  }
+  size_t size() const { return ops_.size(); }
+  int levels() const;
+
+ private:
+  struct Buf {
+    const char* lo;
+    const char* hi;
+    int level;
+  };
+  int level_of(const void* p) const;
+  std::vector<Op> ops_;
+  std::vector<Buf> bufs_;
+};
+
+// Fills op.g / nsplit / chunk / blocks and the MP tiling for a contraction;
+// returns the number of partial elements (of the output type) it needs.
+int64_t plan_contract(Op& op);
+// blocks of a scatter / eye op
+void plan_simple(Op& op);
+
+}  // namespace ttnn

@@ -3,7 +3,8 @@
 // one-sided Jacobi (Hestenes) with round-robin pair ordering, and the
 // eps-pseudo-inverse R_eps^+ = V_1 Sigma_1^-1 U_1^T keeping sigma > eps,
 // eps = eps_factor * u * sigma_max (Sec. 4 recovery phase and stabilised
-// least squares; eq. (stabilized_nystrom)).  One CTA per node.
+// least squares; eq. (stabilized_nystrom)).  One CTA per node; every step
+// works on all trailing columns at once (one warp per column).
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -11,145 +12,217 @@
 namespace ttnn {
 
 constexpr int kQrThreads = 256;
+constexpr int kQrWarps = kQrThreads / 32;
 constexpr int kMaxSweeps = 60;
 
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < kQrThreads / 32; ++w) t += red[w];
-  __syncthreads();
-  return t;
+  return v;
 }
 
-// dynamic shared memory: A (s x r), W (r x r), V (r x r), v0/vn2 (r), red
+// dynamic shared memory (column-major, leading dimension s for A and Q,
+// r for W and V): A (s x r), Q (s x r), W (r x r), V (r x r), small arrays.
 __global__ void __launch_bounds__(kQrThreads) qr_pinv_kernel(const QrJob* jobs, int state_f64,
                                                              double eps_factor, double u,
                                                              int* kept) {
   extern __shared__ double sm[];
   const QrJob job = jobs[blockIdx.x];
   const int s = job.s, r = job.r;
-  double* A = sm;                       // s x r row-major
-  double* W = A + s * r;                // r x r  (R, then R V)
-  double* V = W + r * r;                // r x r
-  double* vnorm = V + r * r;            // r
-  double* red = vnorm + r;              // 8
+  double* A = sm;                         // A[j * s + i]
+  double* Q = A + kMaxRecoverS * kMaxRecoverR;
+  double* W = Q + kMaxRecoverS * kMaxRecoverR;   // W[k * r + i]: column k of R V
+  double* V = W + kMaxRecoverR * kMaxRecoverR;   // V[k * r + i]
+  double* vn = V + kMaxRecoverR * kMaxRecoverR;  // reflector norms (r)
+  double* rd = vn + kMaxRecoverR;                // diag of R / signs / sigmas (r)
   __shared__ int flag;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  for (int e = tid; e < s * r; e += kQrThreads)
-    A[e] = state_f64 ? ((const double*)job.omega)[e] : (double)((const float*)job.omega)[e];
+  for (int e = tid; e < s * r; e += kQrThreads) {
+    const int i = e / r, j = e % r;      // Omega is row-major (s x r)
+    A[j * s + i] = state_f64 ? ((const double*)job.omega)[e] : (double)((const float*)job.omega)[e];
+  }
   __syncthreads();
 
-  // --- Householder QR: reflector k stored as v = A[k:s, k] (v[0] in place)
+  // ---- Householder QR; reflector k is v = A[k:s, k] with v[0] stored in place
   for (int k = 0; k < r; ++k) {
-    double part = 0.0;
-    for (int i = k + tid; i < s; i += kQrThreads) part += A[i * r + k] * A[i * r + k];
-    const double nrm2 = block_sum(part, red);
-    const double alpha = A[k * r + k];
-    const double nrm = sqrt(nrm2);
-    double beta = 0.0, vn2 = 0.0;
-    if (nrm > 0.0) {
-      beta = alpha > 0.0 ? -nrm : nrm;
-      const double v0 = alpha - beta;
-      vn2 = nrm2 - alpha * alpha + v0 * v0;
+    if (warp == 0) {
+      double part = 0.0;
+      for (int i = k + lane; i < s; i += 32) part += A[k * s + i] * A[k * s + i];
+      const double nrm2 = warp_sum(part);
+      if (lane == 0) {
+        const double alpha = A[k * s + k];
+        const double nrm = sqrt(nrm2);
+        double beta = 0.0, vn2 = 0.0;
+        if (nrm > 0.0) {
+          beta = alpha > 0.0 ? -nrm : nrm;
+          const double v0 = alpha - beta;
+          vn2 = nrm2 - alpha * alpha + v0 * v0;
+          A[k * s + k] = v0;
+        }
+        vn[k] = vn2 > 0.0 ? 2.0 / vn2 : 0.0;   // scale of the reflector, one division
+        rd[k] = beta;
+      }
     }
     __syncthreads();
-    if (tid == 0) {
-      vnorm[k] = vn2;
-      A[k * r + k] = alpha - beta;   // v[0]; R[k][k] = beta kept in W below
-      W[k * r + k] = beta;
-    }
-    __syncthreads();
-    if (vn2 > 0.0) {
-      // apply H = I - 2 v v^T / vn2 to columns j > k
-      for (int j = k + 1; j < r; ++j) {
-        double p = 0.0;
-        for (int i = k + tid; i < s; i += kQrThreads) p += A[i * r + k] * A[i * r + j];
-        const double dot = block_sum(p, red);
-        const double f = 2.0 * dot / vn2;
-        for (int i = k + tid; i < s; i += kQrThreads) A[i * r + j] -= f * A[i * r + k];
-        __syncthreads();
+    const double sc = vn[k];
+    if (sc > 0.0) {
+      for (int j = k + 1 + warp; j < r; j += kQrWarps) {
+        double part = 0.0;
+        for (int i = k + lane; i < s; i += 32) part += A[k * s + i] * A[j * s + i];
+        const double f = warp_sum(part) * sc;
+        for (int i = k + lane; i < s; i += 32) A[j * s + i] -= f * A[k * s + i];
       }
     }
     __syncthreads();
   }
-  // R (upper triangle) into W, with R[k][k] already there
-  for (int e = tid; e < r * r; e += kQrThreads) {
-    const int i = e / r, j = e % r;
-    if (j > i) W[e] = A[i * r + j];
-    else if (j < i) W[e] = 0.0;
-  }
-  __syncthreads();
-  // sign convention diag(R) >= 0: flip rows of R (and columns of Q below)
-  // Q = H_0 ... H_{r-1} [I; 0] formed in global memory (job.q, s x r)
+  // ---- Q = H_0 ... H_{r-1} [I; 0]
   for (int e = tid; e < s * r; e += kQrThreads) {
-    const int i = e / r, j = e % r;
-    job.q[e] = (i == j) ? 1.0 : 0.0;
+    const int j = e / s, i = e % s;
+    Q[j * s + i] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int k = r - 1; k >= 0; --k) {
-    const double vn2 = vnorm[k];
-    if (vn2 > 0.0) {
-      for (int j = 0; j < r; ++j) {
-        double p = 0.0;
-        for (int i = k + tid; i < s; i += kQrThreads) p += A[i * r + k] * job.q[i * r + j];
-        const double dot = block_sum(p, red);
-        const double f = 2.0 * dot / vn2;
-        for (int i = k + tid; i < s; i += kQrThreads) job.q[i * r + j] -= f * A[i * r + k];
-        __syncthreads();
+    const double sc = vn[k];
+    if (sc > 0.0) {
+      for (int j = k + warp; j < r; j += kQrWarps) {   // columns j < k are untouched by H_k
+        double part = 0.0;
+        for (int i = k + lane; i < s; i += 32) part += A[k * s + i] * Q[j * s + i];
+        const double f = warp_sum(part) * sc;
+        for (int i = k + lane; i < s; i += 32) Q[j * s + i] -= f * A[k * s + i];
       }
+    }
+    __syncthreads();
+  }
+  // ---- R (upper triangle) into W, signs so that diag(R) >= 0
+  for (int e = tid; e < r * r; e += kQrThreads) {
+    const int j = e / r, i = e % r;      // W column-major: W[j * r + i] = R[i][j]
+    double v = 0.0;
+    if (i == j) v = rd[i];
+    else if (i < j) v = A[j * s + i];
+    W[e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += kQrThreads) {
+    const int j = e / r, i = e % r;
+    if (rd[i] < 0.0) W[e] = -W[e];               // row i of R
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int e = tid; e < s * r; e += kQrThreads) {
+    const int j = e / s, i = e % s;
+    const double q = rd[j] < 0.0 ? -Q[j * s + i] : Q[j * s + i];   // column j of Q
+    job.q[i * r + j] = q;                          // row-major s x r output
+  }
+  __syncthreads();
+
+  // ---- fast path: R_eps^+ = R^-1 when no singular value can fall below eps.
+  // sigma_min(R) >= 1/||R^-1||_F and ||R||_2 <= ||R||_F, so
+  // 1/||R^-1||_F > 4 * eps_factor * u * ||R||_F certifies sigma_min > eps.
+  // R^-1 (upper triangular) by back substitution, one thread per column.
+  double* X = Q;   // Q was written out above; reuse its storage (r x r, column-major)
+  __shared__ double red2[2 * kQrWarps];
+  __shared__ int singular;
+  if (tid == 0) singular = 0;
+  __syncthreads();
+  for (int i = tid; i < r; i += kQrThreads) {
+    const double dgi = W[i * r + i];
+    if (dgi == 0.0) singular = 1;
+    rd[i] = dgi != 0.0 ? 1.0 / dgi : 0.0;   // reciprocal diagonal (rd: diag no longer needed)
+  }
+  __syncthreads();
+  if (!singular) {
+    for (int j = tid; j < r; j += kQrThreads) {
+      for (int i = 0; i < r; ++i) X[j * r + i] = 0.0;
+      X[j * r + j] = rd[j];
+      for (int i = j - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int k = i + 1; k <= j; ++k) acc += W[k * r + i] * X[j * r + k];
+        X[j * r + i] = -acc * rd[i];
+      }
+    }
+    __syncthreads();
+    double pr = 0.0, px = 0.0;
+    for (int e = tid; e < r * r; e += kQrThreads) {
+      pr += W[e] * W[e];
+      px += X[e] * X[e];
+    }
+    pr = warp_sum(pr);
+    px = warp_sum(px);
+    if (lane == 0) {
+      red2[warp] = pr;
+      red2[kQrWarps + warp] = px;
+    }
+    __syncthreads();
+    double rf2 = 0.0, xf2 = 0.0;
+    for (int w = 0; w < kQrWarps; ++w) {
+      rf2 += red2[w];
+      xf2 += red2[kQrWarps + w];
+    }
+    const double margin = 4.0 * eps_factor * u;
+    if (margin * margin * rf2 * xf2 < 1.0 && xf2 > 0.0) {
+      for (int e = tid; e < r * r; e += kQrThreads) {
+        const int i = e / r, j = e % r;
+        job.rp[e] = X[j * r + i];    // row-major R^-1
+      }
+      if (tid == 0) {
+        kept[blockIdx.x] = r;
+        kept[gridDim.x + blockIdx.x] = 0;   // no Jacobi sweep needed
+      }
+      return;
     }
   }
   __syncthreads();
-  for (int k = tid; k < r; k += kQrThreads) vnorm[k] = (W[k * r + k] < 0.0) ? -1.0 : 1.0;
-  __syncthreads();
-  for (int e = tid; e < r * r; e += kQrThreads) W[e] *= vnorm[e / r];
-  for (int e = tid; e < s * r; e += kQrThreads) job.q[e] *= vnorm[e % r];
-  for (int e = tid; e < r * r; e += kQrThreads) V[e] = (e / r == e % r) ? 1.0 : 0.0;
-  __syncthreads();
 
-  // --- one-sided Jacobi on the columns of W = R: W V = U Sigma
-  const int n2 = r + (r & 1);   // even number of "players" (a dummy column if odd)
-  const int warp = tid >> 5, lane = tid & 31, nwarps = kQrThreads / 32;
-  const double tol = 4.0 * 1.1102230246251565e-16;
+  // ---- one-sided Jacobi on the columns of W = R: W V = U Sigma
+  const int n2 = r + (r & 1);   // even number of players (a dummy column if r is odd)
+  // a rotation is skipped once |gamma| <= sqrt(r) * eps * sqrt(alpha beta):
+  // below this the computed gamma is rounding noise (the one-sided Jacobi
+  // stopping test of Demmel & Veselic with m = r rows)
+  const double tol = sqrt((double)r) * 2.220446049250313e-16;
+  int sweeps = 0;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    sweeps = sweep + 1;
     if (tid == 0) flag = 0;
     __syncthreads();
     for (int round = 0; round < n2 - 1; ++round) {
-      for (int pr = warp; pr < n2 / 2; pr += nwarps) {
+      for (int pr = warp; pr < n2 / 2; pr += kQrWarps) {
         int a, b;
         if (pr == 0) { a = round % (n2 - 1); b = n2 - 1; }
         else { a = (round + pr) % (n2 - 1); b = (round - pr + n2 - 1) % (n2 - 1); }
         if (a > b) { const int t = a; a = b; b = t; }
-        if (b >= r) continue;      // dummy column
+        if (b >= r) continue;
         double al = 0.0, be = 0.0, ga = 0.0;
         for (int i = lane; i < r; i += 32) {
-          const double x = W[i * r + a], y = W[i * r + b];
+          const double x = W[a * r + i], y = W[b * r + i];
           al += x * x;
           be += y * y;
           ga += x * y;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        // the rotation's scalars are evaluated by one lane: FP64 division and
+        // square root are long instruction sequences on this part
+        double c = 1.0, sn = 0.0;
+        int rot = 0;
+        if (lane == 0 && ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          rot = 1;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = 1.0 / sqrt(1.0 + t * t);
+          sn = c * t;
+          flag = 1;
         }
-        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
-        if (lane == 0) flag = 1;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        rot = __shfl_sync(0xffffffffu, rot, 0);
+        if (!rot) continue;
+        c = __shfl_sync(0xffffffffu, c, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
         for (int i = lane; i < r; i += 32) {
-          const double x = W[i * r + a], y = W[i * r + b];
-          W[i * r + a] = c * x - sn * y;
-          W[i * r + b] = sn * x + c * y;
-          const double vx = V[i * r + a], vy = V[i * r + b];
-          V[i * r + a] = c * vx - sn * vy;
-          V[i * r + b] = sn * vx + c * vy;
+          const double x = W[a * r + i], y = W[b * r + i];
+          W[a * r + i] = c * x - sn * y;
+          W[b * r + i] = sn * x + c * y;
+          const double vx = V[a * r + i], vy = V[b * r + i];
+          V[a * r + i] = c * vx - sn * vy;
+          V[b * r + i] = sn * vx + c * vy;
         }
       }
       __syncthreads();
@@ -157,45 +230,43 @@ __global__ void __launch_bounds__(kQrThreads) qr_pinv_kernel(const QrJob* jobs, 
     if (flag == 0) break;
     __syncthreads();
   }
-  __syncthreads();
   // singular values sigma_k = ||W[:, k]||
-  double* sig = vnorm;
-  for (int k = warp; k < r; k += nwarps) {
+  for (int k = warp; k < r; k += kQrWarps) {
     double p = 0.0;
-    for (int i = lane; i < r; i += 32) p += W[i * r + k] * W[i * r + k];
-    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-    if (lane == 0) sig[k] = sqrt(p);
+    for (int i = lane; i < r; i += 32) p += W[k * r + i] * W[k * r + i];
+    p = warp_sum(p);
+    if (lane == 0) rd[k] = sqrt(p);
   }
   __syncthreads();
   double smax = 0.0;
-  for (int k = 0; k < r; ++k) smax = fmax(smax, sig[k]);
+  for (int k = 0; k < r; ++k) smax = fmax(smax, rd[k]);
   const double eps = eps_factor * u * smax;
-  // Rp[i][j] = sum_{kept k} V[i][k] W[j][k] / sigma_k^2
+  // 1 / sigma_k^2 of the kept singular values (0 for the dropped ones)
+  double* inv2 = vn;
+  for (int k = tid; k < r; k += kQrThreads) inv2[k] = rd[k] > eps ? 1.0 / (rd[k] * rd[k]) : 0.0;
+  __syncthreads();
+  // Rp[i][j] = sum_{kept k} V[i][k] W[j][k] / sigma_k^2  (row-major output)
   for (int e = tid; e < r * r; e += kQrThreads) {
     const int i = e / r, j = e % r;
     double acc = 0.0;
-    for (int k = 0; k < r; ++k)
-      if (sig[k] > eps) acc += V[i * r + k] * W[j * r + k] / (sig[k] * sig[k]);
+    for (int k = 0; k < r; ++k) acc += V[k * r + i] * W[k * r + j] * inv2[k];
     job.rp[e] = acc;
   }
   if (tid == 0) {
     int cnt = 0;
-    for (int k = 0; k < r; ++k) cnt += sig[k] > eps;
+    for (int k = 0; k < r; ++k) cnt += rd[k] > eps;
     kept[blockIdx.x] = cnt;
+    kept[gridDim.x + blockIdx.x] = sweeps;   // diagnostic: Jacobi sweeps used
   }
 }
 
 ttnn_status launch_qr_pinv(const QrJob* jobs_dev, int njobs, int state_f64, double eps_factor,
                            double u, int* kept_dev, cudaStream_t st) {
   if (njobs == 0) return TTNN_OK;
-  const size_t smem = (size_t)(kMaxRecoverS * kMaxRecoverR + 2 * kMaxRecoverR * kMaxRecoverR +
-                               kMaxRecoverR + 8) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    TTNN_TRY_CUDA(cudaFuncSetAttribute(qr_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    attr_set = true;
-  }
+  const size_t smem = (size_t)(2 * kMaxRecoverS * kMaxRecoverR + 2 * kMaxRecoverR * kMaxRecoverR +
+                               2 * kMaxRecoverR) * sizeof(double);
+  TTNN_TRY_CUDA(cudaFuncSetAttribute(qr_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
   qr_pinv_kernel<<<njobs, kQrThreads, smem, st>>>(jobs_dev, state_f64, eps_factor, u, kept_dev);
   return check_launch("qr_pinv_kernel");
 }

@@ -252,3 +252,33 @@ def test_tensor_core_pass_matches_oracle_and_simt(case, variant):
     finally:
         tc.close()
         simt.close()
+
+
+@pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
+def test_rank_deficient_recovery_truncates_like_oracle(variant):
+    """True ranks 2 below the target 4 (no noise): Omega_v is rank deficient,
+    the certified R^-1 path must refuse and the Jacobi eps-pseudo-inverse must
+    drop the same directions as the oracle; the tensor is still reproduced."""
+    tr = W.toy_tree()
+    dims = [5, 4, 5, 4, 5, 4]
+    n = len(tr[0])
+    T, _ = W.exact_ttn(tr, dims, [2] * n, 3)
+    run = Run(tr, dims, [4] * n, [3] * n, 9, dtype=api.F64, variant=variant)
+    try:
+        api.ttnn_update_dense(run.state, torch.from_numpy(T).cuda())
+        cores = run.recover()
+        t = _otree(tr, dims, 4, 3)
+        drm = O.Drm(t, 9, "f64", "sttnn" if variant else "ttnn")
+        sk = (O.sketch_ttnn if variant == 0 else OS.sketch_sttnn)(T, t, drm)
+        _, kept = O.recover(t, *sk)
+        truncated = 0
+        for v in t.sketched():
+            nd = run.nodes[v]
+            assert nd["kept_rank"] == kept[v]
+            if kept[v] < nd["r"]:
+                truncated += 1
+                assert nd["jacobi_sweeps"] > 0
+        assert truncated > 0
+        assert rel(O.reconstruct(t, cores), T) <= 1e-10
+    finally:
+        run.close()
