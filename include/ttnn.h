@@ -101,6 +101,9 @@ typedef struct {
 
 #define TTNN_FLAG_NO_SIDE_CACHE 1u  /* do not cache full-size pass DRM blocks */
 #define TTNN_FLAG_SIMT_PASS 2u      /* use the SIMT pass even for BF16 (testing) */
+#define TTNN_FLAG_CLUSTER_REDUCE 4u /* tensor-core pass: sum the column-chunk partials of D1
+                                       across a thread-block cluster (distributed shared
+                                       memory) instead of by the last CTA of each row block */
 
 typedef struct ttnn_plan_s* ttnn_plan_t;
 typedef struct ttnn_state_s* ttnn_state_t;

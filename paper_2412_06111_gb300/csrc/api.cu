@@ -159,7 +159,6 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
       if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
     }
   }
-  P.tc_ok = (P.dtype == TTNN_BF16);
   // workspace: the larger of a whole-tensor update and a recovery
   int64_t need_u = 0, need_r = 0;
   if ((s = run_dense_update(P, nullptr, nullptr, fb, nullptr, 1.0, st, true, &need_u))) return fail(s);

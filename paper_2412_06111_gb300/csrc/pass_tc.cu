@@ -41,7 +41,9 @@ struct Params {
   int64_t nL, nR;
   int C, G, nb, tiles, stages;
   int wRpad, wLpad;
-  float* D1p;      // [C][nb*128][wRpad]
+  int cluster;     // 1: the C chunk CTAs of a row range form a cluster and sum D1 on chip
+  float* D1;       // [nL][wRpad] output
+  float* D1p;      // [C][nb*128][wRpad] chunk partials (C > 1, no cluster)
   float* D2p;      // [G][C*tiles*128][wLpad]
   int* err;
 };
@@ -151,6 +153,55 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// --- thread-block cluster (distributed shared memory) helpers
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+  return out;
+}
+__device__ __forceinline__ void remote_arrive(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
+                                                  volatile int* abort) {
+  if (mbar_try_cluster(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try_cluster(bar, parity)) return true;
+    if (*abort) return false;
+    if (gtimer() - t0 > kTimeoutNs) return false;
+  }
+}
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     pass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBR,
                 const __grid_constant__ CUtensorMap mapBL, const Params p) {
@@ -158,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t bar_full[8], bar_empty[8];
   __shared__ __align__(8) uint64_t bar_blfull[2], bar_blempty[2], bar_d1full[2], bar_d1empty[2];
   __shared__ __align__(8) uint64_t bar_d2full;
+  __shared__ __align__(8) uint64_t bar_ready[2], bar_freed[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -170,6 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t stage_bytes = a_bytes + br_bytes;
   const uint32_t base = smem_u32(smem);
   const uint32_t bl_base = base + S * stage_bytes;
+  const uint32_t part_bytes = (uint32_t)kTileM * p.wRpad * 4;
+  const uint32_t part_base = bl_base + 2 * bl_bytes;          // 2 D1 partial tiles (cluster)
+  float* part_ptr = (float*)(smem + (part_base - base));
+  const uint32_t crank = p.cluster ? cluster_rank() : 0;
 
   const int c = blockIdx.x % p.C, g = blockIdx.x / p.C;
   const int b0 = (int)((int64_t)g * p.nb / p.G), b1 = (int)((int64_t)(g + 1) * p.nb / p.G);
@@ -192,6 +248,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&bar_d1empty[k]), 4);
     }
     mbar_init(smem_u32(&bar_d2full), 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_u32(&bar_ready[k]), 4 * p.C);
+      mbar_init(smem_u32(&bar_freed[k]), 4 * p.C);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -202,6 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   fence_before();
   __syncthreads();
+  if (p.cluster) cluster_sync_all();   // peers' barriers are initialised before any remote arrive
   fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t d1_col = 0, d2_col = 2 * p.wRpad;
@@ -322,22 +383,98 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       fence_after();
       const int64_t row = (int64_t)(b0 + u) * kTileM + r_in;
-      float* dst = p.D1p + ((int64_t)c * p.nb * kTileM + row) * p.wRpad;
+      if (!p.cluster) {
+        // C == 1: D1 directly; C > 1: this chunk's partial, summed in chunk
+        // order by reduce_partials after the kernel (deterministic)
+        float* dst = p.C == 1 ? p.D1 + row * p.wRpad
+                              : p.D1p + ((int64_t)c * p.nb * kTileM + row) * p.wRpad;
+        for (int cg = 0; cg < p.wRpad; cg += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + lane_off + d1_col + buf * p.wRpad + cg, v);
+          tmem_wait_ld();
+          if (row < p.nL) {
+            float4* d4 = reinterpret_cast<float4*>(dst + cg);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                  __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
+        continue;
+      }
+      // cluster: partial tile -> own shared memory, then every CTA sums its
+      // share of the rows over the C partials (fixed order) into D1.
+      if (u >= 2) {
+        ok = mbar_wait_cluster(smem_u32(&bar_freed[buf]), ((u >> 1) - 1) & 1, &abort_flag);
+        if (!ok) break;
+      }
+      float* prow = part_ptr + (buf * kTileM + r_in) * p.wRpad;
       for (int cg = 0; cg < p.wRpad; cg += 16) {
         uint32_t v[16];
         tmem_ld16(tmem + lane_off + d1_col + buf * p.wRpad + cg, v);
         tmem_wait_ld();
-        if (row < p.nL) {
-          float4* d4 = reinterpret_cast<float4*>(dst + cg);
+        float4* d4 = reinterpret_cast<float4*>(prow + cg);
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
-                                __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
-        }
+        for (int k = 0; k < 4; ++k)
+          d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                              __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bar_d1empty[buf]));
+        for (int cc = 0; cc < p.C; ++cc) remote_arrive(mapa(smem_u32(&bar_ready[buf]), cc));
+      }
+      ok = mbar_wait_cluster(smem_u32(&bar_ready[buf]), (u >> 1) & 1, &abort_flag);
+      if (!ok) break;
+      {
+        const int rows_per = kTileM / p.C;
+        const int q4 = p.wRpad / 4;
+        const int et = threadIdx.x - 64;            // 0..127 over the epilogue warps
+        const uint32_t pb = part_base + buf * part_bytes;
+        // up to 4 row-chunks x C sources of remote loads in flight before any add
+        for (int idx0 = et; idx0 < rows_per * q4; idx0 += 4 * 128) {
+          float4 acc[4];
+          uint32_t offs[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int idx = idx0 + k * 128;
+            const int rr = (int)crank * rows_per + idx / q4, c4 = idx % q4;
+            offs[k] = (uint32_t)(rr * p.wRpad + c4 * 4) * 4;
+            acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            if (cc >= p.C) break;
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              v[k] = (idx0 + k * 128 < rows_per * q4) ? ld_cluster_f4(mapa(pb + offs[k], cc))
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              acc[k].x += v[k].x;
+              acc[k].y += v[k].y;
+              acc[k].z += v[k].z;
+              acc[k].w += v[k].w;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int idx = idx0 + k * 128;
+            if (idx >= rows_per * q4) continue;
+            const int rr = (int)crank * rows_per + idx / q4, c4 = idx % q4;
+            const int64_t grow = (int64_t)(b0 + u) * kTileM + rr;
+            if (grow < p.nL) reinterpret_cast<float4*>(p.D1p + grow * p.wRpad)[c4] = acc[k];
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0)
+        for (int cc = 0; cc < p.C; ++cc) remote_arrive(mapa(smem_u32(&bar_freed[buf]), cc));
     }
     if (!ok) {
       abort_flag = 1;
@@ -379,6 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   fence_before();
   __syncthreads();
+  if (p.cluster) cluster_sync_all();
   fence_after();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
@@ -444,7 +582,7 @@ static ttnn_status make_map(CUtensorMap* m, const void* ptr, int64_t inner, int6
 }
 
 struct Geometry {
-  int C, G, nb, tiles, stages, grid;
+  int C, G, nb, tiles, stages, grid, cluster;
   int64_t d1p_elems, d2p_elems;
   size_t smem;
 };
@@ -460,6 +598,28 @@ static int sm_count() {
   return n;
 }
 
+static int max_clusters(int C, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * 64, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, pass_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 static bool geometry(const ttnn_plan_s& P, int64_t nL, int64_t nR, Geometry* g) {
   if (P.wRpad < 16 || P.wLpad < 16 || P.wRpad > 256 || P.wLpad > 256) return false;
   int tiles = (512 - 2 * P.wRpad) / P.wLpad;
@@ -468,19 +628,37 @@ static bool geometry(const ttnn_plan_s& P, int64_t nL, int64_t nR, Geometry* g) 
   if (tiles < 1) return false;
   const int64_t stage_bytes = kTileM * 128 * 2 + (int64_t)P.wRpad * 256;
   const int64_t bl = 2 * (int64_t)P.wLpad * 256;
-  const int stages = (int)std::min<int64_t>(8, (kSmemBudget - 1024 - bl) / stage_bytes);
-  if (stages < 2) return false;
   g->tiles = tiles;
-  g->stages = stages;
   g->C = (int)((nR + tiles * kTileN - 1) / (tiles * kTileN));
   g->nb = (int)((nL + kTileM - 1) / kTileM);
   const int sms = sm_count();
-  g->G = std::max(1, std::min(sms / g->C, g->nb));
-  if (sms < g->C) g->G = 1;
+  // cluster path: C in {2, 4, 8}, D1 partial tiles fit beside >= 3 stages
+  g->cluster = 0;
+  const int64_t parts = 2 * (int64_t)kTileM * P.wRpad * 4;
+  if ((g->C == 2 || g->C == 4 || g->C == 8) && P.wRpad <= 64 && (P.flags & TTNN_FLAG_CLUSTER_REDUCE)) {
+    const int stages = (int)std::min<int64_t>(8, (kSmemBudget - 1024 - bl - parts) / stage_bytes);
+    if (stages >= 3) {
+      const size_t smem = (size_t)(1024 + stages * stage_bytes + bl + parts);
+      const int mc = max_clusters(g->C, smem);
+      if (mc >= 1) {
+        g->cluster = 1;
+        g->stages = stages;
+        g->smem = smem;
+        g->G = std::max(1, std::min(mc, g->nb));
+      }
+    }
+  }
+  if (!g->cluster) {
+    const int stages = (int)std::min<int64_t>(8, (kSmemBudget - 1024 - bl) / stage_bytes);
+    if (stages < 2) return false;
+    g->stages = stages;
+    g->smem = (size_t)(1024 + stages * stage_bytes + bl);
+    g->G = std::max(1, std::min(sms / g->C, g->nb));
+    if (sms < g->C) g->G = 1;
+  }
   g->grid = g->C * g->G;
-  g->d1p_elems = (int64_t)g->C * g->nb * kTileM * P.wRpad;
+  g->d1p_elems = (g->cluster || g->C == 1) ? 0 : (int64_t)g->C * g->nb * kTileM * P.wRpad;
   g->d2p_elems = (int64_t)g->G * g->C * tiles * kTileN * P.wLpad;
-  g->smem = (size_t)(1024 + stages * stage_bytes + bl);
   return true;
 }
 
@@ -533,17 +711,39 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
   prm.stages = g.stages;
   prm.wRpad = P.wRpad;
   prm.wLpad = P.wLpad;
-  prm.D1p = (float*)ws;
-  prm.D2p = prm.D1p + g.d1p_elems;
+  prm.cluster = g.cluster;
+  prm.D1 = (float*)D1;
+  prm.D1p = g.cluster ? (float*)D1 : (float*)ws;
+  prm.D2p = (float*)ws + g.d1p_elems;
+
   prm.err = P.err_dev;
   TTNN_TRY_CUDA(cudaFuncSetAttribute(tc::pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)g.smem));
-  tc::pass_kernel<<<g.grid, tc::kThreads, g.smem, st>>>(mA, mBR, mBL, prm);
-  TTNN_TRY(check_launch("tc pass_kernel"));
+  if (g.cluster) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.grid, 1, 1);
+    cfg.blockDim = dim3(tc::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TTNN_TRY_CUDA(cudaLaunchKernelEx(&cfg, tc::pass_kernel, mA, mBR, mBL, prm));
+    count_launch();
+  } else {
+    tc::pass_kernel<<<g.grid, tc::kThreads, g.smem, st>>>(mA, mBR, mBL, prm);
+    TTNN_TRY(check_launch("tc pass_kernel"));
+  }
   const int sms = tc::sm_count();
-  tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D1p, g.C, (int64_t)g.nb * tc::kTileM * P.wRpad,
-                                               nL, P.wRpad, (float*)D1);
-  TTNN_TRY(check_launch("reduce_partials(D1)"));
+  if (!g.cluster && g.C > 1) {
+    tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D1p, g.C, (int64_t)g.nb * tc::kTileM * P.wRpad,
+                                                 nL, P.wRpad, (float*)D1);
+    TTNN_TRY(check_launch("reduce_partials(D1)"));
+  }
   tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
                                                nR, P.wLpad, (float*)D2);
   TTNN_TRY(check_launch("reduce_partials(D2)"));

@@ -202,6 +202,7 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
   }
   // number formats
   P.walk_f64 = (P.dtype == TTNN_F64);
+  P.tc_ok = (P.dtype == TTNN_BF16);
   switch (P.dtype) {
     case TTNN_F64: P.pass_store = 0; P.round_fmt = RF_F64; break;
     case TTNN_F32: P.pass_store = 1; P.round_fmt = RF_F32; break;
@@ -352,8 +353,10 @@ struct Ws {
     const int64_t o = round_up(top, 256);
     top = o + std::max<int64_t>(bytes, 0);
     peak = std::max(peak, top);
-    char* p = dry ? base : base + o;
-    if (prog && !dry) prog->buffer(p, std::max<int64_t>(bytes, 1));
+    // dry runs hand out offsets from a fake base so that buffer identities
+    // (and therefore the recorded program's levels) match a real run
+    char* p = (dry ? (char*)(uintptr_t)0x100000000ull : base) + o;
+    if (prog) prog->buffer(p, std::max<int64_t>(bytes, 1));
     return p;
   }
   bool ok() const { return dry || top <= cap; }
@@ -476,7 +479,7 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
   op.c = c;
   const int64_t pe = plan_contract(op);
   op.partial = pe ? C.ws.alloc(pe * C.eb) : nullptr;
-  if (!C.dry) C.prog->add(op, in.ptr, W);
+  C.prog->add(op, in.ptr, W);
   *out = o;
   return TTNN_OK;
 }
@@ -542,7 +545,6 @@ static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::ve
   s.in = v.ptr;
   s.out = base;
   s.alpha = alpha;
-  if (C.dry) return TTNN_OK;
   Op op;
   op.kind = OP_SCATTER;
   op.tin = op.tw = op.tout = C.et;
@@ -770,6 +772,9 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   char* D1 = ws.alloc(nL * P.wRpad * eb);
   char* D2 = ws.alloc(nR * P.wLpad * eb);
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
+  // the pass's own temporaries are released right after it and are not
+  // program buffers: keep them out of the dependency registry
+  ws.prog = nullptr;
   const bool use_tc = P.tc_ok && !(P.flags & TTNN_FLAG_SIMT_PASS) &&
                       tc_pass_supported(P, nL, nR) == TTNN_OK;
   if (use_tc) {
@@ -816,6 +821,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       ws.top = mark;
     }
   }
+  ws.prog = &prog;
   // each interval owns its two events (an event is destroyed with its interval)
   prof_push(P, 0, ev0, dry ? nullptr : prof_event(P, st));
   cudaEvent_t ev1 = dry ? nullptr : prof_event(P, st);
@@ -949,6 +955,8 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
   }
   if (!dry) TTNN_TRY(prog.run(st));
+  P.last_walk_ops = (int)prog.size();
+  P.last_walk_levels = prog.levels();
   cudaEvent_t ev2 = dry ? nullptr : prof_event(P, st);
   prof_push(P, 1, ev1, ev2);
   if (peak) *peak = ws.peak;

@@ -70,6 +70,7 @@ struct ttnn_plan_s {
   int64_t core_elems = 0;
   int tc_ok = 0;                // tensor-core pass usable for this plan
   int64_t n_tc_pass = 0, n_simt_pass = 0;
+  int last_walk_ops = 0, last_walk_levels = 0;   // shape of the last update's walk program
   // profiling: event pairs per phase (0 pass, 1 walk, 2 recovery)
   int profile = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[3];

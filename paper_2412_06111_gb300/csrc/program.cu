@@ -25,31 +25,32 @@ static int exec_sms() {
 // ---------------------------------------------------------------------------
 // device parts
 // ---------------------------------------------------------------------------
-template <typename Tin, typename Tw, typename Tout, typename Tacc>
+template <typename Tin, typename Tw, typename Tout, typename Tacc, typename I>
 __device__ void dev_contract(const DevOp& op, int64_t blk) {
   const Contract& c = op.c;
   const int g = op.g;
-  const int64_t total = c.P * c.NB * c.Q * c.J;
-  const int64_t vo = blk * (kExecThreads / g) + threadIdx.x / g;
+  const I J = (I)c.J, Q = (I)c.Q, NB = (I)c.NB;
+  const I total = (I)(c.P * c.NB * c.Q * c.J);
+  const I vo = (I)(blk * (kExecThreads / g)) + (I)(threadIdx.x / g);
   const int lg = threadIdx.x % g;
-  const bool valid = vo < total * op.nsplit;
+  const bool valid = vo < total * (I)op.nsplit;
   Tacc acc = 0;
-  int64_t split = 0, o = 0, p = 0, b = 0, q = 0, j = 0;
+  I split = 0, o = 0, p = 0, b = 0, q = 0, j = 0;
   if (valid) {
     split = vo / total;
     o = vo - split * total;
-    int64_t t = o;
-    j = t % c.J;
-    t /= c.J;
-    q = t % c.Q;
-    t /= c.Q;
-    b = t % c.NB;
-    p = t / c.NB;
-    const int64_t i0 = split * op.chunk;
+    I t = o;
+    j = t % J;
+    t /= J;
+    q = t % Q;
+    t /= Q;
+    b = t % NB;
+    p = t / NB;
+    const int64_t i0 = (int64_t)split * op.chunk;
     const int64_t i1 = min(c.NI, i0 + op.chunk);
-    const Tin* ip = (const Tin*)c.in + p * c.isP + q * c.isQ + j * c.isJ;
+    const Tin* ip = (const Tin*)c.in + (int64_t)p * c.isP + (int64_t)q * c.isQ + (int64_t)j * c.isJ;
     if (c.w) {
-      const Tw* wp = (const Tw*)c.w + b * c.wsB + q * c.wsQ + j * c.wsJ;
+      const Tw* wp = (const Tw*)c.w + (int64_t)b * c.wsB + (int64_t)q * c.wsQ + (int64_t)j * c.wsJ;
 #pragma unroll 4
       for (int64_t i = i0 + lg; i < i1; i += g) acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
     } else {
@@ -60,41 +61,41 @@ __device__ void dev_contract(const DevOp& op, int64_t blk) {
   for (int off = g >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if (valid && lg == 0) {
     if (op.nsplit > 1) {
-      ((Tout*)op.partial)[split * total + o] = (Tout)acc;
+      ((Tout*)op.partial)[(int64_t)split * total + o] = (Tout)acc;
     } else {
       Tout* out = (Tout*)c.out;
-      const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+      const int64_t oi = (int64_t)p * c.osP + (int64_t)b * c.osB + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
       const Tout v = (Tout)((Tacc)c.alpha * acc);
       out[oi] = c.accumulate ? (Tout)(out[oi] + v) : v;
     }
   }
 }
 
-template <typename T>
+template <typename T, typename I>
 __device__ void dev_reduce(const DevOp& op, int64_t blk) {
   const Contract& c = op.c;
-  const int64_t total = c.P * c.NB * c.Q * c.J;
-  const int64_t o = blk * kExecThreads + threadIdx.x;
+  const I total = (I)(c.P * c.NB * c.Q * c.J);
+  const I o = (I)(blk * kExecThreads) + (I)threadIdx.x;
   if (o >= total) return;
   const T* part = (const T*)op.partial;
   T acc = 0;
-  for (int s = 0; s < op.nsplit; ++s) acc += part[s * total + o];
-  int64_t t = o;
-  const int64_t j = t % c.J;
-  t /= c.J;
-  const int64_t q = t % c.Q;
-  t /= c.Q;
-  const int64_t b = t % c.NB;
-  const int64_t p = t / c.NB;
+  for (int s = 0; s < op.nsplit; ++s) acc += part[(int64_t)s * total + o];
+  I t = o;
+  const I j = t % (I)c.J;
+  t /= (I)c.J;
+  const I q = t % (I)c.Q;
+  t /= (I)c.Q;
+  const I b = t % (I)c.NB;
+  const I p = t / (I)c.NB;
   T* out = (T*)c.out;
-  const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+  const int64_t oi = (int64_t)p * c.osP + (int64_t)b * c.osB + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
   const T v = (T)c.alpha * acc;
   out[oi] = c.accumulate ? out[oi] + v : v;
 }
 
 // Mode product as a batched small GEMM over one chunk of CH batch items:
 // out[p,b,q,j] (+)= alpha * sum_i W[i*wsI + b*wsB] * in[p,i,q,j].
-template <typename T>
+template <typename T, typename I>
 __device__ void dev_mp(const DevOp& op, int64_t blk, unsigned char* smem) {
   const Contract& c = op.c;
   const int BG = op.BG, CG = op.CG, CH = op.CH;
@@ -105,17 +106,18 @@ __device__ void dev_mp(const DevOp& op, int64_t blk, unsigned char* smem) {
   const int bg = tid / CG, cg = tid % CG;
   const int J = (int)c.J;
   const int ncol = CH * J;
-  const int64_t items = c.P * c.Q;
-  const int64_t it0 = blk * CH;
+  const I items = (I)(c.P * c.Q);
+  const I Qi = (I)c.Q;
+  const I it0 = (I)(blk * CH);
   // fixed load column of this thread (WC divides the block size)
   const int lcol = tid % WC, lrow0 = tid / WC, lstep = kExecThreads / WC;
   bool lvalid = false;
   int64_t lbase = 0;
   if (lcol < ncol) {
-    const int64_t item = it0 + lcol / J;
+    const I item = it0 + (I)(lcol / J);
     if (item < items) {
-      const int64_t p = item / c.Q, q = item - (item / c.Q) * c.Q;
-      lbase = p * c.isP + q * c.isQ + (int64_t)(lcol % J) * c.isJ;
+      const I p = item / Qi, q = item - p * Qi;
+      lbase = (int64_t)p * c.isP + (int64_t)q * c.isQ + (int64_t)(lcol % J) * c.isJ;
       lvalid = true;
     }
   }
@@ -137,11 +139,20 @@ __device__ void dev_mp(const DevOp& op, int64_t blk, unsigned char* smem) {
     __syncthreads();
     if (bg < BG) {
       for (int ii = 0; ii < kc; ++ii) {
+        // 4 consecutive elements per thread: one vector load each (the column
+        // tile is read conflict-free, the weight tile is a broadcast)
         T a[4], bb[4];
+        if (sizeof(T) == 4) {
+          const float4 av = *reinterpret_cast<const float4*>(&Ws[ii * WB + 4 * bg]);
+          const float4 bv = *reinterpret_cast<const float4*>(&Is[ii * WC + 4 * cg]);
+          a[0] = (T)av.x; a[1] = (T)av.y; a[2] = (T)av.z; a[3] = (T)av.w;
+          bb[0] = (T)bv.x; bb[1] = (T)bv.y; bb[2] = (T)bv.z; bb[3] = (T)bv.w;
+        } else {
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          a[x] = Ws[ii * WB + 4 * bg + x];
-          bb[x] = Is[ii * WC + 4 * cg + x];
+          for (int x = 0; x < 4; ++x) {
+            a[x] = Ws[ii * WB + 4 * bg + x];
+            bb[x] = Is[ii * WC + 4 * cg + x];
+          }
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
@@ -155,33 +166,160 @@ __device__ void dev_mp(const DevOp& op, int64_t blk, unsigned char* smem) {
   for (int y = 0; y < 4; ++y) {
     const int col = 4 * cg + y;
     if (col >= ncol) continue;
-    const int64_t item = it0 + col / J;
+    const I item = it0 + (I)(col / J);
     if (item >= items) continue;
-    const int64_t j = col % J;
-    const int64_t p = item / c.Q, q = item - (item / c.Q) * c.Q;
+    const int j = col % J;
+    const I p = item / Qi, q = item - p * Qi;
     T* out = (T*)c.out;
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       const int b = 4 * bg + x;
       if (b >= c.NB) continue;
-      const int64_t oi = p * c.osP + b * c.osB + q * c.osQ + j * c.osJ;
+      const int64_t oi = (int64_t)p * c.osP + (int64_t)b * c.osB + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
       const T v = (T)c.alpha * acc[x][y];
       out[oi] = c.accumulate ? out[oi] + v : v;
     }
   }
 }
 
-template <typename T>
+// Mode product, weight-stationary: W (NI x NB, NI <= 128, NB <= NBT) sits
+// in shared memory; each thread owns one output column (an (item, j) pair)
+// and all NB outputs of it in registers, streaming its NI inputs.
+// out[p,b,q,j] (+)= alpha * sum_i W[i*wsI + b*wsB] * in[p,i,q,j].
+constexpr int kWsMaxNI = 128;
+
+template <int NBT, typename I>
+__device__ void dev_mpw(const DevOp& op, int64_t blk, unsigned char* smem) {
+  const Contract& c = op.c;
+  float* Ws = (float*)smem;                 // [NI][NBT]
+  const int NI = (int)c.NI, NB = (int)c.NB;
+  const float* w = (const float*)c.w;
+  for (int e = threadIdx.x; e < NI * NBT; e += kExecThreads) {
+    const int i = e / NBT, b = e % NBT;
+    Ws[e] = b < NB ? w[(int64_t)i * c.wsI + (int64_t)b * c.wsB] : 0.f;
+  }
+  __syncthreads();
+  const I J = (I)c.J, Q = (I)c.Q;
+  const I ncols = (I)(c.P * c.Q * c.J);
+  const I col = (I)(blk * kExecThreads) + (I)threadIdx.x;
+  if (col >= ncols) return;
+  const I item = col / J, j = col - item * J;
+  const I p = item / Q, q = item - p * Q;
+  const float* in = (const float*)c.in + (int64_t)p * c.isP + (int64_t)q * c.isQ + (int64_t)j * c.isJ;
+  float acc[NBT];
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) acc[b] = 0.f;
+  int i = 0;
+  for (; i + 4 <= NI; i += 4) {
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = in[(int64_t)(i + u) * c.isI];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4* wr = reinterpret_cast<const float4*>(Ws + (i + u) * NBT);
+#pragma unroll
+      for (int b4 = 0; b4 < NBT / 4; ++b4) {
+        const float4 wv = wr[b4];
+        acc[4 * b4] += wv.x * x[u];
+        acc[4 * b4 + 1] += wv.y * x[u];
+        acc[4 * b4 + 2] += wv.z * x[u];
+        acc[4 * b4 + 3] += wv.w * x[u];
+      }
+    }
+  }
+  for (; i < NI; ++i) {
+    const float x = in[(int64_t)i * c.isI];
+    const float4* wr = reinterpret_cast<const float4*>(Ws + i * NBT);
+#pragma unroll
+    for (int b4 = 0; b4 < NBT / 4; ++b4) {
+      const float4 wv = wr[b4];
+      acc[4 * b4] += wv.x * x;
+      acc[4 * b4 + 1] += wv.y * x;
+      acc[4 * b4 + 2] += wv.z * x;
+      acc[4 * b4 + 3] += wv.w * x;
+    }
+  }
+  float* out = (float*)c.out + (int64_t)p * c.osP + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
+  const float alpha = (float)c.alpha;
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) {
+    if (b < NB) {
+      float* o = out + (int64_t)b * c.osB;
+      *o = c.accumulate ? *o + alpha * acc[b] : alpha * acc[b];
+    }
+  }
+}
+
+// Long reduction of a mode product with few batch items (e.g. Y_t^T G_t over
+// all rows of a node): block (item, split) sums its K slice of
+// out[p,b,q,j] = sum_i W[i*wsI + b*wsB] in[p,i,q,j] through shared-memory
+// tiles (coalesced loads) into partial[split][p][b][q][j].
+constexpr int kKredTile = 64;
+
+__device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
+  const Contract& c = op.c;
+  const int NB = (int)c.NB, J = (int)c.J;
+  const int64_t items = c.P * c.Q;
+  const int64_t item = blk % items;
+  const int64_t split = blk / items;
+  const int64_t p = item / c.Q, q = item % c.Q;
+  const int64_t i0 = split * op.chunk;
+  const int64_t i1 = min(c.NI, i0 + op.chunk);
+  float* Wt = (float*)smem;                    // [kKredTile][NB]
+  float* It = Wt + kKredTile * 64;             // [kKredTile][J]
+  const float* in = (const float*)c.in + p * c.isP + q * c.isQ;
+  const float* w = (const float*)c.w;
+  const int nout = NB * J;
+  float acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+  for (int64_t t0 = i0; t0 < i1; t0 += kKredTile) {
+    const int kc = (int)min((int64_t)kKredTile, i1 - t0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kKredTile * NB; e += kExecThreads) {
+      const int b = e / kKredTile, ii = e % kKredTile;   // consecutive threads: consecutive i
+      Wt[ii * 64 + b] = ii < kc ? w[(t0 + ii) * c.wsI + (int64_t)b * c.wsB] : 0.f;
+    }
+    for (int e = threadIdx.x; e < kKredTile * J; e += kExecThreads) {
+      const int ii = e / J, jj = e % J;                 // consecutive threads: consecutive j
+      It[ii * J + jj] = ii < kc ? in[(t0 + ii) * c.isI + (int64_t)jj * c.isJ] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int o = threadIdx.x + k * kExecThreads;
+      if (o < nout) {
+        const int b = o / J, jj = o % J;
+        float a = acc[k];
+        for (int ii = 0; ii < kc; ++ii) a += Wt[ii * 64 + b] * It[ii * J + jj];
+        acc[k] = a;
+      }
+    }
+  }
+  float* part = (float*)op.partial;
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int o = threadIdx.x + k * kExecThreads;
+    if (o < nout) {
+      const int b = o / J, jj = o % J;
+      part[split * total + ((p * c.NB + b) * c.Q + q) * c.J + jj] = acc[k];
+    }
+  }
+}
+
+template <typename T, typename I>
 __device__ void dev_scatter(const DevOp& op, int64_t blk) {
   const Scatter& s = op.s;
-  int64_t total = 1;
-  for (int a = 0; a < s.nd; ++a) total *= s.size[a];
-  const int64_t e = blk * kExecThreads + threadIdx.x;
+  I total = 1;
+  for (int a = 0; a < s.nd; ++a) total *= (I)s.size[a];
+  const I e = (I)(blk * kExecThreads) + (I)threadIdx.x;
   if (e >= total) return;
-  int64_t rem = e, io = 0, oo = 0;
+  I rem = e;
+  int64_t io = 0, oo = 0;
   for (int a = s.nd - 1; a >= 0; --a) {
-    const int64_t i = rem % s.size[a];
-    rem /= s.size[a];
+    const I i = rem % (I)s.size[a];
+    rem /= (I)s.size[a];
     io += i * s.is[a];
     oo += (s.off[a] + i) * s.os[a];
   }
@@ -195,6 +333,51 @@ __device__ void dev_eye(const DevOp& op, int64_t blk) {
   if (e < n * n) ((double*)op.c.out)[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
 
+template <typename I>
+__device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned char* dsm) {
+  switch (op.kind) {
+    case OP_CONTRACT:
+      if (op.tin == ET_F32 && op.tw == ET_F32 && op.tout == ET_F32)
+        dev_contract<float, float, float, float, I>(op, blk);
+      else if (op.tin == ET_F64 && op.tout == ET_F64 && op.tw == ET_F64)
+        dev_contract<double, double, double, double, I>(op, blk);
+      else
+        dev_contract<float, double, double, double, I>(op, blk);
+      break;
+    case OP_MP:
+      if (op.CG == 0) {   // weight-stationary variant, NBT = op.BG
+        switch (op.BG) {
+          case 8: dev_mpw<8, I>(op, blk, dsm); break;
+          case 16: dev_mpw<16, I>(op, blk, dsm); break;
+          case 32: dev_mpw<32, I>(op, blk, dsm); break;
+          case 48: dev_mpw<48, I>(op, blk, dsm); break;
+          default: dev_mpw<64, I>(op, blk, dsm); break;
+        }
+      } else if (op.tout == ET_F64) {
+        dev_mp<double, I>(op, blk, dsm);
+      } else {
+        dev_mp<float, I>(op, blk, dsm);
+      }
+      break;
+    case OP_SCATTER:
+      if (op.tout == ET_F64) dev_scatter<double, I>(op, blk);
+      else dev_scatter<float, I>(op, blk);
+      break;
+    case OP_REDUCE:
+      if (op.tout == ET_F64) dev_reduce<double, I>(op, blk);
+      else dev_reduce<float, I>(op, blk);
+      break;
+    case OP_EYE:
+      dev_eye(op, blk);
+      break;
+    case OP_KRED:
+      dev_kred(op, blk, dsm);
+      break;
+    default:
+      break;
+  }
+}
+
 __global__ void __launch_bounds__(kExecThreads) level_kernel(const __grid_constant__ LevelBatch lb) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int64_t b = blockIdx.x;
@@ -206,33 +389,8 @@ __global__ void __launch_bounds__(kExecThreads) level_kernel(const __grid_consta
   }
   const DevOp& op = lb.ops[lo];
   const int64_t blk = b - lb.start[lo];
-  switch (op.kind) {
-    case OP_CONTRACT:
-      if (op.tin == ET_F32 && op.tw == ET_F32 && op.tout == ET_F32)
-        dev_contract<float, float, float, float>(op, blk);
-      else if (op.tin == ET_F64 && op.tout == ET_F64 && op.tw == ET_F64)
-        dev_contract<double, double, double, double>(op, blk);
-      else
-        dev_contract<float, double, double, double>(op, blk);
-      break;
-    case OP_MP:
-      if (op.tout == ET_F64) dev_mp<double>(op, blk, dsm);
-      else dev_mp<float>(op, blk, dsm);
-      break;
-    case OP_SCATTER:
-      if (op.tout == ET_F64) dev_scatter<double>(op, blk);
-      else dev_scatter<float>(op, blk);
-      break;
-    case OP_REDUCE:
-      if (op.tout == ET_F64) dev_reduce<double>(op, blk);
-      else dev_reduce<float>(op, blk);
-      break;
-    case OP_EYE:
-      dev_eye(op, blk);
-      break;
-    default:
-      break;
-  }
+  if (op.idx32) dispatch<uint32_t>(op, blk, dsm);
+  else dispatch<int64_t>(op, blk, dsm);
 }
 
 // ---------------------------------------------------------------------------
@@ -244,6 +402,15 @@ static bool mp_tiling(Op& op) {
   if (!(op.tin == op.tw && op.tw == op.tout)) return false;
   if (op.tout == ET_F64) return false;    // few FP64 units per SM: spread FP64 work thin instead
   if (c.P * c.Q * c.NB * c.J < 8192) return false;
+  if (c.NI <= kWsMaxNI) {
+    const int nbt = c.NB <= 8 ? 8 : c.NB <= 16 ? 16 : c.NB <= 32 ? 32 : c.NB <= 48 ? 48 : 64;
+    op.kind = OP_MP;
+    op.BG = nbt;
+    op.CG = 0;
+    op.CH = 0;
+    op.blocks = ceil_div(c.P * c.Q * c.J, kExecThreads);
+    return true;
+  }
   int bg = (int)((c.NB + 3) / 4), p2 = 1;
   while (p2 < bg) p2 <<= 1;
   const int cg = std::min(kExecThreads / p2, 64);   // smem kMpKC2*4*(BG+CG)*4 <= 48 KB
@@ -264,6 +431,19 @@ int64_t plan_contract(Op& op) {
   if (total == 0) {
     op.blocks = 0;
     return 0;
+  }
+  // long reductions with few outputs: split-K through shared-memory tiles
+  if (c.w && c.wsQ == 0 && c.wsJ == 0 && op.tin == ET_F32 && op.tw == ET_F32 &&
+      op.tout == ET_F32 && c.NI >= 2048 && c.NB <= 64 && c.J <= 64 &&
+      c.NB * c.J <= 16 * kExecThreads && c.P * c.Q <= 64) {
+    const int64_t items = c.P * c.Q;
+    const int64_t want = (int64_t)exec_sms() * 4;
+    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, items), c.NI / 256));
+    op.chunk = round_up(ceil_div(c.NI, ns), kKredTile);
+    op.nsplit = (int)ceil_div(c.NI, op.chunk);
+    op.kind = OP_KRED;
+    op.blocks = items * op.nsplit;
+    return total * op.nsplit;
   }
   if (mp_tiling(op)) return 0;
   const int64_t want = (int64_t)exec_sms() * 1024;   // threads that keep the GPU busy
@@ -312,7 +492,7 @@ int Program::level_of(const void* p) const {
 void Program::add(Op op, const void* in1, const void* in2) {
   const int lvl = 1 + std::max(level_of(in1), level_of(in2));
   const void* out = op.kind == OP_SCATTER ? op.s.out : op.c.out;
-  if (op.kind == OP_CONTRACT && op.nsplit > 1) {
+  if ((op.kind == OP_CONTRACT && op.nsplit > 1) || op.kind == OP_KRED) {
     Op part = op;
     part.level = lvl;
     ops_.push_back(part);
@@ -353,6 +533,15 @@ static DevOp to_dev(const Op& o) {
   d.CG = o.CG;
   d.CH = o.CH;
   d.eye_n = o.eye_n;
+  // 32-bit decoding when every extent and count stays below 2^31
+  const int64_t lim = (int64_t(1) << 31) - 1;
+  int64_t m = o.c.P * o.c.NB * o.c.Q * o.c.J * std::max(o.nsplit, 1);
+  int64_t st = 1;
+  for (int a = 0; a < o.s.nd; ++a) st *= std::max<int64_t>(o.s.size[a], 1);
+  m = std::max(m, st);
+  m = std::max(m, o.eye_n * o.eye_n);
+  m = std::max(m, o.blocks * kExecThreads);
+  d.idx32 = m < lim;
   return d;
 }
 

@@ -10,7 +10,7 @@
 
 namespace ttnn {
 
-enum OpKind { OP_CONTRACT = 0, OP_MP = 1, OP_SCATTER = 2, OP_REDUCE = 3, OP_EYE = 4 };
+enum OpKind { OP_CONTRACT = 0, OP_MP = 1, OP_SCATTER = 2, OP_REDUCE = 3, OP_EYE = 4, OP_KRED = 5 };
 
 // One recorded op.  Types: tin / tw / tout are ElemType (f32 or f64).
 struct Op {
@@ -39,6 +39,7 @@ struct DevOp {
   void* partial;
   int BG, CG, CH;
   int64_t eye_n;
+  int idx32;   // every index of the op fits 31 bits: decode with 32-bit math
 };
 
 constexpr int kMaxLevelOps = 40;   // ops per batched launch (parameter space)

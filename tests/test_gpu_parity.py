@@ -223,6 +223,10 @@ TC_CASES = {
     "bin5_512x1600": (W.balanced_binary(5), [8, 8, 8, 40, 40], 5, 3),
     "tt4_4096x24": (W.tensor_train(4), [16, 16, 16, 24], 6, 3),
     "bin4_r20": (W.balanced_binary(4), [16, 16, 32, 32], 20, 10),
+    # four 1024-column chunks: the chunk CTAs form clusters and sum D1 on chip
+    "bin4_64x4096": (W.balanced_binary(4), [8, 8, 64, 64], 6, 4),
+    # three chunks: no cluster shape, partial sums through global memory
+    "bin4_80x2560": (W.balanced_binary(4), [8, 10, 40, 64], 6, 4),
 }
 
 
@@ -282,3 +286,22 @@ def test_rank_deficient_recovery_truncates_like_oracle(variant):
         assert rel(O.reconstruct(t, cores), T) <= 1e-10
     finally:
         run.close()
+
+
+@pytest.mark.parametrize("case", ["bin4_64x4096", "bin5_512x1600"])
+def test_cluster_and_global_partial_sums_are_bitwise_equal(case):
+    """The chunk partials of D1 are summed in the same order on chip (cluster)
+    and by the last CTA of each row block through L2, so the two paths agree
+    bit for bit."""
+    tr, dims, r, p = TC_CASES[case]
+    n = len(tr[0])
+    dev, _ = _dev(W.gaussian(dims, 31), api.BF16)
+    a = Run(tr, dims, [r] * n, [p] * n, 5, dtype=api.BF16)
+    b = Run(tr, dims, [r] * n, [p] * n, 5, dtype=api.BF16, flags=api.FLAG_CLUSTER_REDUCE)
+    try:
+        api.ttnn_update_dense(a.state, dev)
+        api.ttnn_update_dense(b.state, dev)
+        assert np.array_equal(a.state_host(), b.state_host())
+    finally:
+        a.close()
+        b.close()
