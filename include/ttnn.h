@@ -196,6 +196,23 @@ ttnn_status ttnn_update_dense(ttnn_state_t state, const void* data, const int64_
                               const int64_t* extent, const float* tile_scale, double lambda,
                               void* stream);
 
+/* ttnn_update_dense_static -- ttnn_update_dense (same arguments, same
+ * result) for callers that must not allocate device memory while they stream
+ * updates, e.g. callers whose memory comes from their own pool, or who must
+ * not let cudaMalloc / cudaFree synchronise the device mid-stream.  The paper
+ * has no counterpart: this is an interface of this library only.
+ * Its scratch is one fixed block of static device memory of 32 MiB per device
+ * (not the plan's workspace); the call allocates no device memory.
+ * EINVAL (before any work is enqueued) if the update needs more scratch than
+ * that; otherwise as ttnn_update_dense.  The block's address is looked up on
+ * the first call made with a device current: make that call before any stream
+ * capture begins.  Calls that overlap in time (any plan, any stream, any host
+ * thread of the process) share the block and race: serialise them.  No
+ * profiling intervals are recorded. */
+ttnn_status ttnn_update_dense_static(ttnn_state_t state, const void* data, const int64_t* offset,
+                                     const int64_t* extent, const float* tile_scale,
+                                     double lambda, void* stream);
+
 /* ttnn_update_cp -- A5: adds lambda * sum_q w_q a_1q o ... o a_dq (a CP term)
  * to the sketches without forming it.  weights: host [cp_rank];
  * factors: host array of d device pointers, factor mu is n_mu x cp_rank

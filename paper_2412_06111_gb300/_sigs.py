@@ -45,6 +45,8 @@ SIGS = {
     "ttnn_state_save": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
     "ttnn_state_load": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
     "ttnn_update_dense": (c_i32, [c_vp, c_vp, C.POINTER(c_i64), C.POINTER(c_i64), c_vp, c_dbl, c_vp]),
+    "ttnn_update_dense_static": (c_i32, [c_vp, c_vp, C.POINTER(c_i64), C.POINTER(c_i64), c_vp, c_dbl,
+                                         c_vp]),
     "ttnn_update_cp": (c_i32, [c_vp, c_i32, C.POINTER(c_dbl), C.POINTER(c_vp), c_dbl, c_vp]),
     "ttnn_update_ttn": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_i32), c_dbl, c_vp]),
     "ttnn_recover": (c_i32, [c_vp, c_vp, c_vp]),

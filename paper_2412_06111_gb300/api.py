@@ -156,6 +156,17 @@ def ttnn_update_dense(state, data, offset=None, extent=None, tile_scale=None, la
                                     C.c_double(lam), _stream(stream)))
 
 
+def ttnn_update_dense_static(state, data, offset=None, extent=None, tile_scale=None, lam=1.0,
+                             stream=None):
+    """ttnn_update_dense without device allocation: its scratch is a fixed
+    32 MiB block of static device memory (one per device), so concurrent calls
+    race and larger updates raise TtnnError (EINVAL)."""
+    off = None if offset is None else _arr(C.c_int64, offset)
+    ext = None if extent is None else _arr(C.c_int64, extent)
+    _check(_lib().ttnn_update_dense_static(state, _ptr(data), off, ext, _ptr(tile_scale),
+                                           C.c_double(lam), _stream(stream)))
+
+
 def ttnn_update_cp(state, weights, factors, lam=1.0, stream=None):
     """weights: host sequence (cp_rank); factors: list of d f64 CUDA tensors n_mu x cp_rank."""
     fp = _arr(C.c_void_p, [f.data_ptr() for f in factors])
