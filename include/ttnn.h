@@ -101,6 +101,9 @@ typedef struct {
 
 #define TTNN_FLAG_NO_SIDE_CACHE 1u  /* do not cache full-size pass DRM blocks */
 #define TTNN_FLAG_SIMT_PASS 2u      /* use the SIMT pass even for BF16 (testing) */
+#define TTNN_FLAG_STRUCTURED_ONLY 8u /* the plan takes CP / TTN-format updates only: no
+                                         cached pass blocks, no dense-pass workspace
+                                         (ttnn_update_dense returns TTNN_EUNSUPPORTED) */
 #define TTNN_FLAG_CLUSTER_REDUCE 4u /* tensor-core pass: sum the column-chunk partials of D1
                                        across a thread-block cluster (distributed shared
                                        memory) instead of by the last CTA of each row block */
@@ -213,18 +216,32 @@ ttnn_status ttnn_update_dense_static(ttnn_state_t state, const void* data, const
                                      const int64_t* extent, const float* tile_scale,
                                      double lambda, void* stream);
 
-/* ttnn_update_cp -- A5: adds lambda * sum_q w_q a_1q o ... o a_dq (a CP term)
- * to the sketches without forming it.  weights: host [cp_rank];
- * factors: host array of d device pointers, factor mu is n_mu x cp_rank
- * row-major binary64. */
+/* ttnn_update_cp -- A5 [Sec. 4 streaming by linearity; Sec. 7 Khatri-Rao
+ * sketchings]: adds lambda * sum_q w_q a_1q o ... o a_dq (a CP term) to the
+ * sketches without forming it: with x_mu = X_mu^T a_mu, y_mu = Y_mu^T a_mu,
+ * Omega_t[i,j] = sum_q w_q prod_{mu in t} y_muq[i] prod_{mu not in t} x_muq[j],
+ * and Psi likewise (identity children and leaves use the raw factors).
+ * weights: host [cp_rank], finite; factors: host array of d device pointers,
+ * factor mu is n_mu x cp_rank row-major binary64.  Products are binary64 on
+ * the stored DRM factors (no second rounding), added into the state.
+ * Two launches per 16 ranks.  EINVAL: null pointers, cp_rank < 1, non-finite
+ * weights or lambda; EUNSUPPORTED: STTNN plans, order > 16, nodes with more
+ * than 9 children. */
 ttnn_status ttnn_update_cp(ttnn_state_t state, int32_t cp_rank, const double* weights,
                            const double* const* factors, double lambda, void* stream);
 
 /* ttnn_update_ttn -- A8 [Sec. 7 structured sketchings, TTN rounding]: adds
- * lambda * sketch(T_in) for a tensor given in TTN format on the same tree.
+ * lambda * sketch(T_in) for a tensor given in TTN format on the same tree,
+ * by an up sweep (cores against the Khatri-Rao X and Y factors) and a down
+ * sweep (environments E_t), never forming T_in.
  * cores_in: host array (n_nodes) of device pointers to binary64 cores in the
- * core layout above with input ranks ranks_in (host [n_nodes], root ignored);
- * identity leaves of the plan still take an (R_v, n_v) input core. */
+ * core layout above with input ranks ranks_in (host [n_nodes] >= 1, root
+ * ignored); identity leaves of the plan still take an (R_v, n_v) input core.
+ * Computed in the plan's walk type (binary64 for TTNN_F64 plans, binary32
+ * otherwise, cores converted once); the DRM factors are the stored values
+ * and their Khatri-Rao products are not rounded again.  The plan workspace
+ * grows (cudaFree + cudaMalloc, which synchronise the device) when an input
+ * needs more than it holds.  EUNSUPPORTED for STTNN plans. */
 ttnn_status ttnn_update_ttn(ttnn_state_t state, const double* const* cores_in,
                             const int32_t* ranks_in, double lambda, void* stream);
 

@@ -1,4 +1,5 @@
 // C ABI entry points (declared in include/ttnn.h).
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -51,6 +52,17 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->kept_dev);
   cudaFree(P->err_dev);
   delete P;
+}
+
+// Replaces the plan workspace by a larger one (cudaFree / cudaMalloc
+// synchronise the device, so no earlier work still uses the old block).
+static ttnn_status grow_workspace(ttnn_plan_s& P, int64_t bytes) {
+  cudaFree(P.ws);
+  P.ws = nullptr;
+  P.ws_bytes = 0;
+  TTNN_TRY(dev_alloc((void**)&P.ws, bytes));
+  P.ws_bytes = bytes;
+  return TTNN_OK;
 }
 
 static int store_bytes(int store) { return store == 0 ? 8 : store == 1 ? 4 : store == 2 ? 2 : 1; }
@@ -144,7 +156,8 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   for (int m = P.Llo; m < P.Lhi; ++m) nL *= P.dims[m];
   for (int m = P.Rlo; m < P.Rhi; ++m) nR *= P.dims[m];
   const int sb = store_bytes(P.pass_store);
-  if (!(P.flags & TTNN_FLAG_NO_SIDE_CACHE)) {
+  const bool dense = !(P.flags & TTNN_FLAG_STRUCTURED_ONLY);
+  if (dense && !(P.flags & TTNN_FLAG_NO_SIDE_CACHE)) {
     if (P.wR > 0) {
       if ((s = dev_alloc(&P.sideR, (int64_t)P.wRpad * nR * sb)) != TTNN_OK) return fail(s);
       if ((s = make_side(P, fb, 0, P.sideR, nR, st))) return fail(s);
@@ -161,7 +174,8 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   }
   // workspace: the larger of a whole-tensor update and a recovery
   int64_t need_u = 0, need_r = 0;
-  if ((s = run_dense_update(P, nullptr, nullptr, fb, nullptr, 1.0, st, true, &need_u))) return fail(s);
+  if (dense && (s = run_dense_update(P, nullptr, nullptr, fb, nullptr, 1.0, st, true, &need_u)))
+    return fail(s);
   if ((s = run_recover(P, nullptr, nullptr, st, true, &need_r))) return fail(s);
   P.ws_bytes = std::max(need_u, need_r) + 4096;
   if ((s = dev_alloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
@@ -335,22 +349,40 @@ ttnn_status ttnn_update_dense(ttnn_state_t S, const void* data, const int64_t* o
     if (b.off[m] != 0 || b.ext[m] != P.dims[m]) b.full = false;
   }
   TTNN_CHECK_ARG(P.pass_store != 3 || tile_scale, "E4M3 updates need tile scales");
+  if (P.flags & TTNN_FLAG_STRUCTURED_ONLY) {
+    set_error("the plan was made with TTNN_FLAG_STRUCTURED_ONLY: no dense updates");
+    return TTNN_EUNSUPPORTED;
+  }
   return run_dense_update(P, S->acc, data, b, tile_scale, lambda, (cudaStream_t)stream, false,
                           nullptr);
 }
 
 ttnn_status ttnn_update_cp(ttnn_state_t S, int32_t cp_rank, const double* weights,
                            const double* const* factors, double lambda, void* stream) {
-  (void)S; (void)cp_rank; (void)weights; (void)factors; (void)lambda; (void)stream;
-  set_error("CP updates are not implemented yet");
-  return TTNN_EUNSUPPORTED;
+  TTNN_CHECK_ARG(S && weights && factors, "null argument");
+  TTNN_CHECK_ARG(cp_rank >= 1, "cp_rank must be >= 1");
+  ttnn_plan_s& P = *S->plan;
+  for (int mu = 0; mu < P.d; ++mu) TTNN_CHECK_ARG(factors[mu], "null factor %d", mu);
+  for (int q = 0; q < cp_rank; ++q)
+    TTNN_CHECK_ARG(std::isfinite(weights[q]), "non-finite weight %d", q);
+  TTNN_CHECK_ARG(std::isfinite(lambda), "non-finite lambda");
+  return run_cp_update(P, S->acc, cp_rank, weights, factors, lambda, (cudaStream_t)stream);
 }
 
 ttnn_status ttnn_update_ttn(ttnn_state_t S, const double* const* cores_in, const int32_t* ranks_in,
                             double lambda, void* stream) {
-  (void)S; (void)cores_in; (void)ranks_in; (void)lambda; (void)stream;
-  set_error("TTN-format updates are not implemented yet");
-  return TTNN_EUNSUPPORTED;
+  TTNN_CHECK_ARG(S && cores_in && ranks_in, "null argument");
+  ttnn_plan_s& P = *S->plan;
+  for (int v = 0; v < (int)P.nodes.size(); ++v) {
+    TTNN_CHECK_ARG(cores_in[v], "null core %d", v);
+    TTNN_CHECK_ARG(v == P.root || ranks_in[v] >= 1, "input rank of node %d must be >= 1", v);
+  }
+  TTNN_CHECK_ARG(std::isfinite(lambda), "non-finite lambda");
+  const cudaStream_t st = (cudaStream_t)stream;
+  int64_t need = 0;
+  TTNN_TRY(run_ttn_update(P, nullptr, cores_in, ranks_in, lambda, st, true, &need));
+  if (need > P.ws_bytes) TTNN_TRY(grow_workspace(P, need + 4096));
+  return run_ttn_update(P, S->acc, cores_in, ranks_in, lambda, st, false, nullptr);
 }
 
 ttnn_status ttnn_recover(ttnn_state_t S, double* cores, void* stream) {

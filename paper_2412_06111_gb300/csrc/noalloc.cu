@@ -83,6 +83,10 @@ ttnn_status ttnn_update_dense_static(ttnn_state_t S, const void* data, const int
     if (b.off[m] != 0 || b.ext[m] != P.dims[m]) b.full = false;
   }
   TTNN_CHECK_ARG(P.pass_store != 3 || tile_scale, "E4M3 updates need tile scales");
+  if (P.flags & TTNN_FLAG_STRUCTURED_ONLY) {
+    set_error("the plan was made with TTNN_FLAG_STRUCTURED_ONLY: no dense updates");
+    return TTNN_EUNSUPPORTED;
+  }
   const cudaStream_t st = (cudaStream_t)stream;
   // size the scratch of this update by recording it without launching
   int64_t need = 0;

@@ -967,6 +967,245 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   return TTNN_OK;
 }
 
+// ---------------------------------------------------------------------------
+// TTN-format input (Sec. 7, structured sketchings; TTN rounding)
+// ---------------------------------------------------------------------------
+// With Khatri-Rao DRMs every sketch entry of a TTN input is a contraction of
+// its cores with rank-one vectors, formed by two sweeps:
+//   up    UX_t[a, j] = sum_b C_t[a, b_1..b_m] prod_k UX_ck[b_k, j]
+//         (leaf: sum_i C_t[a, i] kr(X_mu, mu in t)[i, j]); UY_t likewise with Y_mu
+//   down  E_ck[b_k, j] = sum C_t[a, b..] E_t[a, j] prod_{k' != k} UX_ck'[b_k', j]
+//         (root: without E_t)
+//   Omega_t = UY_t[:, :s_t]^T E_t[:, :r_t];  Psi_leaf = C_t^T E_t;
+//   Psi_t = C_t x_a E_t x_bk V_ck (V_c = UY_c[:, :s_c], or the raw core C_c of
+//   an identity child);  Psi_root = C_root x_bk V_ck.
+// The DRM factors are the stored (rounded) values; products are taken in
+// the walk type, never rounded to the pass format.
+namespace {
+
+constexpr int kRankAxis = -1000;   // id offset of input-rank axes (AX_SK)
+
+// Weight strides (wsI, wsX) of a two-axis view used as W(i, x), i on axis ki.
+void view_w(const View& w, int ki, int64_t* wsI, int64_t* wsX) {
+  *wsI = vstride(w, ki);
+  *wsX = vstride(w, 1 - ki);
+}
+
+// Position of the column axis (AX_J) in a view, -1 if none.
+int j_axis(const View& v) { return find_ax(v, AX_J, -1); }
+
+}  // namespace
+
+ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores_in,
+                           const int32_t* ranks_in, double lambda, cudaStream_t st, bool dry,
+                           int64_t* peak) {
+  if (P.variant != TTNN_VARIANT_TTNN) {
+    set_error("TTN-format updates take TTNN plans");
+    return TTNN_EUNSUPPORTED;
+  }
+  Box box;
+  box.off.assign(P.d, 0);
+  box.ext = P.dims;
+  box.full = true;
+  Ws ws(P.ws, P.ws_bytes, dry);
+  Program prog;
+  ws.prog = &prog;
+  const int eb = P.walk_f64 ? 8 : 4;
+  Ctx C{P, ws, st, dry, eb, P.walk_f64 ? ET_F64 : ET_F32, box, (const char*)P.facw, nullptr, 0,
+        &prog};
+  const int nn = (int)P.nodes.size();
+  auto R = [&](int v) { return (int64_t)ranks_in[v]; };
+  // input cores in the walk type (binary32 plans: converted copies)
+  std::vector<const char*> core(nn, nullptr);
+  for (int v = 0; v < nn; ++v) {
+    const TNode& nd = P.nodes[v];
+    int64_t el = 1;
+    if (v != P.root) el *= R(v);
+    if (nd.leaf) el *= nd.n;
+    else
+      for (int c : nd.ch) el *= R(c);
+    if (P.walk_f64) {
+      core[v] = (const char*)cores_in[v];
+      prog.buffer(core[v], el * 8);
+    } else {
+      char* b = ws.alloc(el * 4);
+      if (!dry) TTNN_TRY(launch_convert_f64_to_f32(cores_in[v], (float*)b, el, st));
+      core[v] = b;
+    }
+  }
+  auto core_view = [&](int v) {
+    const TNode& nd = P.nodes[v];
+    View w;
+    w.ptr = (char*)core[v];
+    if (v != P.root) w.ax.push_back(Ax{AX_SK, kRankAxis - v, R(v), 0});
+    if (nd.leaf) {
+      w.ax.push_back(Ax{AX_SK, v, nd.n, 0});
+    } else {
+      for (int c : nd.ch) w.ax.push_back(Ax{AX_SK, kRankAxis - c, R(c), 0});
+    }
+    w.ld = w.ax.back().size;
+    return w;
+  };
+  // up sweep: UX_v (R_v x rmax), UY_v (R_v x smax), children before parents
+  std::vector<View> UX(nn), UY(nn);
+  for (int li = (int)P.lex.size() - 1; li >= 0; --li) {
+    const int v = P.lex[li];
+    if (v == P.root) continue;
+    const TNode& nd = P.nodes[v];
+    for (int which = 0; which < 2; ++which) {
+      const int64_t w = which == 0 ? P.rmax : P.smax;
+      View cur = core_view(v);
+      if (nd.leaf) {
+        // the leaf's raw axis as its modes (row-major), then Khatri-Rao
+        View m;
+        m.ptr = cur.ptr;
+        m.ax = {cur.ax[0]};
+        for (int mu = nd.lo; mu < nd.hi; ++mu) m.ax.push_back(Ax{AX_MODE, mu, P.dims[mu], 0});
+        m.ld = m.ax.back().size;
+        cur = m;
+        for (int mu = nd.hi - 1; mu >= nd.lo; --mu) {
+          const int k = find_ax(cur, AX_MODE, mu);
+          const char* F = which == 0 ? facX(C, mu) : facY(C, mu);
+          View nx;
+          if (mu == nd.hi - 1) {
+            Ax nax{AX_J, -1, w, 0};
+            TTNN_TRY(contract_view(C, cur, k, F, w, 1, -1, &nax, &nx));
+          } else {
+            TTNN_TRY(contract_view(C, cur, k, F, w, 1, (int)cur.ax.size() - 1, nullptr, &nx));
+          }
+          cur = nx;
+        }
+      } else {
+        for (int k = (int)nd.ch.size() - 1; k >= 0; --k) {
+          const int c = nd.ch[k];
+          const View& uc = which == 0 ? UX[c] : UY[c];
+          const int ka = find_ax(cur, AX_SK, kRankAxis - c);
+          int64_t wsI, wsX;
+          view_w(uc, 0, &wsI, &wsX);
+          View nx;
+          if (k == (int)nd.ch.size() - 1) {
+            Ax nax{AX_J, -1, w, 0};
+            TTNN_TRY(contract_view(C, cur, ka, uc.ptr, wsI, wsX, -1, &nax, &nx));
+          } else {
+            TTNN_TRY(contract_view(C, cur, ka, uc.ptr, wsI, wsX, (int)cur.ax.size() - 1, nullptr,
+                                   &nx));
+          }
+          cur = nx;
+        }
+      }
+      (which == 0 ? UX[v] : UY[v]) = cur;
+    }
+  }
+  // down sweep: E_c has two axes, the rank axis of c and the column axis.
+  // Every other axis of C_v is contracted; the column axis is created by
+  // the first contraction and each later one shares it (it is either the
+  // last axis, or sits right before c's axis).
+  std::vector<View> E(nn);
+  for (int v : P.lex) {
+    const TNode& nd = P.nodes[v];
+    if (nd.leaf || (v != P.root && nd.rsub == 0)) continue;
+    for (int c : nd.ch) {
+      if (P.nodes[c].rsub == 0) continue;
+      const int bc = kRankAxis - c;
+      auto is_c = [&](const Ax& a) { return a.kind == AX_SK && a.id == bc; };
+      View cur = core_view(v);
+      bool have_j = false;
+      while (!have_j || cur.ax.size() > 2) {
+        const int L = (int)cur.ax.size() - 1;
+        int pick, shared = -1;
+        if (!have_j) {
+          pick = is_c(cur.ax[L]) ? L - 1 : L;
+        } else if (j_axis(cur) == L) {
+          pick = is_c(cur.ax[0]) ? 1 : 0;
+          shared = L;
+        } else {
+          shared = j_axis(cur);   // layout [..., x, j, c]
+          pick = shared - 1;
+        }
+        const int id = cur.ax[pick].id;
+        const View& Wv = id == kRankAxis - v ? E[v] : UX[kRankAxis - id];
+        const int ki = id == kRankAxis - v ? find_ax(E[v], AX_SK, id) : 0;
+        int64_t wsI, wsX;
+        view_w(Wv, ki, &wsI, &wsX);
+        View nx;
+        if (!have_j) {
+          Ax nax{AX_J, -1, P.nodes[c].rsub, 0};
+          TTNN_TRY(contract_view(C, cur, pick, Wv.ptr, wsI, wsX, -1, &nax, &nx));
+          have_j = true;
+        } else {
+          TTNN_TRY(contract_view(C, cur, pick, Wv.ptr, wsI, wsX, shared, nullptr, &nx));
+        }
+        cur = nx;
+      }
+      E[c] = cur;
+    }
+  }
+  // sketches.  V_c: UY_c (first s_c columns) or the raw core of an identity c
+  auto children_y = [&](View cur, const TNode& nd, View* out) -> ttnn_status {
+    for (int k = (int)nd.ch.size() - 1; k >= 0; --k) {
+      const int c = nd.ch[k];
+      const TNode& cn = P.nodes[c];
+      const View Wc = cn.identity ? core_view(c) : UY[c];
+      const int ka = find_ax(cur, AX_SK, kRankAxis - c);
+      int64_t wsI, wsX;
+      view_w(Wc, 0, &wsI, &wsX);
+      Ax nax{AX_SK, c, cn.identity ? cn.n : (int64_t)cn.s, 0};
+      View nx;
+      TTNN_TRY(contract_view(C, cur, ka, Wc.ptr, wsI, wsX, -1, &nax, &nx));
+      cur = nx;
+    }
+    *out = cur;
+    return TTNN_OK;
+  };
+  for (int v : P.lex) {
+    const TNode& nd = P.nodes[v];
+    if (v == P.root) {
+      View cur;
+      TTNN_TRY(children_y(core_view(v), nd, &cur));
+      TTNN_TRY(scatter_into(C, cur, state_at(C, acc, nd.ps_off), psi_strides(C, cur, nd, false),
+                            lambda));
+      continue;
+    }
+    if (!nd.sketched()) continue;
+    const View& Et = E[v];
+    const int ka = find_ax(Et, AX_SK, kRankAxis - v);
+    {  // Omega_t = UY_t[:, :s_t]^T E_t[:, :r_t]
+      View e = Et;
+      e.ax[j_axis(e)].size = nd.r;   // the first or the last axis: strides unchanged
+      int64_t wsI, wsX;
+      view_w(UY[v], 0, &wsI, &wsX);
+      Ax nax{AX_SK, v, nd.s, 0};
+      View om;
+      TTNN_TRY(contract_view(C, e, ka, UY[v].ptr, wsI, wsX, -1, &nax, &om));
+      std::vector<int64_t> os(2);
+      for (int a = 0; a < 2; ++a) os[a] = om.ax[a].kind == AX_J ? 1 : nd.r;
+      TTNN_TRY(scatter_into(C, om, state_at(C, acc, nd.om_off), os, lambda));
+    }
+    {  // Psi_t: C_t's parent rank axis against E_t (new column axis first)
+      int64_t wsI, wsX;
+      view_w(Et, ka, &wsI, &wsX);
+      Ax nax{AX_J, -1, nd.r, 0};
+      View cur;
+      TTNN_TRY(contract_view(C, core_view(v), 0, Et.ptr, wsI, wsX, -1, &nax, &cur));
+      if (nd.leaf) {
+        TTNN_TRY(scatter_into(C, cur, state_at(C, acc, nd.ps_off), {1, (int64_t)nd.r}, lambda));
+      } else {
+        View y;
+        TTNN_TRY(children_y(cur, nd, &y));
+        TTNN_TRY(scatter_into(C, y, state_at(C, acc, nd.ps_off), psi_strides(C, y, nd, true),
+                              lambda));
+      }
+    }
+  }
+  if (!dry) TTNN_TRY(prog.run(st));
+  if (peak) *peak = ws.peak;
+  if (!ws.ok()) {
+    set_error("internal: workspace overflow (%lld > %lld)", (long long)ws.peak, (long long)ws.cap);
+    return TTNN_ENOMEM;
+  }
+  return TTNN_OK;
+}
+
 cudaEvent_t prof_event(ttnn_plan_s& P, cudaStream_t st) {
   if (!P.profile) return nullptr;
   cudaEvent_t e = nullptr;

@@ -98,6 +98,15 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
                              int64_t* peak);
+// CP term update (structured.cu): factors are d device pointers, n_mu x Q
+// row-major binary64; weights host [Q].
+ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weights,
+                          const double* const* factors, double lambda, cudaStream_t st);
+// TTN-format input update (plan.cu): cores_in host array of device binary64
+// cores, ranks_in host [n_nodes].  dry: records only, *peak = workspace bytes.
+ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores_in,
+                           const int32_t* ranks_in, double lambda, cudaStream_t st, bool dry,
+                           int64_t* peak);
 ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
                       cudaStream_t st);
 ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st);

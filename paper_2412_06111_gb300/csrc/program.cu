@@ -1,5 +1,6 @@
 // Batched executor of small-contraction programs (see program.cuh).
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "program.cuh"
@@ -327,6 +328,48 @@ __device__ void dev_scatter(const DevOp& op, int64_t blk) {
   out[oo] = out[oo] + (T)s.alpha * ((const T*)s.in)[io];
 }
 
+__device__ void dev_proj(const DevOp& op, int64_t blk) {
+  const Proj& m = op.pj;
+  const int64_t e = blk * kExecThreads + threadIdx.x;
+  if (e >= (int64_t)m.nq * m.ncols) return;
+  const int q = (int)(e / m.ncols), j = (int)(e % m.ncols);
+  const double* a = m.a + (int64_t)(m.q0 + q) * m.saq;
+  double acc = 0.0;
+  if (!m.F) {
+    acc = a[(int64_t)j * m.sak];
+  } else {
+    const double* F = m.F + j;
+    for (int64_t k = 0; k < m.n; ++k) acc += F[k * m.ldF] * a[k * m.sak];
+  }
+  if (m.has_w) acc *= m.w[q];
+  m.out[(int64_t)q * m.ldo + j] = acc;
+}
+
+__device__ void dev_outer(const DevOp& op, int64_t blk) {
+  const Outer& m = op.ou;
+  int64_t total = 1;
+  for (int a = 0; a < m.A; ++a) total *= m.n[a];
+  const int64_t e = blk * kExecThreads + threadIdx.x;
+  if (e >= total) return;
+  int64_t idx[kOuterAxes];
+  int64_t rem = e, oo = 0;
+  for (int a = m.A - 1; a >= 0; --a) {
+    idx[a] = rem % m.n[a];
+    rem /= m.n[a];
+    oo += idx[a] * m.os[a];
+  }
+  int64_t xo[kOuterVecs];
+  for (int k = 0; k < m.K; ++k) xo[k] = ((idx[m.ax[k]] / m.dv[k]) % m.md[k]) * m.si[k];
+  double acc = 0.0;
+  for (int q = 0; q < m.Q; ++q) {
+    double t = 1.0;
+    for (int k = 0; k < m.K; ++k) t *= m.v[k][(int64_t)q * m.sq[k] + xo[k]];
+    acc += t;
+  }
+  if (m.out_f64) ((double*)m.out)[oo] += m.alpha * acc;
+  else ((float*)m.out)[oo] += (float)(m.alpha * acc);
+}
+
 __device__ void dev_eye(const DevOp& op, int64_t blk) {
   const int64_t n = op.eye_n;
   const int64_t e = blk * kExecThreads + threadIdx.x;
@@ -372,6 +415,12 @@ __device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned 
       break;
     case OP_KRED:
       dev_kred(op, blk, dsm);
+      break;
+    case OP_PROJ:
+      dev_proj(op, blk);
+      break;
+    case OP_OUTER:
+      dev_outer(op, blk);
       break;
     default:
       break;
@@ -471,6 +520,11 @@ void plan_simple(Op& op) {
     total = op.eye_n * op.eye_n;
   } else if (op.kind == OP_REDUCE) {
     total = op.c.P * op.c.NB * op.c.Q * op.c.J;
+  } else if (op.kind == OP_PROJ) {
+    total = (int64_t)op.pj.nq * op.pj.ncols;
+  } else if (op.kind == OP_OUTER) {
+    total = 1;
+    for (int a = 0; a < op.ou.A; ++a) total *= op.ou.n[a];
   }
   op.blocks = ceil_div(total, kExecThreads);
 }
@@ -491,7 +545,10 @@ int Program::level_of(const void* p) const {
 
 void Program::add(Op op, const void* in1, const void* in2) {
   const int lvl = 1 + std::max(level_of(in1), level_of(in2));
-  const void* out = op.kind == OP_SCATTER ? op.s.out : op.c.out;
+  const void* out = op.kind == OP_SCATTER ? op.s.out
+                    : op.kind == OP_PROJ  ? (const void*)op.pj.out
+                    : op.kind == OP_OUTER ? op.ou.out
+                                          : op.c.out;
   if ((op.kind == OP_CONTRACT && op.nsplit > 1) || op.kind == OP_KRED) {
     Op part = op;
     part.level = lvl;
@@ -519,12 +576,15 @@ int Program::levels() const {
 
 static DevOp to_dev(const Op& o) {
   DevOp d;
+  memset(&d, 0, sizeof(d));
   d.kind = o.kind;
   d.tin = o.tin;
   d.tw = o.tw;
   d.tout = o.tout;
   d.c = o.c;
-  d.s = o.s;
+  if (o.kind == OP_PROJ) d.pj = o.pj;
+  else if (o.kind == OP_OUTER) d.ou = o.ou;
+  else d.s = o.s;
   d.g = o.g;
   d.nsplit = o.nsplit;
   d.chunk = o.chunk;
@@ -536,9 +596,11 @@ static DevOp to_dev(const Op& o) {
   // 32-bit decoding when every extent and count stays below 2^31
   const int64_t lim = (int64_t(1) << 31) - 1;
   int64_t m = o.c.P * o.c.NB * o.c.Q * o.c.J * std::max(o.nsplit, 1);
-  int64_t st = 1;
-  for (int a = 0; a < o.s.nd; ++a) st *= std::max<int64_t>(o.s.size[a], 1);
-  m = std::max(m, st);
+  if (o.kind == OP_SCATTER) {
+    int64_t st = 1;
+    for (int a = 0; a < o.s.nd; ++a) st *= std::max<int64_t>(o.s.size[a], 1);
+    m = std::max(m, st);
+  }
   m = std::max(m, o.eye_n * o.eye_n);
   m = std::max(m, o.blocks * kExecThreads);
   d.idx32 = m < lim;

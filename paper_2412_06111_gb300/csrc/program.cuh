@@ -10,7 +10,39 @@
 
 namespace ttnn {
 
-enum OpKind { OP_CONTRACT = 0, OP_MP = 1, OP_SCATTER = 2, OP_REDUCE = 3, OP_EYE = 4, OP_KRED = 5 };
+enum OpKind {
+  OP_CONTRACT = 0, OP_MP = 1, OP_SCATTER = 2, OP_REDUCE = 3, OP_EYE = 4, OP_KRED = 5,
+  OP_PROJ = 6,    // projections of CP factors onto DRM factors (binary64)
+  OP_OUTER = 7    // sums of outer products of vector products into a sketch
+};
+
+// OP_PROJ:  out[q * ldo + j] = w_q * sum_{k < n} F[k * ldF + j] * a[k * sak + (q0 + q) * saq]
+// for q < nq, j < ncols (w_q = 1 when has_w == 0); with F == NULL it copies
+// out[q * ldo + j] = w_q * a[j * sak + (q0 + q) * saq].
+constexpr int kProjQ = 16;
+struct Proj {
+  const double* F;
+  const double* a;
+  double* out;
+  int64_t n;
+  int ldF, ncols, sak, saq, q0, nq, ldo, has_w;
+  double w[kProjQ];
+};
+
+// OP_OUTER:  out[sum_a i_a * os_a] += alpha * sum_{q < Q} prod_k v_k[q * sq_k + x_k * si_k]
+// with x_k = (i_{ax_k} / dv_k) % md_k: vector k is indexed by a digit of
+// output axis ax_k (a Kronecker factor of that axis).
+constexpr int kOuterVecs = 16;
+constexpr int kOuterAxes = 10;
+struct Outer {
+  const double* v[kOuterVecs];
+  int sq[kOuterVecs], si[kOuterVecs], dv[kOuterVecs], md[kOuterVecs];
+  int8_t ax[kOuterVecs];
+  int K, A, Q, out_f64;
+  int64_t n[kOuterAxes], os[kOuterAxes];
+  void* out;
+  double alpha;
+};
 
 // One recorded op.  Types: tin / tw / tout are ElemType (f32 or f64).
 struct Op {
@@ -18,6 +50,8 @@ struct Op {
   int tin = ET_F32, tw = ET_F32, tout = ET_F32;
   Contract c;
   Scatter s;
+  Proj pj;
+  Outer ou;
   // contraction details
   int g = 1;            // lanes cooperating on one output (power of two <= 32)
   int nsplit = 1;       // split of the reduction index (partials + OP_REDUCE)
@@ -33,7 +67,12 @@ struct Op {
 struct DevOp {
   int kind, tin, tw, tout;
   Contract c;
-  Scatter s;
+  union {
+    Scatter s;
+    Proj pj;
+    Outer ou;
+  };
+  DevOp() {}   // filled field by field (after a memset) on the host
   int g, nsplit;
   int64_t chunk;
   void* partial;
@@ -42,9 +81,10 @@ struct DevOp {
   int idx32;   // every index of the op fits 31 bits: decode with 32-bit math
 };
 
-constexpr int kMaxLevelOps = 40;   // ops per batched launch (parameter space)
+constexpr int kMaxLevelOps = 36;   // ops per batched launch (parameter space)
 
 struct LevelBatch {
+  LevelBatch() {}
   int nops;
   int64_t start[kMaxLevelOps + 1];   // prefix sums of blocks
   DevOp ops[kMaxLevelOps];
