@@ -142,8 +142,10 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
-def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
-    """Times `steps` whole-path steps on device-resident data.  Returns a dict."""
+def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=False):
+    """Times `steps` whole-path steps on device-resident data.  Returns a dict.
+    quantize: `data` is binary32 and is first quantised to E4M3 tiles with the
+    plan (timed apart: the producer's step, not the sketch's)."""
     log("form dtype", dtype, "variant", variant)
     tr = W.balanced_binary(D)
     n = len(tr[0])
@@ -151,13 +153,28 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
     plan = api.ttnn_plan_create(tr, dims, [RANK] * n, [OVERSAMPLE] * n, SEED, variant=variant,
                                 sketch_dtype=dtype)
     state = api.ttnn_state_create(plan)
+    scale, quant_ms = None, None
+    if quantize:
+        nl = NMODE ** ((D + 1) // 2)
+        nrt, nct = -(-nl // 128), -(-(data.numel() // nl) // 128)
+        q8 = torch.empty(data.numel(), dtype=torch.uint8, device="cuda")
+        scale = torch.empty(nrt * nct, dtype=torch.float32, device="cuda")
+        api.ttnn_fp8_quantize(plan, data, q8, scale)
+        torch.cuda.synchronize()
+        qa, qb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qa.record()
+        api.ttnn_fp8_quantize(plan, data, q8, scale)
+        qb.record()
+        torch.cuda.synchronize()
+        quant_ms = qa.elapsed_time(qb)
+        data = q8
     ce = api.ttnn_plan_sizes(plan)[2]
     cores = torch.zeros(ce, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     log("plan and state ready")
     for _ in range(warmup):
         api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, data)
+        api.ttnn_update_dense(state, data, tile_scale=scale)
         api.ttnn_recover(state, cores)
     torch.cuda.synchronize()
     log("warm-up done")
@@ -173,7 +190,7 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
     for _ in range(steps):
         t0 = time.perf_counter()
         api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, data)
+        api.ttnn_update_dense(state, data, tile_scale=scale)
         api.ttnn_recover(state, cores)      # synchronises (reads kept ranks)
         lat.append((time.perf_counter() - t0) * 1e3)
     e1.record(stream)
@@ -190,7 +207,8 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data):
     return {"ms_per_step": ms, "launches": launches, "tc_passes": passes[0], "simt_passes": passes[1],
             "pass_ms": prof[0][0] / max(prof[0][1], 1), "walk_ms": prof[1][0] / max(prof[1][1], 1),
             "recover_ms": prof[2][0] / max(prof[2][1], 1),
-            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "quantize_ms": quant_ms}
 
 
 def run_e2e(api, W, dtype, steps, warmup, torch, host):
@@ -311,6 +329,10 @@ def main():
     with Clocks(dev) as clk:
         bf = run_form(api, W, api.BF16, api.VARIANT_TTNN, args.steps, warmup, ws, torch, a16)
     f32 = run_form(api, W, api.F32, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch, a32)
+    x2 = run_form(api, W, api.BF16X2, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch,
+                  a32)
+    f8 = run_form(api, W, api.E4M3, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch,
+                  a32, quantize=True)
     st = run_form(api, W, api.BF16, api.VARIANT_STTNN, max(3, args.steps // 2), warmup, ws, torch, a16)
     host16 = a16.cpu().pin_memory()
     del a32
@@ -341,6 +363,13 @@ def main():
                        "ms_per_step": f32["ms_per_step"], "pass_ms": f32["pass_ms"]},
         "sttnn_bf16": {"value": N * 2 / (st["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",
                        "ms_per_step": st["ms_per_step"], "pass_ms": st["pass_ms"]},
+        "bf16x2_split": {"value": N * 4 / (x2["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",
+                         "ms_per_step": x2["ms_per_step"], "pass_ms": x2["pass_ms"],
+                         "pass_gbs": N * 4 / (x2["pass_ms"] * 1e-3) / 1e9},
+        "fp8_e4m3": {"value": N * 1 / (f8["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",
+                     "ms_per_step": f8["ms_per_step"], "pass_ms": f8["pass_ms"],
+                     "pass_gbs": N * 1 / (f8["pass_ms"] * 1e-3) / 1e9,
+                     "quantize_ms": f8["quantize_ms"]},
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_sample()

@@ -153,7 +153,10 @@ ttnn_status ttnn_philox_gaussian(uint64_t seed, int32_t kind, int32_t ident, int
  * tree, dims (host [d]), ranks and oversample (host [n_nodes]) are read during
  * the call only.  opts may be NULL (TTNN, F32, eps_factor 10, u = 2^-52).
  * EINVAL: invalid tree/sizes (see conventions); EUNSUPPORTED: STTNN whose
- * first root child is an identity leaf; ENOMEM/ECUDA. */
+ * first root child is an identity leaf, or a TTNN_BF16X2 / TTNN_E4M3 plan
+ * whose whole-tensor pass matrix (n_L x n_R) the tensor-core pass does not
+ * take (n_L a multiple of 8; n_R a multiple of 8, or of 16 for E4M3; side
+ * widths of at most 256 columns); ENOMEM/ECUDA. */
 ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* dims,
                              const int32_t* ranks, const int32_t* oversample, uint64_t seed,
                              const ttnn_opts* opts, void* stream, ttnn_plan_t* out);
@@ -191,8 +194,9 @@ ttnn_status ttnn_state_load(ttnn_state_t state, const void* host_buf, size_t byt
  * linearity"]: adds lambda * sketch(H) to the state, where H is zero outside
  * the box offset[mu] <= i_mu < offset[mu] + extent[mu] and equals `data` on
  * it.  data: device, row-major over the extents, in the plan's format
- * (TTNN_BF16X2 plans take binary32; TTNN_E4M3 plans take the E4M3 bytes with
- * `tile_scale` (device, one binary32 per 128x128 tile of the pass matrix, see
+ * (TTNN_BF16X2 plans take binary32 and sketch hi + lo with hi = bf16(x),
+ * lo = bf16(x - hi); TTNN_E4M3 plans take the E4M3 bytes with `tile_scale`
+ * (device, one binary32 per 128x128 tile of the box's pass matrix, see
  * ttnn_fp8_quantize) ).  offset/extent: host [d], NULL = whole tensor.
  * EINVAL: box outside the tensor, empty box, NULL data. */
 ttnn_status ttnn_update_dense(ttnn_state_t state, const void* data, const int64_t* offset,
@@ -266,10 +270,15 @@ ttnn_status ttnn_round(ttnn_plan_t plan, const double* const* cores_in, const in
                        double* cores, void* stream);
 
 /* ttnn_fp8_quantize -- helper for TTNN_E4M3 plans: quantises a binary32
- * dense tensor (device, whole tensor or box extents) to E4M3 bytes (device
- * dst) with one binary32 scale = max|tile| / 448 per 128 x 128 tile of the
- * pass matrix (rows = first-level left modes, columns = the rest); scales
- * (device) has ceil(rows/128) * ceil(cols/128) entries. */
+ * dense tensor (device, whole tensor or box extents; extent host [d] or NULL)
+ * to E4M3 bytes (device dst, same element order) with one binary32 scale per
+ * 128 x 128 tile of the pass matrix (rows = the plan's first-level left modes,
+ * columns = the rest): s = max|tile| / 448 (binary32 division; 1 for an
+ * all-zero tile), q = e4m3(x / s) (binary32 division, nearest-even,
+ * saturating at +-448).  scales (device) is row-major [ceil(rows/128)]
+ * [ceil(cols/128)].  The E4M3 pass sketches the dequantised tiles
+ * bf16(f32(q * s)).  Inputs must be finite.  EINVAL: null pointers, extents
+ * outside 1..n_mu. */
 ttnn_status ttnn_fp8_quantize(ttnn_plan_t plan, const float* src, const int64_t* extent,
                               uint8_t* dst, float* scales, void* stream);
 

@@ -195,6 +195,9 @@ def ttnn_round(plan, cores_in, ranks_in, cores, stream=None):
 
 
 def ttnn_fp8_quantize(plan, src, dst, scales, extent=None, stream=None):
+    """src: f32 CUDA tensor (whole tensor or box extents); dst: uint8 CUDA
+    tensor of the same element count; scales: f32 CUDA tensor with one entry
+    per 128 x 128 tile of the pass matrix."""
     ext = None if extent is None else _arr(C.c_int64, extent)
     _check(_lib().ttnn_fp8_quantize(plan, _ptr(src), ext, _ptr(dst), _ptr(scales), _stream(stream)))
 

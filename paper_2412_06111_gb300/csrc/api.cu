@@ -155,7 +155,7 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   int64_t nL = 1, nR = 1;
   for (int m = P.Llo; m < P.Lhi; ++m) nL *= P.dims[m];
   for (int m = P.Rlo; m < P.Rhi; ++m) nR *= P.dims[m];
-  const int sb = store_bytes(P.pass_store);
+  const int sb = store_bytes(P.side_store);
   const bool dense = !(P.flags & TTNN_FLAG_STRUCTURED_ONLY);
   if (dense && !(P.flags & TTNN_FLAG_NO_SIDE_CACHE)) {
     if (P.wR > 0) {
@@ -415,9 +415,15 @@ ttnn_status ttnn_round(ttnn_plan_t P, const double* const* cores_in, const int32
 
 ttnn_status ttnn_fp8_quantize(ttnn_plan_t P, const float* src, const int64_t* extent, uint8_t* dst,
                               float* scales, void* stream) {
-  (void)P; (void)src; (void)extent; (void)dst; (void)scales; (void)stream;
-  set_error("FP8 quantisation is not implemented yet");
-  return TTNN_EUNSUPPORTED;
+  TTNN_CHECK_ARG(P && src && dst && scales, "null argument");
+  int64_t rows = 1, cols = 1;
+  for (int m = 0; m < P->d; ++m) {
+    const int64_t e = extent ? extent[m] : P->dims[m];
+    TTNN_CHECK_ARG(e >= 1 && e <= P->dims[m], "extent of mode %d outside 1..n", m);
+    if (m >= P->Llo && m < P->Lhi) rows *= e;
+    else cols *= e;
+  }
+  return launch_quantize_fp8(src, rows, cols, dst, scales, (cudaStream_t)stream);
 }
 
 ttnn_status ttnn_profile(ttnn_plan_t P, int32_t enable) {

@@ -19,23 +19,17 @@
 // issuer, warps 2-5 epilogue (TMEM lane quarter = warp % 4).  Every mbarrier
 // wait is bounded by a %globaltimer deadline; on expiry the kernel records
 // an error flag, drains its own copies and MMAs, frees TMEM and returns.
-#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 
-#include "plan.cuh"
+#include "tc_ptx.cuh"
 
 namespace ttnn {
 
 namespace tc {
 
 constexpr int kThreads = 192;
-constexpr int kTileM = 128;           // rows of M per tile (MMA M for D1)
-constexpr int kTileN = 128;           // columns of M per tile (MMA M for D2)
-constexpr int kMaxTiles = 8;          // column tiles per chunk
-constexpr int kSmemBudget = 232448 - 2048;   // 227 KB opt-in minus static shared memory
-constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s per wait
 
 struct Params {
   int64_t nL, nR;
@@ -47,111 +41,6 @@ struct Params {
   float* D2p;      // [G][C*tiles*128][wLpad]
   int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false on timeout or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort) return false;
-    if (gtimer() - t0 > kTimeoutNs) return false;
-  }
-}
-// Bounded wait that ignores the abort flag (used to drain own work).
-__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = gtimer();
-  while (!mbar_try(bar, parity))
-    if (gtimer() - t0 > kTimeoutNs) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                       uint32_t bar, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
-      : "memory");
-}
-
-// tcgen05 shared-memory descriptor: start, leading / stride byte offsets,
-// fixed version bits 46-48 = 0b001, 128-byte swizzle (mode 2, bits 61-63).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor of kind::f16: D f32, A/B bf16, A K- or MN-major,
-// B K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 // --- thread-block cluster (distributed shared memory) helpers
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -523,7 +412,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// D[i][w] = sum_k P[k][i][w] for w < wpad (rows i < rows).
 __global__ void reduce_partials(const float* P, int K, int64_t stride_k, int64_t rows, int wpad,
                                 float* D) {
   const int64_t n4 = rows * wpad / 4;
@@ -559,26 +447,34 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D bf16 map over a row-major (outer x inner) array, 64 x box_outer boxes.
-static ttnn_status make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer,
-                            int box_outer) {
+// 2-D map over a row-major (outer x inner) array of esize-byte elements.
+ttnn_status encode_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize,
+                       int64_t inner, int64_t outer, uint32_t box_inner, uint32_t box_outer,
+                       CUtensorMapSwizzle sw) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled unavailable");
     return TTNN_ECUDA;
   }
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
-  cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
+  cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1u, 1u};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
     return TTNN_ECUDA;
   }
   return TTNN_OK;
+}
+
+// bf16 map with 64 x box_outer boxes, 128-byte swizzle.
+static ttnn_status make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer,
+                            int box_outer) {
+  return encode_map(m, ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, inner, outer, 64u,
+                    (uint32_t)box_outer, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 struct Geometry {
@@ -587,7 +483,7 @@ struct Geometry {
   size_t smem;
 };
 
-static int sm_count() {
+int sm_count() {
   static int n = 0;
   if (!n) {
     int dev = 0;

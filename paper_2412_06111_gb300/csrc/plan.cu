@@ -19,6 +19,12 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
                            const void* sR, int64_t ldR, const void* sL, int64_t ldL, void* D1,
                            void* D2, const float* tile_scale, void* ws, int64_t ws_bytes,
                            cudaStream_t st, bool dry, int64_t* ws_need);
+// BF16X2 / E4M3 tensor-core pass (pass_cvt.cu)
+ttnn_status cvt_pass_supported(const ttnn_plan_s& P, int64_t nL, int64_t nR);
+ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int64_t nR,
+                            const void* sR, int64_t ldR, const void* sL, int64_t ldL, void* D1,
+                            void* D2, const float* tile_scale, void* ws, int64_t ws_bytes,
+                            cudaStream_t st, bool dry, int64_t* ws_need);
 
 // ---------------------------------------------------------------------------
 // plan construction
@@ -202,13 +208,16 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
   }
   // number formats
   P.walk_f64 = (P.dtype == TTNN_F64);
-  P.tc_ok = (P.dtype == TTNN_BF16);
+  P.tc_ok = (P.dtype == TTNN_BF16 || P.dtype == TTNN_BF16X2 || P.dtype == TTNN_E4M3);
+  // BF16X2: binary32 tensor, bfloat16 DRM blocks.  E4M3: E4M3 tensor, DRM
+  // blocks rounded to E4M3 values and stored as bfloat16 (exact) for the
+  // bfloat16 tensor cores that multiply the dequantised tiles.
   switch (P.dtype) {
-    case TTNN_F64: P.pass_store = 0; P.round_fmt = RF_F64; break;
-    case TTNN_F32: P.pass_store = 1; P.round_fmt = RF_F32; break;
-    case TTNN_BF16: P.pass_store = 2; P.round_fmt = RF_BF16; break;
-    case TTNN_E4M3: P.pass_store = 3; P.round_fmt = RF_E4M3; break;
-    default: P.pass_store = 2; P.round_fmt = RF_BF16; break;   // BF16X2: bf16 DRM blocks
+    case TTNN_F64: P.pass_store = 0; P.side_store = 0; P.round_fmt = RF_F64; break;
+    case TTNN_F32: P.pass_store = 1; P.side_store = 1; P.round_fmt = RF_F32; break;
+    case TTNN_BF16: P.pass_store = 2; P.side_store = 2; P.round_fmt = RF_BF16; break;
+    case TTNN_E4M3: P.pass_store = 3; P.side_store = 2; P.round_fmt = RF_E4M3; break;
+    default: P.pass_store = 1; P.side_store = 2; P.round_fmt = RF_BF16; break;   // BF16X2
   }
   // first-level split
   const TNode& R0 = P.nodes[root];
@@ -685,7 +694,7 @@ static void side_spec_common(ttnn_plan_s& P, const Box& box, int lo, int hi, Sid
   s.rmax = P.rmax;
   s.smax = P.smax;
   s.round_fmt = P.round_fmt;
-  s.store = P.pass_store;
+  s.store = P.side_store;
 }
 
 static int store_bytes(int store) { return store == 0 ? 8 : store == 1 ? 4 : store == 2 ? 2 : 1; }
@@ -739,7 +748,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   int64_t nL = 1, nR = 1;
   for (int m = P.Llo; m < P.Lhi; ++m) nL *= box.ext[m];
   for (int m = P.Rlo; m < P.Rhi; ++m) nR *= box.ext[m];
-  const int sb = store_bytes(P.pass_store);
+  const int sb = store_bytes(P.side_store);
   // side blocks of the box
   const void* sR = nullptr;
   const void* sL = nullptr;
@@ -775,17 +784,20 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   // the pass's own temporaries are released right after it and are not
   // program buffers: keep them out of the dependency registry
   ws.prog = nullptr;
+  const bool cvt = P.dtype == TTNN_BF16X2 || P.dtype == TTNN_E4M3;
   const bool use_tc = P.tc_ok && !(P.flags & TTNN_FLAG_SIMT_PASS) &&
-                      tc_pass_supported(P, nL, nR) == TTNN_OK;
+                      (cvt ? cvt_pass_supported(P, nL, nR) : tc_pass_supported(P, nL, nR)) ==
+                          TTNN_OK;
   if (use_tc) {
+    auto launch = cvt ? launch_cvt_pass : launch_tc_pass;
     const int64_t mark = ws.top;
     int64_t need = 0;
-    TTNN_TRY(launch_tc_pass(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, nullptr, 0, st,
-                            true, &need));
+    TTNN_TRY(launch(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, nullptr, 0, st, true,
+                    &need));
     char* tw = ws.alloc(need);
     if (!dry) {
-      TTNN_TRY(launch_tc_pass(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, st,
-                              false, nullptr));
+      TTNN_TRY(launch(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, st, false,
+                      nullptr));
       ++P.n_tc_pass;
     }
     ws.top = mark;

@@ -50,7 +50,8 @@ struct ttnn_plan_s {
   int wR = 0, wL = 0, wRpad = 0, wLpad = 0;
   // number formats
   int walk_f64 = 0;             // tree walk / accumulators in binary64
-  int pass_store = 1;           // storage of the tensor and side blocks: 0 f64 1 f32 2 bf16 3 e4m3
+  int pass_store = 1;           // storage of the tensor: 0 f64 1 f32 2 bf16 3 e4m3
+  int side_store = 1;           // storage of the pass DRM side blocks (same codes)
   int round_fmt = 1;            // DRM rounding (RoundFmt)
   // device memory
   double* fac64 = nullptr;      // X_mu, Y_mu, XT_v (binary64)
@@ -107,6 +108,9 @@ ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weight
 ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores_in,
                            const int32_t* ranks_in, double lambda, cudaStream_t st, bool dry,
                            int64_t* peak);
+// Per-128x128-tile E4M3 quantisation of a binary32 rows x cols matrix (pass_cvt.cu).
+ttnn_status launch_quantize_fp8(const float* src, int64_t rows, int64_t cols, uint8_t* dst,
+                                float* scales, cudaStream_t st);
 ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
                       cudaStream_t st);
 ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st);
