@@ -298,6 +298,71 @@ ttnn_status ttnn_plan_pass_counts(ttnn_plan_t plan, int64_t* tensor_core, int64_
 /* Number of device kernels this library has launched in this process. */
 ttnn_status ttnn_kernel_launches(int64_t* count);
 
+/* ---------------------------------------------------------------------- */
+/* Serving (A11): many resident sketch streams on one GPU.                 */
+/* The paper streams updates into one sketch (Sec. 4, linearity); a server */
+/* keeps many such streams resident and folds a continuous flow of update  */
+/* requests into them.  A worker thread takes batches from a bounded queue */
+/* (at most one request per stream per batch, so each stream applies its   */
+/* requests in submission order), launches every update's first-level pass */
+/* and then the tree walks of the whole batch as one merged program; a     */
+/* stream's sketch is the same, bit for bit, as applying its updates alone  */
+/* with ttnn_update_dense.  All server calls are thread-safe.               */
+/* ---------------------------------------------------------------------- */
+typedef struct ttnn_server_s* ttnn_server_t;
+
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device memory all open streams may hold (plans + states) */
+  int32_t max_batch;         /* requests per batch; <= 0: 64 */
+  int32_t queue_capacity;    /* pending requests; <= 0: 65536 */
+} ttnn_server_opts;
+
+typedef struct {
+  int64_t completed_updates, completed_recoveries, failed, batches;
+  int64_t update_bytes;      /* tensor bytes of the completed updates */
+  double p50_us, p99_us, max_us;  /* request latency: submit -> completion seen by the worker */
+  double seconds;            /* since the last reset */
+  int64_t device_bytes;      /* held by the open streams */
+  int32_t open_streams;
+  int64_t queued;
+} ttnn_server_report;
+
+/* Creates a server on the current device (its own CUDA streams and worker
+ * thread).  EINVAL: budget <= 0; ECUDA / ENOMEM. */
+ttnn_status ttnn_server_create(const ttnn_server_opts* opts, ttnn_server_t* out);
+/* Finishes every queued request, stops the worker and frees all streams. */
+void ttnn_server_destroy(ttnn_server_t server);
+/* Opens a stream: a plan + zeroed state as ttnn_plan_create /
+ * ttnn_state_create (same arguments).  Admission: EBUSY (nothing kept) when
+ * the stream's device memory would take the open streams over the budget. */
+ttnn_status ttnn_server_open(ttnn_server_t server, const ttnn_tree* tree, int32_t d,
+                             const int64_t* dims, const int32_t* ranks,
+                             const int32_t* oversample, uint64_t seed, const ttnn_opts* opts,
+                             int32_t* stream_id);
+/* Closes a stream once its requests are done (waits at most timeout_us:
+ * ETIMEOUT, stream kept) and frees its memory. */
+ttnn_status ttnn_server_close(ttnn_server_t server, int32_t stream_id, int64_t timeout_us);
+/* Queues ttnn_update_dense(stream, data, offset, extent, tile_scale, lambda).
+ * data / tile_scale (device) must stay valid until the ticket is done.
+ * Argument errors as ttnn_update_dense (checked here); EBUSY: queue full. */
+ttnn_status ttnn_server_submit(ttnn_server_t server, int32_t stream_id, const void* data,
+                               const int64_t* offset, const int64_t* extent,
+                               const float* tile_scale, double lambda, uint64_t* ticket);
+/* Queues ttnn_recover of the stream into `cores` (device, core_elems). */
+ttnn_status ttnn_server_recover(ttnn_server_t server, int32_t stream_id, double* cores,
+                                uint64_t* ticket);
+/* Waits at most timeout_us for a ticket: TTNN_OK with *result = the
+ * request's status (a failed request's message via ttnn_last_error), or
+ * ETIMEOUT (ticket still pending; wait again).  A finished ticket is
+ * reported once.  EINVAL: unknown ticket. */
+ttnn_status ttnn_server_wait(ttnn_server_t server, uint64_t ticket, int64_t timeout_us,
+                             ttnn_status* result);
+/* The stream's state (read it only when its tickets are done). */
+ttnn_status ttnn_server_stream_state(ttnn_server_t server, int32_t stream_id,
+                                     ttnn_state_t* state);
+/* Statistics since the last reset (reset != 0 restarts them). */
+ttnn_status ttnn_server_stats(ttnn_server_t server, int32_t reset, ttnn_server_report* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,17 @@ class TtnnNodeInfo(C.Structure):
                 ("jacobi_sweeps", c_i32)]
 
 
+class TtnnServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", c_i64), ("max_batch", c_i32), ("queue_capacity", c_i32)]
+
+
+class TtnnServerReport(C.Structure):
+    _fields_ = [("completed_updates", c_i64), ("completed_recoveries", c_i64), ("failed", c_i64),
+                ("batches", c_i64), ("update_bytes", c_i64), ("p50_us", c_dbl), ("p99_us", c_dbl),
+                ("max_us", c_dbl), ("seconds", c_dbl), ("device_bytes", c_i64),
+                ("open_streams", c_i32), ("queued", c_i64)]
+
+
 SIGS = {
     "ttnn_status_string": (C.c_char_p, [c_i32]),
     "ttnn_last_error": (c_i32, [C.c_char_p, c_sz]),
@@ -57,6 +68,18 @@ SIGS = {
     "ttnn_profile_read": (c_i32, [c_vp, c_i32, C.POINTER(c_dbl), C.POINTER(c_i32)]),
     "ttnn_kernel_launches": (c_i32, [C.POINTER(c_i64)]),
     "ttnn_plan_pass_counts": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
+    "ttnn_server_create": (c_i32, [C.POINTER(TtnnServerOpts), C.POINTER(c_vp)]),
+    "ttnn_server_destroy": (None, [c_vp]),
+    "ttnn_server_open": (c_i32, [c_vp, C.POINTER(TtnnTree), c_i32, C.POINTER(c_i64),
+                                 C.POINTER(c_i32), C.POINTER(c_i32), c_u64, C.POINTER(TtnnOpts),
+                                 C.POINTER(c_i32)]),
+    "ttnn_server_close": (c_i32, [c_vp, c_i32, c_i64]),
+    "ttnn_server_submit": (c_i32, [c_vp, c_i32, c_vp, C.POINTER(c_i64), C.POINTER(c_i64), c_vp,
+                                   c_dbl, C.POINTER(c_u64)]),
+    "ttnn_server_recover": (c_i32, [c_vp, c_i32, c_vp, C.POINTER(c_u64)]),
+    "ttnn_server_wait": (c_i32, [c_vp, c_u64, c_i64, C.POINTER(c_i32)]),
+    "ttnn_server_stream_state": (c_i32, [c_vp, c_i32, C.POINTER(c_vp)]),
+    "ttnn_server_stats": (c_i32, [c_vp, c_i32, C.POINTER(TtnnServerReport)]),
 }
 
 

@@ -7,7 +7,7 @@ There is no fallback: without the compiled library or a GPU the calls fail.
 """
 import ctypes as C
 
-from . import _native
+from . import _native, _sigs
 from ._sigs import TtnnNodeInfo, TtnnOpts, TtnnTree
 
 F64, F32, BF16, E4M3, BF16X2 = 0, 1, 2, 3, 4
@@ -224,3 +224,68 @@ def ttnn_plan_pass_counts(plan):
     a, b = C.c_int64(), C.c_int64()
     _check(_lib().ttnn_plan_pass_counts(plan, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def ttnn_server_create(hbm_budget_bytes, max_batch=0, queue_capacity=0):
+    out = C.c_void_p()
+    opts = _sigs.TtnnServerOpts(int(hbm_budget_bytes), int(max_batch), int(queue_capacity))
+    _check(_lib().ttnn_server_create(C.byref(opts), C.byref(out)))
+    return out
+
+
+def ttnn_server_destroy(server):
+    _lib().ttnn_server_destroy(server)
+
+
+def ttnn_server_open(server, tree, dims, ranks, oversample, seed, variant=VARIANT_TTNN,
+                     sketch_dtype=F32, eps_factor=10.0, unit_roundoff=2.0 ** -52, flags=0):
+    if not isinstance(tree, Tree):
+        tree = Tree(*tree)
+    opts = TtnnOpts(variant, sketch_dtype, eps_factor, unit_roundoff, flags)
+    sid = C.c_int32()
+    _check(_lib().ttnn_server_open(server, C.byref(tree.c), len(dims), _arr(C.c_int64, dims),
+                                   _arr(C.c_int32, ranks), _arr(C.c_int32, oversample),
+                                   C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), C.byref(opts),
+                                   C.byref(sid)))
+    return sid.value
+
+
+def ttnn_server_close(server, stream_id, timeout_us=10_000_000):
+    _check(_lib().ttnn_server_close(server, stream_id, int(timeout_us)))
+
+
+def ttnn_server_submit(server, stream_id, data, offset=None, extent=None, tile_scale=None, lam=1.0):
+    off = None if offset is None else _arr(C.c_int64, offset)
+    ext = None if extent is None else _arr(C.c_int64, extent)
+    t = C.c_uint64()
+    _check(_lib().ttnn_server_submit(server, stream_id, _ptr(data), off, ext, _ptr(tile_scale),
+                                     C.c_double(lam), C.byref(t)))
+    return t.value
+
+
+def ttnn_server_recover(server, stream_id, cores):
+    t = C.c_uint64()
+    _check(_lib().ttnn_server_recover(server, stream_id, _ptr(cores), C.byref(t)))
+    return t.value
+
+
+def ttnn_server_wait(server, ticket, timeout_us=10_000_000):
+    """Returns the request's status (0 = OK); raises TtnnError on ETIMEOUT / EINVAL."""
+    res = C.c_int32()
+    _check(_lib().ttnn_server_wait(server, C.c_uint64(ticket), int(timeout_us), C.byref(res)))
+    return res.value
+
+
+def ttnn_server_stream_state(server, stream_id):
+    out = C.c_void_p()
+    _check(_lib().ttnn_server_stream_state(server, stream_id, C.byref(out)))
+    return out
+
+
+def ttnn_server_stats(server, reset=False):
+    rep = _sigs.TtnnServerReport()
+    _check(_lib().ttnn_server_stats(server, 1 if reset else 0, C.byref(rep)))
+    return {k: getattr(rep, k) for k, _ in _sigs.TtnnServerReport._fields_}

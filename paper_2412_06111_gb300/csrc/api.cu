@@ -58,10 +58,12 @@ static void free_plan(ttnn_plan_s* P) {
 // synchronise the device, so no earlier work still uses the old block).
 static ttnn_status grow_workspace(ttnn_plan_s& P, int64_t bytes) {
   cudaFree(P.ws);
+  P.dev_bytes -= P.ws_bytes;
   P.ws = nullptr;
   P.ws_bytes = 0;
   TTNN_TRY(dev_alloc((void**)&P.ws, bytes));
   P.ws_bytes = bytes;
+  P.dev_bytes += bytes;
   return TTNN_OK;
 }
 
@@ -124,6 +126,11 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
     return TTNN_ENOMEM;
   }
   ttnn_plan_s& P = *hold;
+  auto palloc = [&P](void** ptr, int64_t bytes) {
+    const ttnn_status r = dev_alloc(ptr, bytes);
+    if (r == TTNN_OK && bytes > 0) P.dev_bytes += bytes;
+    return r;
+  };
   ttnn_opts def{TTNN_VARIANT_TTNN, TTNN_F32, 10.0, 2.220446049250313e-16, 0};
   TTNN_TRY(build_plan(P, tree, d, dims, ranks, oversample, seed, opts ? opts : &def));
   cudaStream_t st = (cudaStream_t)stream;
@@ -134,7 +141,7 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
     return e;
   };
   // DRM factors (binary64 master, walk-type copy)
-  if ((s = dev_alloc((void**)&P.fac64, P.fac_elems * 8)) != TTNN_OK) return fail(s);
+  if ((s = palloc((void**)&P.fac64, P.fac_elems * 8)) != TTNN_OK) return fail(s);
   for (int m = 0; m < P.d; ++m) {
     if ((s = launch_philox(seed, 1, m, P.dims[m], P.rmax, P.round_fmt, P.fac64 + P.x_off[m], st))) return fail(s);
     if ((s = launch_philox(seed, 2, m, P.dims[m], P.smax, P.round_fmt, P.fac64 + P.y_off[m], st))) return fail(s);
@@ -147,7 +154,7 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   if (P.walk_f64) {
     P.facw = P.fac64;
   } else {
-    if ((s = dev_alloc(&P.facw, P.fac_elems * 4)) != TTNN_OK) return fail(s);
+    if ((s = palloc(&P.facw, P.fac_elems * 4)) != TTNN_OK) return fail(s);
     if ((s = launch_convert_f64_to_f32(P.fac64, (float*)P.facw, P.fac_elems, st))) return fail(s);
   }
   // cached full-size pass blocks
@@ -159,29 +166,37 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   const bool dense = !(P.flags & TTNN_FLAG_STRUCTURED_ONLY);
   if (dense && !(P.flags & TTNN_FLAG_NO_SIDE_CACHE)) {
     if (P.wR > 0) {
-      if ((s = dev_alloc(&P.sideR, (int64_t)P.wRpad * nR * sb)) != TTNN_OK) return fail(s);
+      if ((s = palloc(&P.sideR, (int64_t)P.wRpad * nR * sb)) != TTNN_OK) return fail(s);
       if ((s = make_side(P, fb, 0, P.sideR, nR, st))) return fail(s);
     }
     if (P.wL > 0) {
-      if ((s = dev_alloc(&P.sideL, (int64_t)P.wLpad * nL * sb)) != TTNN_OK) return fail(s);
+      if ((s = palloc(&P.sideL, (int64_t)P.wLpad * nL * sb)) != TTNN_OK) return fail(s);
       if ((s = make_side(P, fb, 1, P.sideL, nL, st))) return fail(s);
     }
     const TNode& yc = P.nodes[P.ychild];
     if (!yc.identity) {
-      if ((s = dev_alloc(&P.yW, (int64_t)yc.s * yc.n * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
+      if ((s = palloc(&P.yW, (int64_t)yc.s * yc.n * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
       if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
     }
   }
-  // workspace: the larger of a whole-tensor update and a recovery
+  // workspace: the larger of a whole-tensor update (cached DRM blocks), an
+  // update of a box as large as the tensor (blocks generated into the
+  // workspace: bounds every box update) and a recovery
   int64_t need_u = 0, need_r = 0;
-  if (dense && (s = run_dense_update(P, nullptr, nullptr, fb, nullptr, 1.0, st, true, &need_u)))
-    return fail(s);
+  if (dense) {
+    if ((s = dense_update_need(P, fb, &need_u))) return fail(s);
+    Box bb = fb;
+    bb.full = false;
+    int64_t need_b = 0;
+    if ((s = dense_update_need(P, bb, &need_b))) return fail(s);
+    need_u = std::max(need_u, need_b);
+  }
   if ((s = run_recover(P, nullptr, nullptr, st, true, &need_r))) return fail(s);
   P.ws_bytes = std::max(need_u, need_r) + 4096;
-  if ((s = dev_alloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
-  if ((s = dev_alloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
-  if ((s = dev_alloc((void**)&P.kept_dev, 2 * std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
-  if ((s = dev_alloc((void**)&P.err_dev, sizeof(int))) != TTNN_OK) return fail(s);
+  if ((s = palloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
+  if ((s = palloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
+  if ((s = palloc((void**)&P.kept_dev, 2 * std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
+  if ((s = palloc((void**)&P.err_dev, sizeof(int))) != TTNN_OK) return fail(s);
   if ((s = launch_fill_zero(P.err_dev, sizeof(int), st)) != TTNN_OK) return fail(s);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -353,6 +368,9 @@ ttnn_status ttnn_update_dense(ttnn_state_t S, const void* data, const int64_t* o
     set_error("the plan was made with TTNN_FLAG_STRUCTURED_ONLY: no dense updates");
     return TTNN_EUNSUPPORTED;
   }
+  int64_t need = 0;
+  TTNN_TRY(dense_update_need(P, b, &need));
+  if (need > P.ws_bytes) TTNN_TRY(grow_workspace(P, need + 4096));
   return run_dense_update(P, S->acc, data, b, tile_scale, lambda, (cudaStream_t)stream, false,
                           nullptr);
 }

@@ -736,9 +736,33 @@ ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, 
   return launch_side(s, out, st);
 }
 
+ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need) {
+  std::vector<int64_t> key = box.ext;
+  key.push_back(box.full ? 1 : 0);
+  auto it = P.ws_need_cache.find(key);
+  if (it != P.ws_need_cache.end()) {
+    *need = it->second;
+    return TTNN_OK;
+  }
+  int64_t n = 0;
+  TTNN_TRY(run_dense_update(P, nullptr, nullptr, box, nullptr, 1.0, nullptr, true, &n));
+  P.ws_need_cache[key] = n;
+  *need = n;
+  return TTNN_OK;
+}
+
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
-                             int64_t* peak) {
+                             int64_t* peak, Program* merge) {
+  if (!dry) {
+    int64_t need = 0;
+    TTNN_TRY(dense_update_need(P, box, &need));
+    if (need > P.ws_bytes) {
+      set_error("dense update needs %lld workspace bytes, the plan holds %lld", (long long)need,
+                (long long)P.ws_bytes);
+      return TTNN_ENOMEM;
+    }
+  }
   Ws ws(P.ws, P.ws_bytes, dry);
   Program prog;
   ws.prog = &prog;
@@ -966,7 +990,10 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     os.back() = rest;
     TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
   }
-  if (!dry) TTNN_TRY(prog.run(st));
+  if (!dry) {
+    if (merge) merge->absorb(prog);
+    else TTNN_TRY(prog.run(st));
+  }
   P.last_walk_ops = (int)prog.size();
   P.last_walk_levels = prog.levels();
   cudaEvent_t ev2 = dry ? nullptr : prof_event(P, st);

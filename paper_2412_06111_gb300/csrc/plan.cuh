@@ -2,10 +2,12 @@
 #pragma once
 
 #include <array>
+#include <map>
 #include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "program.cuh"
 
 struct TNode {
   int user = -1, lex = -1, level = 0, parent = -1, pos = 0;
@@ -63,6 +65,9 @@ struct ttnn_plan_s {
   void* yW = nullptr;           // walk-type copy of the pass Y block (full box)
   char* ws = nullptr;
   int64_t ws_bytes = 0;
+  int64_t dev_bytes = 0;        // device memory the plan holds (all its allocations)
+  // workspace bytes a dense update needs, by box extents (+ whole-tensor flag)
+  std::map<std::vector<int64_t>, int64_t> ws_need_cache;
   ttnn::QrJob* jobs_dev = nullptr;
   int* kept_dev = nullptr;
   int* err_dev = nullptr;       // device error word of bounded waits (tensor-core pass)
@@ -96,9 +101,15 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
 
 // Runs (or, with dry = true, sizes) one dense update.  Returns the peak
 // workspace bytes through *peak when dry.
+// Workspace bytes a dense update of `box` needs (dry run, cached per shape).
+ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need);
+// A real (non-dry) update first checks its workspace need against the plan's
+// workspace and returns TTNN_ENOMEM, launching nothing, when it does not fit.
+// merge != NULL: the tree-walk program is appended to *merge instead of run
+// (the caller runs it; the pass has been launched already).
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
-                             int64_t* peak);
+                             int64_t* peak, ttnn::Program* merge = nullptr);
 // CP term update (structured.cu): factors are d device pointers, n_mu x Q
 // row-major binary64; weights host [Q].
 ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weights,

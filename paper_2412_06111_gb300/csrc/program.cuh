@@ -102,6 +102,9 @@ class Program {
     ops_.clear();
     bufs_.clear();
   }
+  // Appends another program's ops (levels kept): programs over disjoint
+  // buffers then share their level launches.
+  void absorb(const Program& o) { ops_.insert(ops_.end(), o.ops_.begin(), o.ops_.end()); }
   size_t size() const { return ops_.size(); }
   int levels() const;
 

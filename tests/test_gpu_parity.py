@@ -305,3 +305,24 @@ def test_cluster_and_global_partial_sums_are_bitwise_equal(case):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_near_full_box_update(case):
+    """A box one index short of the tensor on one mode generates its DRM
+    blocks into the workspace (the cached whole-tensor blocks do not apply):
+    the plan's workspace must hold it; the sketch matches the oracle."""
+    tr, dims, r, p = CASES[case]
+    n = len(tr[0])
+    off = [0] * len(dims)
+    ext = list(dims)
+    off[-1], ext[-1] = 1, dims[-1] - 1
+    B = W.gaussian(ext, 41)
+    run = Run(tr, dims, [r] * n, [p] * n, 12, dtype=api.F64)
+    try:
+        api.ttnn_update_dense(run.state, torch.from_numpy(np.ascontiguousarray(B)).cuda(), off, ext)
+        t = _otree(tr, dims, r, p)
+        _compare_sketches(run, t, W.embed_box(dims, off, ext, B), O.Drm(t, 12, "f64"),
+                          api.VARIANT_TTNN, 1e-12)
+    finally:
+        run.close()
