@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -244,6 +246,146 @@ def run_e2e(api, W, dtype, steps, warmup, torch, host):
     return ms, host.numel() * host.element_size(), ce * 8
 
 
+def run_streaming(api, W, torch, n_updates=4096, n_lat=256):
+    """Streamed order-6 workload: 32^6 caterpillar (tensor train, identity
+    single-mode leaves), r = 16, s = 24, BF16 plan; each update is one rank-2
+    CP term (N(0,1) factors, binary64) plus one 32^3 box of N(0, 0.01) noise
+    on 3 uniformly chosen modes (the others fixed at uniform indices).
+    Throughput over n_updates back to back; latency over n_lat synchronised
+    updates.  Inputs resident on the device."""
+    d, n = 6, 32
+    tr = W.tensor_train(d)
+    nn = len(tr[0])
+    dims = [n] * d
+    plan = api.ttnn_plan_create(tr, dims, [16] * nn, [8] * nn, SEED + 3, sketch_dtype=api.BF16)
+    state = api.ttnn_state_create(plan)
+    g = torch.Generator(device="cuda").manual_seed(1003)
+    facs = torch.randn(n_updates, d, n, 2, dtype=torch.float64, device="cuda", generator=g)
+    boxes = (torch.randn(n_updates, n * n * n, device="cuda", generator=g) * 0.1).to(torch.bfloat16)
+    rng = np.random.default_rng(1003)
+    geo = []
+    for _ in range(n_updates):
+        modes = sorted(rng.choice(d, size=3, replace=False).tolist())
+        off = [int(rng.integers(0, n)) for _ in range(d)]
+        ext = [1] * d
+        for mu in modes:
+            ext[mu], off[mu] = n, 0
+        geo.append((off, ext))
+    flist = [[facs[i, mu] for mu in range(d)] for i in range(n_updates)]
+
+    def one(i):
+        api.ttnn_update_cp(state, [1.0, 1.0], flist[i])
+        off, ext = geo[i]
+        api.ttnn_update_dense(state, boxes[i], off, ext)
+
+    for i in range(16):
+        one(i)
+    torch.cuda.synchronize()
+    l0 = api.ttnn_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for i in range(n_updates):
+        one(i)
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    launches = api.ttnn_kernel_launches() - l0
+    lat = []
+    for i in range(n_lat):
+        t1 = time.perf_counter()
+        one(i)
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t1) * 1e6)
+    lat.sort()
+    cores = torch.zeros(api.ttnn_plan_sizes(plan)[2], dtype=torch.float64, device="cuda")
+    r0 = time.perf_counter()
+    api.ttnn_recover(state, cores)
+    rec_ms = (time.perf_counter() - r0) * 1e3
+    api.ttnn_state_destroy(state)
+    api.ttnn_plan_destroy(plan)
+    upd_bytes = n * n * n * 2 + d * n * 2 * 8
+    return {"workload": "32^6 tensor train r=16 s=24 BF16; update = rank-2 CP + 32^3 box",
+            "updates": n_updates, "updates_per_s": n_updates / (ms * 1e-3),
+            "host_wall_updates_per_s": n_updates / wall,
+            "update_gbs": n_updates * upd_bytes / (ms * 1e-3) / 1e9,
+            "launches_per_update": launches / n_updates,
+            "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "recover_ms": rec_ms}
+
+
+def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
+    """Serving mix: n_streams resident BF16 streams of mixed order, sizes,
+    trees and ranks (workloads.serving_stream_spec; streams whose device
+    footprint exceeds 512 MiB are redrawn), fed a Poisson stream of N(0,1)
+    slices (one mode fixed at a uniform index) at `rate`/s for `seconds`."""
+    rng = np.random.default_rng(1004)
+    srv = api.ttnn_server_create(160 << 30, max_batch=64)
+    sids, dims_of = [], []
+    t_open = time.perf_counter()
+    tries = 0
+    while len(sids) < n_streams and tries < 20 * n_streams:
+        tries += 1
+        sp = W.serving_stream_spec(rng)
+        nn = len(sp["tree"][0])
+        before = api.ttnn_server_stats(srv)["device_bytes"]
+        try:
+            sid = api.ttnn_server_open(srv, sp["tree"], sp["dims"], [sp["r"]] * nn, [sp["p"]] * nn,
+                                       SEED + len(sids), sketch_dtype=api.BF16)
+        except api.TtnnError:
+            continue
+        if api.ttnn_server_stats(srv)["device_bytes"] - before > (512 << 20):
+            api.ttnn_server_close(srv, sid)
+            continue
+        sids.append(sid)
+        dims_of.append(sp["dims"])
+    open_s = time.perf_counter() - t_open
+    n_streams = len(sids)
+    max_slice = max(int(np.prod(dm)) // min(dm) for dm in dims_of)
+    buf = torch.randn(max_slice, device="cuda").to(torch.bfloat16)
+    arrivals = W.poisson_slices(rng, n_streams, dims_of, rate, seconds)
+    tickets = []
+    # warm-up: one slice per stream
+    for j, sid in enumerate(sids):
+        ext = list(dims_of[j])
+        ext[0] = 1
+        tickets.append(api.ttnn_server_submit(srv, sid, buf, None, ext))
+    for t in tickets:
+        api.ttnn_server_wait(srv, t, 60_000_000)
+    api.ttnn_server_stats(srv, reset=True)
+    tickets = []
+    late = 0
+    t0 = time.perf_counter()
+    for (ta, s, mu, idx) in arrivals:
+        while True:
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+        if now - ta > 1e-3:
+            late += 1
+        dm = dims_of[s]
+        off = [0] * len(dm)
+        ext = list(dm)
+        off[mu], ext[mu] = idx, 1
+        tickets.append(api.ttnn_server_submit(srv, sids[s], buf, off, ext))
+    failed = 0
+    for t in tickets:
+        failed += api.ttnn_server_wait(srv, t, 120_000_000) != 0
+    wall = time.perf_counter() - t0
+    rep = api.ttnn_server_stats(srv)
+    dev_bytes = rep["device_bytes"]
+    api.ttnn_server_destroy(srv)
+    return {"workload": f"{n_streams} streams (d 3-6, n in 16..128, binary/TT/Tucker, r 4-32, "
+                        f"p=r/2, BF16), Poisson slices at {rate:.0f}/s for {seconds:.0f} s",
+            "offered_per_s": len(arrivals) / seconds, "completed": rep["completed_updates"],
+            "completed_per_s": rep["completed_updates"] / wall, "failed": failed + rep["failed"],
+            "update_gbs": rep["update_bytes"] / wall / 1e9,
+            "latency_us": {"p50": rep["p50_us"], "p99": rep["p99_us"], "max": rep["max_us"]},
+            "batches": rep["batches"], "late_submits": late, "open_s": open_s,
+            "device_gb": dev_bytes / 1e9}
+
+
 def cpu_oracle_sample(max_seconds=25.0):
     """The FP64 oracle (as it stands) on a bounded sample of the workload: the
     same tree/ranks on a 16 x 64^4 slab (a quarter) of the tensor."""
@@ -289,6 +431,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave out the streamed-update and serving-mix legs (extra keys)")
     ap.add_argument("--nmode", type=int, default=NMODE, help="mode size (64 = the stated workload)")
     args = ap.parse_args()
     NMODE = args.nmode
@@ -371,6 +515,11 @@ def main():
                      "pass_gbs": N * 1 / (f8["pass_ms"] * 1e-3) / 1e9,
                      "quantize_ms": f8["quantize_ms"]},
     }
+    if rank == 0 and not args.no_serving:
+        log("streaming leg")
+        out["streaming"] = run_streaming(api, W, torch)
+        log("serving leg")
+        out["serving"] = run_serving(api, W, torch)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_sample()
     if rank == 0:

@@ -274,3 +274,39 @@ def rounding_input(tree, dims, r_dom, r_noise, seed, dom_scale=100.0):
                 C[tuple(slice(0, r_dom) for _ in shape)] *= dom_scale
         cores[v] = C
     return cores
+
+
+# ---------------------------------------------------------------------------
+# Serving mix (many resident streams, Poisson slice updates)
+# ---------------------------------------------------------------------------
+def serving_stream_spec(rng, max_entries=2e8):
+    """One stream of the serving mix: order d ~ U{3..6}; mode sizes drawn from
+    {16, 32, 64, 128}, each redrawn while the tensor has more than
+    `max_entries` entries; tree ~ U{balanced binary, tensor train, Tucker};
+    rank r ~ U{4..32} on every node, oversampling p = r // 2."""
+    d = int(rng.integers(3, 7))
+    dims = []
+    for _ in range(d):
+        while True:
+            n = int(rng.choice([16, 32, 64, 128]))
+            if np.prod(dims + [n]) * 16 ** (d - len(dims) - 1) <= max_entries:
+                break
+        dims.append(n)
+    kind = ["binary", "tt", "tucker"][int(rng.integers(0, 3))]
+    tree = {"binary": balanced_binary, "tt": tensor_train, "tucker": tucker}[kind](d)
+    r = int(rng.integers(4, 33))
+    return {"kind": kind, "tree": tree, "dims": dims, "r": r, "p": r // 2}
+
+
+def poisson_slices(rng, n_streams, dims_of, rate, seconds):
+    """Arrival times (s) of a Poisson stream of slice updates at `rate`/s for
+    `seconds`; each picks a stream uniformly, a mode uniformly and an index of
+    that mode uniformly.  Returns a list of (t, stream, mode, index)."""
+    out, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= seconds:
+            return out
+        s = int(rng.integers(0, n_streams))
+        mu = int(rng.integers(0, len(dims_of[s])))
+        out.append((t, s, mu, int(rng.integers(0, dims_of[s][mu]))))
