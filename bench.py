@@ -321,7 +321,7 @@ def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
     footprint exceeds 512 MiB are redrawn), fed a Poisson stream of N(0,1)
     slices (one mode fixed at a uniform index) at `rate`/s for `seconds`."""
     rng = np.random.default_rng(1004)
-    srv = api.ttnn_server_create(160 << 30, max_batch=64)
+    srv = api.ttnn_server_create(160 << 30, max_batch=64, workers=8)
     sids, dims_of = [], []
     t_open = time.perf_counter()
     tries = 0
@@ -369,9 +369,13 @@ def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
         ext = list(dm)
         off[mu], ext[mu] = idx, 1
         tickets.append(api.ttnn_server_submit(srv, sids[s], buf, off, ext))
-    failed = 0
+    failed, errors = 0, {}
     for t in tickets:
-        failed += api.ttnn_server_wait(srv, t, 120_000_000) != 0
+        st = api.ttnn_server_wait(srv, t, 120_000_000)
+        if st != 0:
+            failed += 1
+            key = f"{st}: {api.last_error_message()}"
+            errors[key] = errors.get(key, 0) + 1
     wall = time.perf_counter() - t0
     rep = api.ttnn_server_stats(srv)
     dev_bytes = rep["device_bytes"]
@@ -383,6 +387,7 @@ def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
             "update_gbs": rep["update_bytes"] / wall / 1e9,
             "latency_us": {"p50": rep["p50_us"], "p99": rep["p99_us"], "max": rep["max_us"]},
             "batches": rep["batches"], "late_submits": late, "open_s": open_s,
+            "worker_host_s": rep["worker_host_s"], "wall_s": wall, "errors": errors,
             "device_gb": dev_bytes / 1e9}
 
 

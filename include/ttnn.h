@@ -302,12 +302,14 @@ ttnn_status ttnn_kernel_launches(int64_t* count);
 /* Serving (A11): many resident sketch streams on one GPU.                 */
 /* The paper streams updates into one sketch (Sec. 4, linearity); a server */
 /* keeps many such streams resident and folds a continuous flow of update  */
-/* requests into them.  A worker thread takes batches from a bounded queue */
-/* (at most one request per stream per batch, so each stream applies its   */
-/* requests in submission order), launches every update's first-level pass */
-/* and then the tree walks of the whole batch as one merged program; a     */
-/* stream's sketch is the same, bit for bit, as applying its updates alone  */
-/* with ttnn_update_dense.  All server calls are thread-safe.               */
+/* requests into them.  Worker threads, each with its own CUDA stream and  */
+/* queue (stream k is served by worker k % workers), take batches (at most  */
+/* one request per stream per batch, so each stream applies its requests   */
+/* in submission order), launch every update's first-level pass and then   */
+/* the tree walks of the whole batch as one merged program; completion is  */
+/* tracked with CUDA events.  A stream's sketch is the same, bit for bit,  */
+/* as applying its updates alone with ttnn_update_dense.  All server calls */
+/* are thread-safe.                                                        */
 /* ---------------------------------------------------------------------- */
 typedef struct ttnn_server_s* ttnn_server_t;
 
@@ -315,6 +317,7 @@ typedef struct {
   int64_t hbm_budget_bytes;  /* device memory all open streams may hold (plans + states) */
   int32_t max_batch;         /* requests per batch; <= 0: 64 */
   int32_t queue_capacity;    /* pending requests; <= 0: 65536 */
+  int32_t workers;           /* worker threads, each with its own CUDA stream; <= 0: 4 */
 } ttnn_server_opts;
 
 typedef struct {
@@ -325,6 +328,7 @@ typedef struct {
   int64_t device_bytes;      /* held by the open streams */
   int32_t open_streams;
   int64_t queued;
+  double worker_host_s;      /* worker time spent recording and launching batches */
 } ttnn_server_report;
 
 /* Creates a server on the current device (its own CUDA streams and worker

@@ -27,14 +27,15 @@ class TtnnNodeInfo(C.Structure):
 
 
 class TtnnServerOpts(C.Structure):
-    _fields_ = [("hbm_budget_bytes", c_i64), ("max_batch", c_i32), ("queue_capacity", c_i32)]
+    _fields_ = [("hbm_budget_bytes", c_i64), ("max_batch", c_i32), ("queue_capacity", c_i32),
+                ("workers", c_i32)]
 
 
 class TtnnServerReport(C.Structure):
     _fields_ = [("completed_updates", c_i64), ("completed_recoveries", c_i64), ("failed", c_i64),
                 ("batches", c_i64), ("update_bytes", c_i64), ("p50_us", c_dbl), ("p99_us", c_dbl),
                 ("max_us", c_dbl), ("seconds", c_dbl), ("device_bytes", c_i64),
-                ("open_streams", c_i32), ("queued", c_i64)]
+                ("open_streams", c_i32), ("queued", c_i64), ("worker_host_s", c_dbl)]
 
 
 SIGS = {

@@ -34,6 +34,13 @@ def _check(status):
         raise TtnnError(status, lib.ttnn_status_string(status).decode() + ": " + buf.value.decode())
 
 
+def last_error_message():
+    """The calling thread's last library error message."""
+    buf = C.create_string_buffer(512)
+    _lib().ttnn_last_error(buf, 512)
+    return buf.value.decode()
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -229,9 +236,10 @@ def ttnn_plan_pass_counts(plan):
 # ---------------------------------------------------------------------------
 # serving
 # ---------------------------------------------------------------------------
-def ttnn_server_create(hbm_budget_bytes, max_batch=0, queue_capacity=0):
+def ttnn_server_create(hbm_budget_bytes, max_batch=0, queue_capacity=0, workers=0):
     out = C.c_void_p()
-    opts = _sigs.TtnnServerOpts(int(hbm_budget_bytes), int(max_batch), int(queue_capacity))
+    opts = _sigs.TtnnServerOpts(int(hbm_budget_bytes), int(max_batch), int(queue_capacity),
+                                int(workers))
     _check(_lib().ttnn_server_create(C.byref(opts), C.byref(out)))
     return out
 

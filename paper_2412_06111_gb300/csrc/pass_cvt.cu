@@ -576,12 +576,10 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
   prm.D2p = (float*)ws + g.d1p_elems;
   prm.err = P.err_dev;
   if (mode == tc::MODE_SPLIT) {
-    TTNN_TRY_CUDA(cudaFuncSetAttribute(tc::pass_cvt_kernel<tc::MODE_SPLIT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+    TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_SPLIT>, 1));
     tc::pass_cvt_kernel<tc::MODE_SPLIT><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
   } else {
-    TTNN_TRY_CUDA(cudaFuncSetAttribute(tc::pass_cvt_kernel<tc::MODE_FP8>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+    TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_FP8>, 2));
     tc::pass_cvt_kernel<tc::MODE_FP8><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
   }
   TTNN_TRY(check_launch("tc pass_cvt_kernel"));

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tc_ptx.cuh"
 
@@ -483,6 +484,24 @@ struct Geometry {
   size_t smem;
 };
 
+ttnn_status smem_limit_once(const void* func, int slot) {
+  static std::mutex mu;
+  static bool done[4][64] = {};
+  int dev = 0;
+  TTNN_TRY_CUDA(cudaGetDevice(&dev));
+  if (slot < 0 || slot >= 4 || dev < 0 || dev >= 64) {
+    set_error("internal: shared-memory limit slot");
+    return TTNN_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done[slot][dev]) {
+    TTNN_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemBudget));
+    done[slot][dev] = true;
+  }
+  return TTNN_OK;
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -507,8 +526,7 @@ static int max_clusters(int C, size_t smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess ||
+  if (smem_limit_once((const void*)pass_kernel, 0) != TTNN_OK ||
       cudaOccupancyMaxActiveClusters(&n, pass_kernel, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -613,8 +631,7 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
   prm.D2p = (float*)ws + g.d1p_elems;
 
   prm.err = P.err_dev;
-  TTNN_TRY_CUDA(cudaFuncSetAttribute(tc::pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)g.smem));
+  TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_kernel, 0));
   if (g.cluster) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g.grid, 1, 1);

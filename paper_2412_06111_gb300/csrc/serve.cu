@@ -3,12 +3,14 @@
 // linear in the tensor, so every update is folded in as it arrives, and
 // recovery runs whenever a caller asks for the current approximation).
 //
-// One worker thread owns the device work.  It takes batches from a bounded
-// request queue -- at most one request per stream per batch, so every
-// stream sees its requests in submission order -- launches the first-level
-// pass of every update in the batch, then runs the tree walks of all of them
-// as one merged program (each dependency level of every walk in one launch),
-// then the recoveries of the batch.  Streams are admitted while the device
+// Worker threads own the device work, each with its own CUDA stream and
+// request queue (server stream k goes to worker k % workers).  A worker takes
+// batches from its queue -- at most one request per stream per batch, so
+// every stream sees its requests in submission order -- launches the
+// first-level pass of every update in the batch, then runs the tree walks of
+// all of them as one merged program (each dependency level of every walk in
+// one launch), then the recoveries; completion is tracked by CUDA events, so
+// a worker records the next batch while the device runs the previous ones.  Streams are admitted while the device
 // memory of all open streams stays within the server's budget.  Every wait
 // of a caller is bounded.
 #include <algorithm>
@@ -60,26 +62,36 @@ struct Slot {
 
 using namespace ttnn;
 
+// One worker: its own CUDA stream and request queue; stream k of the server
+// is served by worker k % (number of workers), so each stream's requests
+// stay in order on one CUDA stream while workers record in parallel.
+struct Worker {
+  cudaStream_t st = nullptr;
+  std::deque<Request> queue;
+  std::condition_variable cv_work;
+  std::thread thread;
+};
+
 struct ttnn_server_s {
   int device = 0;
-  cudaStream_t st = nullptr;        // worker's stream
   cudaStream_t st_admin = nullptr;  // plan creation
   int64_t budget = 0, used = 0;
   int max_batch = 64;
   size_t capacity = 65536;
+  size_t queued = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<Request> queue;
+  std::condition_variable cv_done;
+  std::vector<Worker> workers;
   std::map<int, Slot> slots;
   std::map<uint64_t, Done> done;
   std::set<uint64_t> inflight;
   int next_stream = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::thread worker;
   // statistics since the last reset
   std::vector<double> lat_us;
   int64_t n_updates = 0, n_recovers = 0, n_batches = 0, n_failed = 0, bytes = 0;
+  double host_s = 0;   // worker time spent recording and launching batches
   Clock::time_point since = Clock::now();
 };
 
@@ -106,79 +118,146 @@ void finish(ttnn_server_s& S, const Request& r, ttnn_status s, const std::string
   }
 }
 
-void worker_main(ttnn_server_s* S) {
+// A batch whose device work has been enqueued; done when its event is.
+struct InFlight {
+  cudaEvent_t ev = nullptr;
+  std::vector<Request> reqs;
+  std::vector<ttnn_status> st;
+  std::vector<std::string> msg;
+};
+
+constexpr int kMaxInFlight = 4;
+
+void complete(ttnn_server_s* S, InFlight& f, ttnn_status ev_status, const std::string& ev_msg) {
+  const Clock::time_point t1 = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t i = 0; i < f.reqs.size(); ++i) {
+      ttnn_status s = f.st[i];
+      std::string m = f.msg[i];
+      if (s == TTNN_OK && ev_status != TTNN_OK) {
+        s = ev_status;
+        m = ev_msg;
+      }
+      finish(*S, f.reqs[i], s, m, t1);
+    }
+    ++S->n_batches;
+  }
+  S->cv_done.notify_all();
+}
+
+// Completes the oldest in-flight batch, waiting for it if `block`.
+bool retire(ttnn_server_s* S, std::deque<InFlight>& q, std::vector<cudaEvent_t>& pool, bool block) {
+  if (q.empty()) return false;
+  InFlight& f = q.front();
+  cudaError_t e = block ? cudaEventSynchronize(f.ev) : cudaEventQuery(f.ev);
+  if (e == cudaErrorNotReady) return false;
+  ttnn_status es = TTNN_OK;
+  std::string em;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    es = TTNN_ECUDA;
+    em = std::string("serving batch: ") + cudaGetErrorString(e);
+  }
+  complete(S, f, es, em);
+  pool.push_back(f.ev);
+  q.pop_front();
+  return true;
+}
+
+void worker_main(ttnn_server_s* S, int k) {
   cudaSetDevice(S->device);
-  std::vector<Request> batch;
+  Worker& W = S->workers[k];
+  std::deque<InFlight> inflight;
+  std::vector<cudaEvent_t> pool;
   std::vector<std::pair<ttnn_plan_s*, ttnn_state_s*>> who;
   while (true) {
-    batch.clear();
+    while (retire(S, inflight, pool, false)) {
+    }
+    InFlight f;
     who.clear();
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait_for(lk, std::chrono::milliseconds(50),
-                          [&] { return S->stop || !S->queue.empty(); });
-      if (S->stop && S->queue.empty()) return;
+      if (inflight.empty())
+        W.cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                           [&] { return S->stop || !W.queue.empty(); });
+      if (S->stop && W.queue.empty() && inflight.empty()) break;
       // one request per stream per batch, in queue order; a stream whose
       // earlier request was deferred defers all its later ones too
       std::set<int> in_batch, blocked;
-      for (auto it = S->queue.begin();
-           it != S->queue.end() && (int)batch.size() < S->max_batch;) {
+      for (auto it = W.queue.begin();
+           it != W.queue.end() && (int)f.reqs.size() < S->max_batch;) {
         if (blocked.count(it->stream) || in_batch.count(it->stream)) {
           blocked.insert(it->stream);
           ++it;
           continue;
         }
         in_batch.insert(it->stream);
-        batch.push_back(*it);
+        f.reqs.push_back(*it);
         auto& sl = S->slots.at(it->stream);
         who.emplace_back(sl.plan, sl.state);
-        it = S->queue.erase(it);
+        it = W.queue.erase(it);
+        --S->queued;
       }
     }
-    if (batch.empty()) continue;
-    // updates: passes now, walks merged
-    std::vector<ttnn_status> st(batch.size(), TTNN_OK);
-    std::vector<std::string> msg(batch.size());
+    if (f.reqs.empty()) {
+      // nothing new: wait for the oldest batch on the device
+      retire(S, inflight, pool, true);
+      continue;
+    }
+    const Clock::time_point th0 = Clock::now();
+    const size_t nb = f.reqs.size();
+    f.st.assign(nb, TTNN_OK);
+    f.msg.assign(nb, std::string());
+    // updates: every first-level pass now, the walks as one merged program
     Program merged;
-    for (size_t i = 0; i < batch.size(); ++i) {
-      const Request& r = batch[i];
+    for (size_t i = 0; i < nb; ++i) {
+      const Request& r = f.reqs[i];
       if (r.kind != 0) continue;
-      st[i] = run_dense_update(*who[i].first, who[i].second->acc, r.data, r.box, r.scale, r.lambda,
-                               S->st, false, nullptr, &merged);
-      if (st[i] != TTNN_OK) msg[i] = last_error();
+      f.st[i] = run_dense_update(*who[i].first, who[i].second->acc, r.data, r.box, r.scale,
+                                 r.lambda, W.st, false, nullptr, &merged);
+      if (f.st[i] != TTNN_OK) f.msg[i] = last_error();
     }
-    ttnn_status ms = merged.run(S->st);
-    std::string mmsg = ms == TTNN_OK ? "" : last_error();
-    if (ms == TTNN_OK) {
-      const cudaError_t e = cudaStreamSynchronize(S->st);
-      if (e != cudaSuccess) {
-        ms = TTNN_ECUDA;
-        mmsg = std::string("serving batch: ") + cudaGetErrorString(e);
-      }
+    const ttnn_status ms = merged.run(W.st);
+    if (ms != TTNN_OK) {
+      const std::string m = last_error();
+      for (size_t i = 0; i < nb; ++i)
+        if (f.reqs[i].kind == 0 && f.st[i] == TTNN_OK) {
+          f.st[i] = ms;
+          f.msg[i] = m;
+        }
     }
-    for (size_t i = 0; i < batch.size(); ++i)
-      if (batch[i].kind == 0 && st[i] == TTNN_OK && ms != TTNN_OK) {
-        st[i] = ms;
-        msg[i] = mmsg;
-      }
-    const Clock::time_point t_upd = Clock::now();
-    // recoveries (each synchronises the stream)
-    std::vector<Clock::time_point> t_rec(batch.size(), t_upd);
-    for (size_t i = 0; i < batch.size(); ++i) {
-      const Request& r = batch[i];
+    // recoveries (each waits for the stream's earlier work: it reads the
+    // kept ranks back)
+    for (size_t i = 0; i < nb; ++i) {
+      const Request& r = f.reqs[i];
       if (r.kind != 1) continue;
-      st[i] = run_recover(*who[i].first, who[i].second->acc, r.cores, S->st, false, nullptr);
-      if (st[i] != TTNN_OK) msg[i] = last_error();
-      t_rec[i] = Clock::now();
+      f.st[i] = run_recover(*who[i].first, who[i].second->acc, r.cores, W.st, false, nullptr);
+      if (f.st[i] != TTNN_OK) f.msg[i] = last_error();
     }
+    if (pool.empty()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(W.st);
+        while (retire(S, inflight, pool, true)) {
+        }
+        complete(S, f, TTNN_OK, "");
+        continue;
+      }
+      pool.push_back(e);
+    }
+    f.ev = pool.back();
+    pool.pop_back();
+    cudaEventRecord(f.ev, W.st);
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      for (size_t i = 0; i < batch.size(); ++i)
-        finish(*S, batch[i], st[i], msg[i], batch[i].kind == 0 ? t_upd : t_rec[i]);
-      ++S->n_batches;
+      S->host_s += std::chrono::duration<double>(Clock::now() - th0).count();
     }
-    S->cv_done.notify_all();
+    inflight.push_back(std::move(f));
+    if ((int)inflight.size() > kMaxInFlight) retire(S, inflight, pool, true);
   }
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -198,23 +277,36 @@ ttnn_status ttnn_server_create(const ttnn_server_opts* opts, ttnn_server_t* out)
   S->budget = opts->hbm_budget_bytes;
   S->max_batch = opts->max_batch > 0 ? opts->max_batch : 64;
   S->capacity = opts->queue_capacity > 0 ? (size_t)opts->queue_capacity : 65536;
+  const int nw = opts->workers > 0 ? std::min(opts->workers, 64) : 4;
+  S->workers = std::vector<Worker>(nw);
   cudaError_t e = cudaGetDevice(&S->device);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st_admin, cudaStreamNonBlocking);
+  for (int k = 0; k < nw && e == cudaSuccess; ++k)
+    e = cudaStreamCreateWithFlags(&S->workers[k].st, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("server streams: %s", cudaGetErrorString(e));
-    if (S->st) cudaStreamDestroy(S->st);
+    for (auto& w : S->workers)
+      if (w.st) cudaStreamDestroy(w.st);
+    if (S->st_admin) cudaStreamDestroy(S->st_admin);
     delete S;
     return TTNN_ECUDA;
   }
   try {
-    S->worker = std::thread(worker_main, S);
+    for (int k = 0; k < nw; ++k) S->workers[k].thread = std::thread(worker_main, S, k);
   } catch (...) {
-    cudaStreamDestroy(S->st);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stop = true;
+    }
+    for (auto& w : S->workers) {
+      w.cv_work.notify_all();
+      if (w.thread.joinable()) w.thread.join();
+      cudaStreamDestroy(w.st);
+    }
     cudaStreamDestroy(S->st_admin);
     delete S;
-    set_error("cannot start the server thread");
+    set_error("cannot start the server threads");
     return TTNN_ENOMEM;
   }
   *out = S;
@@ -227,13 +319,15 @@ void ttnn_server_destroy(ttnn_server_t S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
   }
-  S->cv_work.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  for (auto& w : S->workers) {
+    w.cv_work.notify_all();
+    if (w.thread.joinable()) w.thread.join();
+  }
   for (auto& kv : S->slots) {
     ttnn_state_destroy(kv.second.state);
     ttnn_plan_destroy(kv.second.plan);
   }
-  cudaStreamDestroy(S->st);
+  for (auto& w : S->workers) cudaStreamDestroy(w.st);
   cudaStreamDestroy(S->st_admin);
   delete S;
 }
@@ -294,11 +388,12 @@ ttnn_status ttnn_server_close(ttnn_server_t S, int32_t stream_id, int64_t timeou
 }
 
 static ttnn_status enqueue(ttnn_server_s* S, Request&& r, uint64_t* ticket) {
+  Worker& W = S->workers[r.stream % (int)S->workers.size()];
   {
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->slots.find(r.stream);
     TTNN_CHECK_ARG(it != S->slots.end(), "no open stream %d", r.stream);
-    if (S->queue.size() >= S->capacity) {
+    if (S->queued >= S->capacity) {
       set_error("request queue full (%zu)", S->capacity);
       return TTNN_EBUSY;
     }
@@ -307,9 +402,10 @@ static ttnn_status enqueue(ttnn_server_s* S, Request&& r, uint64_t* ticket) {
     ++it->second.pending;
     S->inflight.insert(r.ticket);
     *ticket = r.ticket;
-    S->queue.push_back(std::move(r));
+    W.queue.push_back(std::move(r));
+    ++S->queued;
   }
-  S->cv_work.notify_one();
+  W.cv_work.notify_one();
   return TTNN_OK;
 }
 
@@ -405,8 +501,10 @@ ttnn_status ttnn_server_stats(ttnn_server_t S, int32_t reset, ttnn_server_report
   out->seconds = std::chrono::duration<double>(Clock::now() - S->since).count();
   out->device_bytes = S->used;
   out->open_streams = (int32_t)S->slots.size();
-  out->queued = (int64_t)S->queue.size();
+  out->queued = (int64_t)S->queued;
+  out->worker_host_s = S->host_s;
   if (reset) {
+    S->host_s = 0;
     S->lat_us.clear();
     S->n_updates = S->n_recovers = S->n_batches = S->n_failed = S->bytes = 0;
     S->since = Clock::now();

@@ -123,6 +123,10 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 // Host helpers (pass_tc.cu).
+// Raises a kernel's dynamic shared memory limit to kSmemBudget, once per
+// device.  Setting it per launch to the launch's own size would race between
+// host threads launching the same kernel with different sizes.
+ttnn_status smem_limit_once(const void* func, int slot);
 ttnn_status encode_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize,
                        int64_t inner, int64_t outer, uint32_t box_inner, uint32_t box_outer,
                        CUtensorMapSwizzle sw);
