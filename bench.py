@@ -144,28 +144,45 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
-def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=False):
+def _geometry(ws, rank):
+    """Global dims (mode 0 of n*ws points) and this rank's mode-0 slab."""
+    from paper_2412_06111_gb300 import shard
+    dims = [NMODE * ws] + [NMODE] * (D - 1)
+    off, ext = shard.shard_box(dims, ws, rank, 0)
+    return dims, (None, None) if ws == 1 else (off, ext)
+
+
+def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=False, rank=0):
     """Times `steps` whole-path steps on device-resident data.  Returns a dict.
     quantize: `data` is binary32 and is first quantised to E4M3 tiles with the
     plan (timed apart: the producer's step, not the sketch's)."""
+    from paper_2412_06111_gb300 import shard
     log("form dtype", dtype, "variant", variant)
     tr = W.balanced_binary(D)
     n = len(tr[0])
-    dims = [NMODE] * D
+    dims, (off, ext) = _geometry(ws, rank)
     plan = api.ttnn_plan_create(tr, dims, [RANK] * n, [OVERSAMPLE] * n, SEED, variant=variant,
                                 sketch_dtype=dtype)
+
+    def step():
+        api.ttnn_state_zero(state)
+        api.ttnn_update_dense(state, data, off, ext, tile_scale=scale)
+        if ws > 1:
+            shard.allreduce_state_(plan, state)    # the one exchange: sum of sketches
+        api.ttnn_recover(state, cores)              # synchronises (reads kept ranks)
+
     state = api.ttnn_state_create(plan)
     scale, quant_ms = None, None
     if quantize:
-        nl = NMODE ** ((D + 1) // 2)
+        nl = NMODE ** ((D + 1) // 2)        # the slab's pass-matrix rows (mode 0 is in L)
         nrt, nct = -(-nl // 128), -(-(data.numel() // nl) // 128)
         q8 = torch.empty(data.numel(), dtype=torch.uint8, device="cuda")
         scale = torch.empty(nrt * nct, dtype=torch.float32, device="cuda")
-        api.ttnn_fp8_quantize(plan, data, q8, scale)
+        api.ttnn_fp8_quantize(plan, data, q8, scale, extent=ext)
         torch.cuda.synchronize()
         qa, qb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         qa.record()
-        api.ttnn_fp8_quantize(plan, data, q8, scale)
+        api.ttnn_fp8_quantize(plan, data, q8, scale, extent=ext)
         qb.record()
         torch.cuda.synchronize()
         quant_ms = qa.elapsed_time(qb)
@@ -175,9 +192,7 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     stream = torch.cuda.current_stream()
     log("plan and state ready")
     for _ in range(warmup):
-        api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, data, tile_scale=scale)
-        api.ttnn_recover(state, cores)
+        step()
     torch.cuda.synchronize()
     log("warm-up done")
     api.ttnn_profile(plan, True)
@@ -191,9 +206,7 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     e0.record(stream)
     for _ in range(steps):
         t0 = time.perf_counter()
-        api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, data, tile_scale=scale)
-        api.ttnn_recover(state, cores)      # synchronises (reads kept ranks)
+        step()
         lat.append((time.perf_counter() - t0) * 1e3)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -213,32 +226,36 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
             "quantize_ms": quant_ms}
 
 
-def run_e2e(api, W, dtype, steps, warmup, torch, host):
+def run_e2e(api, W, dtype, steps, warmup, torch, host, ws=1, rank=0):
     """Same metric through the public API from pinned host memory: H2D copy of
-    the tensor, update, recovery, D2H copy of the cores every step."""
+    the tensor (this rank's slab), update, (all-reduce,) recovery, D2H copy of
+    the cores every step."""
+    from paper_2412_06111_gb300 import shard
     tr = W.balanced_binary(D)
     n = len(tr[0])
-    dims = [NMODE] * D
+    dims, (off, ext) = _geometry(ws, rank)
     plan = api.ttnn_plan_create(tr, dims, [RANK] * n, [OVERSAMPLE] * n, SEED, sketch_dtype=dtype)
     state = api.ttnn_state_create(plan)
     ce = api.ttnn_plan_sizes(plan)[2]
     cores = torch.zeros(ce, dtype=torch.float64, device="cuda")
     cores_h = torch.zeros(ce, dtype=torch.float64).pin_memory()
     dev = torch.empty_like(host, device="cuda")
-    for _ in range(warmup):
+    def step():
         dev.copy_(host, non_blocking=True)
         api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, dev)
+        api.ttnn_update_dense(state, dev, off, ext)
+        if ws > 1:
+            shard.allreduce_state_(plan, state)
         api.ttnn_recover(state, cores)
         cores_h.copy_(cores, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
     torch.cuda.synchronize()
+    _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(steps):
-        dev.copy_(host, non_blocking=True)
-        api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, dev)
-        api.ttnn_recover(state, cores)
-        cores_h.copy_(cores, non_blocking=True)
+        step()
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     api.ttnn_state_destroy(state)
@@ -472,20 +489,22 @@ def main():
     torch.cuda.set_device(dev)
     hbm, bf16_tf, peak_src = _peaks()
     N = NMODE ** D
-    a32 = W.inv_sum_torch(D, NMODE, "cuda", torch.float32)
+    a32 = W.inv_sum_slab_torch(D, NMODE, ws, rank, "cuda", torch.float32)
     a16 = a32.to(torch.bfloat16)
     log("tensor ready", N)
     with Clocks(dev) as clk:
-        bf = run_form(api, W, api.BF16, api.VARIANT_TTNN, args.steps, warmup, ws, torch, a16)
-    f32 = run_form(api, W, api.F32, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch, a32)
-    x2 = run_form(api, W, api.BF16X2, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch,
-                  a32)
-    f8 = run_form(api, W, api.E4M3, api.VARIANT_TTNN, max(3, args.steps // 2), warmup, ws, torch,
-                  a32, quantize=True)
-    st = run_form(api, W, api.BF16, api.VARIANT_STTNN, max(3, args.steps // 2), warmup, ws, torch, a16)
+        bf = run_form(api, W, api.BF16, api.VARIANT_TTNN, args.steps, warmup, ws, torch, a16,
+                      rank=rank)
+    k = max(3, args.steps // 2)
+    f32 = run_form(api, W, api.F32, api.VARIANT_TTNN, k, warmup, ws, torch, a32, rank=rank)
+    x2 = run_form(api, W, api.BF16X2, api.VARIANT_TTNN, k, warmup, ws, torch, a32, rank=rank)
+    f8 = run_form(api, W, api.E4M3, api.VARIANT_TTNN, k, warmup, ws, torch, a32, quantize=True,
+                  rank=rank)
+    st = run_form(api, W, api.BF16, api.VARIANT_STTNN, k, warmup, ws, torch, a16, rank=rank)
     host16 = a16.cpu().pin_memory()
     del a32
-    e2e_ms, h2d, d2h = run_e2e(api, W, api.BF16, max(3, args.steps // 2), 2, torch, host16)
+    e2e_ms, h2d, d2h = run_e2e(api, W, api.BF16, k, 2, torch, host16, ws, rank)
+    e2e_ms = _max_over_ranks(e2e_ms, ws)
     ms = _max_over_ranks(bf["ms_per_step"], ws)
     value = N * 2 * ws / (ms * 1e-3) / 1e9
     pass_gbs = N * 2 / (bf["pass_ms"] * 1e-3) / 1e9
@@ -494,14 +513,19 @@ def main():
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "dense order-5 64^5 f(x)=1/sum(x) on [1,2]^5, balanced binary tree, "
+        "config": {"workload": (f"dense order-5 {NMODE * ws}x{NMODE}^4" if ws > 1 else
+                                f"dense order-5 {NMODE}^5") +
+                               " f(x)=1/sum(x) on [1,2]^5, balanced binary tree, "
                                "ranks 20, oversampling 10, TTNN, one whole-tensor update + recovery "
                                "per step", "global_batch": 1, "l2": "inputs larger than L2 (2.1 GB)",
-                   "parallelism": f"replicas{ws}"},
+                   "parallelism": "single GPU" if ws == 1 else
+                   f"sharded{ws}: each rank owns a 64^5 mode-0 slab of a ({NMODE}*{ws})x{NMODE}^4 "
+                   "tensor; one NCCL sum all-reduce of the sketch state per step; recovery on "
+                   "every rank"},
         "roofline": {"bound": "hbm", "achieved": pass_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": pass_gbs / hbm, "traffic": traffic,
                      "kernel": "first-level pass", "peak_source": peak_src},
-        "e2e": {"value": N * 2 / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": N * 2 * ws / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(bf["launches"]),
         "clocks": clk.summary(),

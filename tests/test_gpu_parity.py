@@ -326,3 +326,24 @@ def test_near_full_box_update(case):
                           api.VARIANT_TTNN, 1e-12)
     finally:
         run.close()
+
+
+def test_shard_state_tensor_aliases_the_state():
+    """The tensor the all-reduce works on is the state itself: scaling it in
+    place scales the sketches; with one rank the all-reduce is the identity."""
+    from paper_2412_06111_gb300 import shard
+    tr, dims, r, p = CASES["binary4"]
+    n = len(tr[0])
+    for dtype in (api.F64, api.F32):
+        run = Run(tr, dims, [r] * n, [p] * n, 2, dtype=dtype)
+        try:
+            api.ttnn_update_dense(run.state, _dev(W.gaussian(dims, 3), dtype)[0])
+            before = run.state_host()
+            t = shard.state_tensor(run.plan, run.state)
+            assert t.numel() == before.size
+            assert np.array_equal(t.cpu().numpy().astype(np.float64), before)
+            t.mul_(2.0)
+            shard.allreduce_state_(run.plan, run.state)
+            assert np.array_equal(run.state_host(), 2.0 * before)
+        finally:
+            run.close()

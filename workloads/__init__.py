@@ -181,6 +181,22 @@ def inv_sum_torch(d, n, device, dtype):
     return (1.0 / s).to(dtype)
 
 
+def inv_sum_slab_torch(d, n, world, rank, device, dtype):
+    """Rank `rank`'s slab (mode-0 indices [rank*n, (rank+1)*n)) of the order-d
+    tensor 1/sum(x) whose mode 0 has n*world grid points on [1, 2] and the
+    other modes n; world = 1 gives inv_sum_torch(d, n)."""
+    import torch
+    m = n * world
+    x0 = 1.0 + (rank * n + torch.arange(n, dtype=torch.float64, device=device)) / (m - 1)
+    x = 1.0 + torch.arange(n, dtype=torch.float64, device=device) / (n - 1)
+    s = torch.zeros([n] * d, dtype=torch.float64, device=device)
+    for mu in range(d):
+        sh = [1] * d
+        sh[mu] = n
+        s = s + (x0 if mu == 0 else x).reshape(sh)
+    return (1.0 / s).to(dtype)
+
+
 def gaussian(shape, seed, scale=1.0):
     return np.random.default_rng(seed).standard_normal(shape) * scale
 
