@@ -164,12 +164,15 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     plan = api.ttnn_plan_create(tr, dims, [RANK] * n, [OVERSAMPLE] * n, SEED, variant=variant,
                                 sketch_dtype=dtype)
 
-    def step():
+    def step(sync=False):
         api.ttnn_state_zero(state)
         api.ttnn_update_dense(state, data, off, ext, tile_scale=scale)
         if ws > 1:
             shard.allreduce_state_(plan, state)    # the one exchange: sum of sketches
-        api.ttnn_recover(state, cores)              # synchronises (reads kept ranks)
+        if sync:
+            api.ttnn_recover(state, cores)          # waits, reads the kept ranks back
+        else:
+            api.ttnn_recover_async(state, cores)    # the next step is recorded meanwhile
 
     state = api.ttnn_state_create(plan)
     scale, quant_ms = None, None
@@ -202,17 +205,21 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     _barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat = []
     e0.record(stream)
     for _ in range(steps):
-        t0 = time.perf_counter()
         step()
-        lat.append((time.perf_counter() - t0) * 1e3)
     e1.record(stream)
     torch.cuda.synchronize()
+    api.ttnn_plan_sync(plan)
     _barrier(ws)
     ms = e0.elapsed_time(e1) / steps
     launches = api.ttnn_kernel_launches() - l0
+    # latency of one update + recovery round trip (host wall clock, waited on)
+    lat = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        step(sync=True)
+        lat.append((time.perf_counter() - t0) * 1e3)
     passes = api.ttnn_plan_pass_counts(plan)
     api.ttnn_profile(plan, False)
     prof = [api.ttnn_profile_read(plan, ph) for ph in range(3)]

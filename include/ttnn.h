@@ -255,8 +255,18 @@ ttnn_status ttnn_update_ttn(ttnn_state_t state, const double* const* cores_in,
  * B_v = (kron_c Q_c)^T Psi_v R_v,eps^+ (children's Q), leaf B_v = Psi_v
  * R_v,eps^+, root B = (kron_c Q_c)^T Psi_root; all in binary64.
  * cores: device, core_elems binary64 values at the per-node offsets.
- * Synchronises the stream before returning (kept ranks are read back). */
+ * Synchronises the stream before returning (kept ranks are read back).
+ * ETIMEOUT: a bounded device wait of an earlier update or recovery on this
+ * plan ran out (the cores are then unspecified). */
 ttnn_status ttnn_recover(ttnn_state_t state, double* cores, void* stream);
+/* ttnn_recover without the wait: returns once the recovery is enqueued; the
+ * kept ranks and the device error word are copied back asynchronously and
+ * taken in by the next ttnn_plan_sync, ttnn_plan_node or recovery call on
+ * the plan.  For pipelines that read the cores on the device. */
+ttnn_status ttnn_recover_async(ttnn_state_t state, double* cores, void* stream);
+/* Waits for the read-back of the last asynchronous recovery; ETIMEOUT if a
+ * bounded device wait of an earlier call on the plan ran out. */
+ttnn_status ttnn_plan_sync(ttnn_plan_t plan);
 
 /* sttnn_run -- STTNN end to end on a whole dense tensor [Sec. 5]: a plan made
  * with variant TTNN_VARIANT_STTNN, one pass over `dense` (plan format), then

@@ -62,6 +62,8 @@ SIGS = {
     "ttnn_update_cp": (c_i32, [c_vp, c_i32, C.POINTER(c_dbl), C.POINTER(c_vp), c_dbl, c_vp]),
     "ttnn_update_ttn": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_i32), c_dbl, c_vp]),
     "ttnn_recover": (c_i32, [c_vp, c_vp, c_vp]),
+    "ttnn_recover_async": (c_i32, [c_vp, c_vp, c_vp]),
+    "ttnn_plan_sync": (c_i32, [c_vp]),
     "sttnn_run": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "ttnn_round": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_i32), c_vp, c_vp]),
     "ttnn_fp8_quantize": (c_i32, [c_vp, c_vp, C.POINTER(c_i64), c_vp, c_vp, c_vp]),

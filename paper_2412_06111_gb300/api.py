@@ -192,6 +192,14 @@ def ttnn_recover(state, cores, stream=None):
     _check(_lib().ttnn_recover(state, _ptr(cores), _stream(stream)))
 
 
+def ttnn_recover_async(state, cores, stream=None):
+    _check(_lib().ttnn_recover_async(state, _ptr(cores), _stream(stream)))
+
+
+def ttnn_plan_sync(plan):
+    _check(_lib().ttnn_plan_sync(plan))
+
+
 def sttnn_run(plan, dense, cores, tile_scale=None, stream=None):
     _check(_lib().sttnn_run(plan, _ptr(dense), _ptr(tile_scale), _ptr(cores), _stream(stream)))
 

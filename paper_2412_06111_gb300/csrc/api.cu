@@ -42,6 +42,7 @@ static void free_plan(ttnn_plan_s* P) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
     }
+  for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
   cudaFree(P->fac64);
   if (P->facw != (void*)P->fac64) cudaFree(P->facw);
   cudaFree(P->sideR);
@@ -51,6 +52,8 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->jobs_dev);
   cudaFree(P->kept_dev);
   cudaFree(P->err_dev);
+  if (P->host_kept) cudaFreeHost(P->host_kept);
+  if (P->kept_ev) cudaEventDestroy(P->kept_ev);
   delete P;
 }
 
@@ -65,6 +68,15 @@ static ttnn_status grow_workspace(ttnn_plan_s& P, int64_t bytes) {
   P.ws_bytes = bytes;
   P.dev_bytes += bytes;
   return TTNN_OK;
+}
+
+// A device timeout seen while ttnn_plan_node waited for a read-back is
+// reported by the next recovery / sync call.
+static ttnn_status take_timeout(ttnn_plan_s& P) {
+  if (!P.timeout_seen) return TTNN_OK;
+  P.timeout_seen = false;
+  set_error("a bounded device wait ran out in an earlier update or recovery");
+  return TTNN_ETIMEOUT;
 }
 
 static int store_bytes(int store) { return store == 0 ? 8 : store == 1 ? 4 : store == 2 ? 2 : 1; }
@@ -197,6 +209,13 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   if ((s = palloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
   if ((s = palloc((void**)&P.kept_dev, 2 * std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
   if ((s = palloc((void**)&P.err_dev, sizeof(int))) != TTNN_OK) return fail(s);
+  if (cudaHostAlloc((void**)&P.host_kept, (2 * std::max(1, P.n_sketched) + 1) * sizeof(int),
+                    cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P.kept_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plan creation: pinned read-back buffer or event");
+    return fail(TTNN_ENOMEM);
+  }
   if ((s = launch_fill_zero(P.err_dev, sizeof(int), st)) != TTNN_OK) return fail(s);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -222,6 +241,13 @@ ttnn_status ttnn_plan_sizes(ttnn_plan_t P, int64_t* state_elems, int32_t* state_
 ttnn_status ttnn_plan_node(ttnn_plan_t P, int32_t v, ttnn_node_info* o) {
   TTNN_CHECK_ARG(P && o, "null argument");
   TTNN_CHECK_ARG(v >= 0 && v < (int)P->nodes.size(), "node index out of range");
+  // kept ranks of a recovery still in flight: wait for its read-back (a
+  // device timeout it carries is reported by ttnn_plan_sync / ttnn_recover)
+  if (P->kept_pending) {
+    const ttnn_status ss = plan_sync(*P);
+    if (ss != TTNN_OK && ss != TTNN_ETIMEOUT) return ss;
+    if (ss == TTNN_ETIMEOUT) P->timeout_seen = true;
+  }
   const TNode& nd = P->nodes[v];
   memset(o, 0, sizeof(*o));
   o->user_index = v;
@@ -405,7 +431,20 @@ ttnn_status ttnn_update_ttn(ttnn_state_t S, const double* const* cores_in, const
 
 ttnn_status ttnn_recover(ttnn_state_t S, double* cores, void* stream) {
   TTNN_CHECK_ARG(S && cores, "null argument");
+  TTNN_TRY(take_timeout(*S->plan));
   return run_recover(*S->plan, S->acc, cores, (cudaStream_t)stream, false, nullptr);
+}
+
+ttnn_status ttnn_recover_async(ttnn_state_t S, double* cores, void* stream) {
+  TTNN_CHECK_ARG(S && cores, "null argument");
+  TTNN_TRY(take_timeout(*S->plan));
+  return run_recover(*S->plan, S->acc, cores, (cudaStream_t)stream, false, nullptr, true);
+}
+
+ttnn_status ttnn_plan_sync(ttnn_plan_t P) {
+  TTNN_CHECK_ARG(P, "null plan");
+  TTNN_TRY(take_timeout(*P));
+  return plan_sync(*P);
 }
 
 ttnn_status sttnn_run(ttnn_plan_t P, const void* dense, const float* tile_scale, double* cores,
@@ -467,8 +506,8 @@ ttnn_status ttnn_profile_read(ttnn_plan_t P, int32_t phase, double* total_ms, in
     }
     tot += ms;
     ++cnt;
-    cudaEventDestroy(pr.first);
-    cudaEventDestroy(pr.second);
+    P->prof_pool.push_back(pr.first);
+    P->prof_pool.push_back(pr.second);
   }
   P->prof[phase].clear();
   if (total_ms) *total_ms = tot;

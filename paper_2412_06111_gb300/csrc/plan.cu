@@ -1271,8 +1271,26 @@ void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b) {
 // ---------------------------------------------------------------------------
 // recovery: QR / eps-pseudo-inverse, then core assembly in binary64
 // ---------------------------------------------------------------------------
+ttnn_status plan_sync(ttnn_plan_s& P) {
+  if (!P.kept_pending) return TTNN_OK;
+  P.kept_pending = false;
+  TTNN_TRY_CUDA(cudaEventSynchronize(P.kept_ev));
+  const size_t nj = P.kept_nodes.size();
+  for (size_t k = 0; k < nj; ++k) {
+    P.nodes[P.kept_nodes[k]].kept = P.host_kept[k];
+    P.nodes[P.kept_nodes[k]].sweeps = P.host_kept[nj + k];
+  }
+  const int err = P.host_kept[2 * nj];
+  if (err) {
+    TTNN_TRY_CUDA(cudaMemset(P.err_dev, 0, sizeof(int)));
+    set_error("a bounded device wait ran out in an earlier update or recovery (code %d)", err);
+    return TTNN_ETIMEOUT;
+  }
+  return TTNN_OK;
+}
+
 ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
-                        int64_t* peak) {
+                        int64_t* peak, bool async) {
   Ws ws(P.ws, P.ws_bytes, dry);
   Program prog;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
@@ -1399,26 +1417,25 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
   }
   if (!dry) TTNN_TRY(prog.run(st));
   if (!dry) prof_push(P, 2, ev0, prof_event(P, st));
-  if (!dry && !jobs.empty()) {
-    std::vector<int> kept(2 * jobs.size());
-    TTNN_TRY_CUDA(cudaMemcpyAsync(kept.data(), P.kept_dev, kept.size() * sizeof(int),
+  if (dry) return TTNN_OK;
+  // read-back of kept ranks, sweeps and the device error word into pinned
+  // host memory, completed by an event (plan_sync waits for it)
+  if (P.kept_pending) {
+    // an earlier read-back nobody waited for: its data is superseded
+    TTNN_TRY_CUDA(cudaEventSynchronize(P.kept_ev));
+    P.kept_pending = false;
+    if (P.host_kept[2 * P.kept_nodes.size()]) P.timeout_seen = true;
+  }
+  const size_t nj = jobs.size();
+  P.kept_nodes = job_node;
+  if (nj)
+    TTNN_TRY_CUDA(cudaMemcpyAsync(P.host_kept, P.kept_dev, 2 * nj * sizeof(int),
                                   cudaMemcpyDeviceToHost, st));
-    TTNN_TRY_CUDA(cudaStreamSynchronize(st));
-    for (size_t k = 0; k < jobs.size(); ++k) {
-      P.nodes[job_node[k]].kept = kept[k];
-      P.nodes[job_node[k]].sweeps = kept[jobs.size() + k];
-    }
-  }
-  if (!dry && P.err_dev) {
-    int err = 0;
-    TTNN_TRY_CUDA(cudaMemcpyAsync(&err, P.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TTNN_TRY_CUDA(cudaStreamSynchronize(st));
-    if (err) {
-      TTNN_TRY_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
-      set_error("a bounded device wait ran out in an earlier update (code %d)", err);
-      return TTNN_ETIMEOUT;
-    }
-  }
+  TTNN_TRY_CUDA(cudaMemcpyAsync(P.host_kept + 2 * nj, P.err_dev, sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
+  TTNN_TRY_CUDA(cudaEventRecord(P.kept_ev, st));
+  P.kept_pending = true;
+  if (!async) TTNN_TRY(plan_sync(P));
   return TTNN_OK;
 }
 

@@ -71,6 +71,12 @@ struct ttnn_plan_s {
   ttnn::QrJob* jobs_dev = nullptr;
   int* kept_dev = nullptr;
   int* err_dev = nullptr;       // device error word of bounded waits (tensor-core pass)
+  // read-back of the last recovery: kept ranks, Jacobi sweeps, error word
+  int* host_kept = nullptr;     // pinned, 2 * n_sketched + 1 ints
+  cudaEvent_t kept_ev = nullptr;
+  bool kept_pending = false;
+  bool timeout_seen = false;    // a read-back waited for by ttnn_plan_node carried a timeout
+  std::vector<int> kept_nodes;  // node of each job of the pending read-back
   int n_sketched = 0;
   int64_t state_elems = 0;
   int64_t core_elems = 0;
@@ -80,6 +86,7 @@ struct ttnn_plan_s {
   // profiling: event pairs per phase (0 pass, 1 walk, 2 recovery)
   int profile = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[3];
+  std::vector<cudaEvent_t> prof_pool;   // events of read intervals, reused
 };
 
 struct ttnn_state_s {
@@ -128,7 +135,13 @@ ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, 
 // records an event on `st` if profiling is on (returns nullptr otherwise)
 cudaEvent_t prof_event(ttnn_plan_s& P, cudaStream_t st);
 void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b);
+// Waits for a pending recovery read-back and stores kept ranks / sweeps in
+// the nodes; TTNN_ETIMEOUT (and clears the device word) if a bounded device
+// wait of an earlier update or recovery ran out.
+ttnn_status plan_sync(ttnn_plan_s& P);
+// async: returns once everything is enqueued (read-back completes later,
+// see plan_sync); otherwise waits and checks like plan_sync.
 ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
-                        int64_t* peak);
+                        int64_t* peak, bool async = false);
 
 }  // namespace ttnn
