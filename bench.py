@@ -144,6 +144,58 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
+SAMPLES, SAMPLE_SEED = 20000, 77
+
+
+def _ttn_sample_error(api, plan, tree, cores_dev, ws, rank):
+    """Final relative error of the recovered TTN against the exact binary64
+    values of 1/sum(x) at SAMPLES seeded indices (host evaluation of the
+    cores: leaf slices, then each transfer tensor against its children)."""
+    parent, leaf_modes, _ = tree
+    nn = len(parent)
+    nodes = [api.ttnn_plan_node(plan, v) for v in range(nn)]
+    host = cores_dev.cpu().numpy()
+    dims, _ = _geometry(ws, rank)
+    rng = np.random.default_rng(SAMPLE_SEED)
+    idx = np.stack([rng.integers(0, dims[m], size=SAMPLES) for m in range(D)], axis=1)
+    grid = np.stack([idx[:, m] / (dims[m] - 1) for m in range(D)], axis=1)
+    exact = 1.0 / (1.0 + grid).sum(axis=1)
+    ch = {v: sorted([c for c in range(nn) if parent[c] == v], key=lambda c: nodes[c]["mode_lo"])
+          for v in range(nn)}
+    letters = "bcdefghijk"
+
+    def val(v):
+        nd = nodes[v]
+        core = host[nd["core_offset"]:nd["core_offset"] + nd["core_elems"]].reshape(nd["core_shape"])
+        if not ch[v]:
+            lo, hi = nd["mode_lo"], nd["mode_hi"]
+            flat = np.ravel_multi_index(tuple(idx[:, lo:hi].T), [dims[m] for m in range(lo, hi)])
+            return core.reshape(core.shape[0], -1)[:, flat].T
+        vecs = [val(c) for c in ch[v]]
+        m = len(vecs)
+        head = "" if parent[v] < 0 else "a"
+        spec = head + letters[:m] + "," + ",".join("s" + letters[k] for k in range(m)) + "->s" + head
+        return np.einsum(spec, core, *vecs, optimize=True)
+
+    root = parent.index(-1)
+    approx = val(root)
+    return float(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+
+
+def _oracle_error():
+    """The FP64 oracle's error on the same samples (tests/golden, written by
+    a script that calls only the oracle), or None."""
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                     "fullsize_oracle_error.txt")
+    try:
+        for line in open(p):
+            if line.startswith("sampled_rel_error:"):
+                return float(line.split(":", 1)[1])
+    except OSError:
+        pass
+    return None
+
+
 def _geometry(ws, rank):
     """Global dims (mode 0 of n*ws points) and this rank's mode-0 slab."""
     from paper_2412_06111_gb300 import shard
@@ -223,6 +275,7 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     passes = api.ttnn_plan_pass_counts(plan)
     api.ttnn_profile(plan, False)
     prof = [api.ttnn_profile_read(plan, ph) for ph in range(3)]
+    err = _ttn_sample_error(api, plan, tr, cores, ws, rank) if NMODE == 64 else None
     api.ttnn_state_destroy(state)
     api.ttnn_plan_destroy(plan)
     lat.sort()
@@ -230,7 +283,7 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
             "pass_ms": prof[0][0] / max(prof[0][1], 1), "walk_ms": prof[1][0] / max(prof[1][1], 1),
             "recover_ms": prof[2][0] / max(prof[2][1], 1),
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "quantize_ms": quant_ms}
+            "quantize_ms": quant_ms, "rel_error": err}
 
 
 def run_e2e(api, W, dtype, steps, warmup, torch, host, ws=1, rank=0):
@@ -539,6 +592,11 @@ def main():
         "latency_ms": {"p50": bf["p50_ms"], "p99": bf["p99_ms"]},
         "phases_ms": {"pass": bf["pass_ms"], "walk": bf["walk_ms"], "recover": bf["recover_ms"]},
         "pass_path": {"tensor_core": bf["tc_passes"], "simt": bf["simt_passes"]},
+        "rel_error": {"note": "final relative error of the recovered TTN vs the exact binary64 "
+                              f"tensor on {SAMPLES} seeded entries",
+                      "fp64_oracle": _oracle_error(), "bf16": bf["rel_error"],
+                      "fp32_plain": f32["rel_error"], "bf16x2_split": x2["rel_error"],
+                      "fp8_e4m3": f8["rel_error"], "sttnn_bf16": st["rel_error"]},
         "fp32_plain": {"value": N * 4 / (f32["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",
                        "ms_per_step": f32["ms_per_step"], "pass_ms": f32["pass_ms"]},
         "sttnn_bf16": {"value": N * 2 / (st["ms_per_step"] * 1e-3) / 1e9, "unit": "GB/s",
