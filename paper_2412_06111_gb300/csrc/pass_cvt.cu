@@ -440,8 +440,11 @@ static bool cvt_geometry(int mode, const ttnn_plan_s& P, int64_t nL, int64_t nR,
   if (P.wRpad < 16 || P.wLpad < 16 || P.wRpad > 256 || P.wLpad > 256) return false;
   int tiles = (512 - 2 * P.wRpad) / P.wLpad;
   tiles = std::min(tiles, kMaxTiles);
-  tiles = (int)std::min<int64_t>(tiles, (nR + kTileN - 1) / kTileN);
+  const int64_t ntile = (nR + kTileN - 1) / kTileN;
+  tiles = (int)std::min<int64_t>(tiles, ntile);
   if (tiles < 1) return false;
+  // as few chunks as TMEM allows, tiles spread evenly over them
+  tiles = (int)((ntile + (ntile + tiles - 1) / tiles - 1) / ((ntile + tiles - 1) / tiles));
   const int64_t op = mode == MODE_SPLIT ? 65536 : 32768, raw = mode == MODE_SPLIT ? 0 : 16384;
   const int64_t stage_bytes = op + raw + (int64_t)P.wRpad * 256;
   const int64_t bl = 2 * (int64_t)P.wLpad * 256;

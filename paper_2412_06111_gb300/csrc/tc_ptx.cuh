@@ -13,7 +13,7 @@ namespace tc {
 
 constexpr int kTileM = 128;           // rows of M per tile (MMA M for D1)
 constexpr int kTileN = 128;           // columns of M per tile (MMA M for D2)
-constexpr int kMaxTiles = 8;          // column tiles per chunk
+constexpr int kMaxTiles = 16;         // column tiles per chunk (TMEM bounds it first)
 constexpr int kSmemBudget = 232448 - 2048;   // 227 KB opt-in minus static shared memory
 constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s per wait
 
