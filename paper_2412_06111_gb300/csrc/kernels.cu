@@ -130,6 +130,53 @@ __global__ void side_kernel(SideSpec s, void* out) {
   }
 }
 
+template <typename T>
+__global__ void side_gather_kernel(SideSpec s, const T* src, int64_t src_ld, T* out) {
+  int64_t rows = 1;
+  for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];
+  const int64_t n = rows * s.total_cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, row = e - c * rows;
+    int64_t rem = row, full = 0, stride = 1;
+    for (int m = s.nmodes - 1; m >= 0; --m) {
+      const int64_t i = rem % s.ext[m];
+      rem /= s.ext[m];
+      full += (s.off[m] + i) * stride;
+      stride *= s.full[m];
+    }
+    out[c * s.ld + row] = src[c * src_ld + full];
+  }
+}
+
+ttnn_status launch_side_gather(const SideSpec& s, const void* src, int64_t src_ld, void* out,
+                               cudaStream_t st) {
+  int64_t rows = 1;
+  for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];
+  const int64_t n = rows * s.total_cols;
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), 65535);
+  switch (s.store) {
+    case 0:
+      side_gather_kernel<uint64_t><<<(unsigned)blocks, 256, 0, st>>>(s, (const uint64_t*)src, src_ld,
+                                                                     (uint64_t*)out);
+      break;
+    case 1:
+      side_gather_kernel<uint32_t><<<(unsigned)blocks, 256, 0, st>>>(s, (const uint32_t*)src, src_ld,
+                                                                     (uint32_t*)out);
+      break;
+    case 2:
+      side_gather_kernel<uint16_t><<<(unsigned)blocks, 256, 0, st>>>(s, (const uint16_t*)src, src_ld,
+                                                                     (uint16_t*)out);
+      break;
+    default:
+      side_gather_kernel<uint8_t><<<(unsigned)blocks, 256, 0, st>>>(s, (const uint8_t*)src, src_ld,
+                                                                    (uint8_t*)out);
+      break;
+  }
+  return check_launch("side_gather_kernel");
+}
+
 ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st) {
   int64_t rows = 1;
   for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];

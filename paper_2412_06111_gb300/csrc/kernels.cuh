@@ -75,6 +75,11 @@ struct SideSpec {
   int64_t ld = 0;                 // leading dim (>= rows)
 };
 ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st);
+// The side block of a box cut from the whole-tensor block `src` (the same
+// values: a gather of the box's rows); src is [total_cols][prod full] with
+// leading dimension src_ld, in the storage format s.store.
+ttnn_status launch_side_gather(const SideSpec& s, const void* src, int64_t src_ld, void* out,
+                               cudaStream_t st);
 
 // misc
 ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st);

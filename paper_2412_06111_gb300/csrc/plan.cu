@@ -719,6 +719,13 @@ ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int6
     s.total_cols = P.wLpad;
   }
   s.ld = ld;
+  // a box of a plan with cached whole-tensor blocks: cut its rows from them
+  const void* cache = which == 0 ? P.sideR : P.sideL;
+  if (!box.full && cache) {
+    int64_t nfull = 1;
+    for (int k = 0; k < s.nmodes; ++k) nfull *= s.full[k];
+    return launch_side_gather(s, cache, nfull, out, st);
+  }
   return launch_side(s, out, st);
 }
 
@@ -733,6 +740,7 @@ ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, 
   s.total_cols = c.s;
   s.store = P.walk_f64 ? 0 : 1;
   s.ld = ld;
+  if (!box.full && P.yW) return launch_side_gather(s, P.yW, c.n, out, st);
   return launch_side(s, out, st);
 }
 
