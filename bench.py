@@ -92,16 +92,18 @@ class Clocks:
 
 def _pass_traffic():
     """DRAM bytes per pass_kernel launch from the committed ncu summary, or
-    None once the kernel source differs from the one that was profiled."""
+    None once the kernel's sources differ from the ones that were profiled."""
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
     prof = os.path.join(root, "profiles", "pass_kernel_64p5_bf16.md")
-    src = os.path.join(root, "paper_2412_06111_gb300", "csrc", "pass_tc.cu")
+    h = hashlib.sha256()
     try:
         text = open(prof).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for f in ("pass_tc.cu", "tc_ptx.cuh"):
+            h.update(open(os.path.join(root, "paper_2412_06111_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
+    digest = h.hexdigest()
     vals = {}
     for line in text.splitlines():
         key, sep, val = line.partition(": ")
