@@ -177,6 +177,73 @@ ttnn_status launch_side_gather(const SideSpec& s, const void* src, int64_t src_l
   return check_launch("side_gather_kernel");
 }
 
+constexpr int kGatherJobs = 32;
+struct GatherBatch {
+  int n;
+  int64_t start[kGatherJobs + 1];   // prefix sums of blocks
+  GatherJob jobs[kGatherJobs];
+};
+
+template <typename T>
+__device__ void gather_rows(const GatherJob& g, int64_t e) {
+  const SideSpec& s = g.s;
+  int64_t rows = 1;
+  for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];
+  if (e >= rows * s.total_cols) return;
+  const int64_t c = e / rows, row = e - c * rows;
+  int64_t rem = row, full = 0, stride = 1;
+  for (int m = s.nmodes - 1; m >= 0; --m) {
+    const int64_t i = rem % s.ext[m];
+    rem /= s.ext[m];
+    full += (s.off[m] + i) * stride;
+    stride *= s.full[m];
+  }
+  ((T*)g.out)[c * s.ld + row] = ((const T*)g.src)[c * g.src_ld + full];
+}
+
+__global__ void side_gather_batch_kernel(const __grid_constant__ GatherBatch b) {
+  const int64_t blk = blockIdx.x;
+  int lo = 0, hi = b.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (b.start[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const GatherJob& g = b.jobs[lo];
+  const int64_t e = (blk - b.start[lo]) * blockDim.x + threadIdx.x;
+  switch (g.s.store) {
+    case 0: gather_rows<uint64_t>(g, e); break;
+    case 1: gather_rows<uint32_t>(g, e); break;
+    case 2: gather_rows<uint16_t>(g, e); break;
+    default: gather_rows<uint8_t>(g, e); break;
+  }
+}
+
+ttnn_status launch_side_gather_batch(const GatherJob* jobs, int n, cudaStream_t st) {
+  for (int j0 = 0; j0 < n; j0 += kGatherJobs) {
+    GatherBatch b;
+    b.n = 0;
+    b.start[0] = 0;
+    for (int j = j0; j < n && b.n < kGatherJobs; ++j) {
+      int64_t rows = 1;
+      for (int m = 0; m < jobs[j].s.nmodes; ++m) rows *= jobs[j].s.ext[m];
+      const int64_t blocks = ceil_div(rows * jobs[j].s.total_cols, 256);
+      if (blocks == 0) continue;
+      b.jobs[b.n] = jobs[j];
+      b.start[b.n + 1] = b.start[b.n] + blocks;
+      ++b.n;
+    }
+    if (b.n == 0) continue;
+    if (b.start[b.n] >= (int64_t(1) << 31)) {
+      set_error("side gather batch too large");
+      return TTNN_EUNSUPPORTED;
+    }
+    side_gather_batch_kernel<<<(unsigned)b.start[b.n], 256, 0, st>>>(b);
+    TTNN_TRY(check_launch("side_gather_batch_kernel"));
+  }
+  return TTNN_OK;
+}
+
 ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st) {
   int64_t rows = 1;
   for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];

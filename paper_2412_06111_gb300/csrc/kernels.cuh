@@ -80,6 +80,14 @@ ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st);
 // leading dimension src_ld, in the storage format s.store.
 ttnn_status launch_side_gather(const SideSpec& s, const void* src, int64_t src_ld, void* out,
                                cudaStream_t st);
+// Many such gathers (possibly of different plans and formats) in few launches.
+struct GatherJob {
+  SideSpec s;
+  const void* src = nullptr;
+  int64_t src_ld = 0;
+  void* out = nullptr;
+};
+ttnn_status launch_side_gather_batch(const GatherJob* jobs, int n, cudaStream_t st);
 
 // misc
 ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st);

@@ -700,7 +700,7 @@ static void side_spec_common(ttnn_plan_s& P, const Box& box, int lo, int hi, Sid
 static int store_bytes(int store) { return store == 0 ? 8 : store == 1 ? 4 : store == 2 ? 2 : 1; }
 
 ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
-                      cudaStream_t st) {
+                      cudaStream_t st, std::vector<GatherJob>* defer) {
   SideSpec s;
   if (which == 0) {   // B_R: rows over R modes
     side_spec_common(P, box, P.Rlo, P.Rhi, s);
@@ -724,13 +724,18 @@ ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int6
   if (!box.full && cache) {
     int64_t nfull = 1;
     for (int k = 0; k < s.nmodes; ++k) nfull *= s.full[k];
+    if (defer) {
+      defer->push_back(GatherJob{s, cache, nfull, out});
+      return TTNN_OK;
+    }
     return launch_side_gather(s, cache, nfull, out, st);
   }
   return launch_side(s, out, st);
 }
 
 // Walk-type copy of the pass Y block (rows over the Y child's box modes).
-ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st) {
+ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st,
+                         std::vector<GatherJob>* defer) {
   SideSpec s;
   const TNode& c = P.nodes[P.ychild];
   side_spec_common(P, box, c.lo, c.hi, s);
@@ -740,8 +745,20 @@ ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, 
   s.total_cols = c.s;
   s.store = P.walk_f64 ? 0 : 1;
   s.ld = ld;
-  if (!box.full && P.yW) return launch_side_gather(s, P.yW, c.n, out, st);
+  if (!box.full && P.yW) {
+    if (defer) {
+      defer->push_back(GatherJob{s, P.yW, c.n, out});
+      return TTNN_OK;
+    }
+    return launch_side_gather(s, P.yW, c.n, out, st);
+  }
   return launch_side(s, out, st);
+}
+
+ttnn_status UpdateBatch::launch(cudaStream_t st) {
+  if (!gathers.empty()) TTNN_TRY(launch_side_gather_batch(gathers.data(), (int)gathers.size(), st));
+  for (auto& p : passes) TTNN_TRY(p(st));
+  return walks.run(st);
 }
 
 ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need) {
@@ -761,7 +778,7 @@ ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need) {
 
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
-                             int64_t* peak, Program* merge) {
+                             int64_t* peak, UpdateBatch* batch) {
   if (!dry) {
     int64_t need = 0;
     TTNN_TRY(dense_update_need(P, box, &need));
@@ -788,12 +805,12 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   if (box.full && P.sideL) sL = P.sideL;
   if (P.wR > 0 && !sR) {
     char* b = ws.alloc((int64_t)P.wRpad * nR * sb);
-    if (!dry) TTNN_TRY(make_side(P, box, 0, b, nR, st));
+    if (!dry) TTNN_TRY(make_side(P, box, 0, b, nR, st, batch ? &batch->gathers : nullptr));
     sR = b;
   }
   if (P.wL > 0 && !sL) {
     char* b = ws.alloc((int64_t)P.wLpad * nL * sb);
-    if (!dry) TTNN_TRY(make_side(P, box, 1, b, nL, st));
+    if (!dry) TTNN_TRY(make_side(P, box, 1, b, nL, st, batch ? &batch->gathers : nullptr));
     sL = b;
   }
   if (!P.nodes[P.ychild].identity) {
@@ -805,7 +822,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       C.yw = (const char*)P.yW;
     } else {
       char* b = ws.alloc((int64_t)yc.s * ny * eb);
-      if (!dry) TTNN_TRY(make_side_yw(P, box, b, ny, st));
+      if (!dry) TTNN_TRY(make_side_yw(P, box, b, ny, st, batch ? &batch->gathers : nullptr));
       C.yw = b;
     }
   }
@@ -828,10 +845,16 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
                     &need));
     char* tw = ws.alloc(need);
     if (!dry) {
-      TTNN_TRY(launch(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, st, false,
-                      nullptr));
       ++P.n_tc_pass;
+      auto go = [&P, launch, data, nL, nR, sR, sL, D1, D2, tile_scale, tw, need](cudaStream_t s) {
+        return launch(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, s, false,
+                      nullptr);
+      };
+      if (batch) batch->passes.push_back(go);
+      else TTNN_TRY(go(st));
     }
+    // released: in stream order the walk (which reuses the bytes) runs after
+    // the pass, deferred or not
     ws.top = mark;
   } else {
     if (P.pass_store == 3 || P.dtype == TTNN_BF16X2) {
@@ -849,7 +872,10 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       const int ns = gemm_choose_split(g);
       const int64_t mark = ws.top;
       char* part = ns > 1 ? ws.alloc((int64_t)ns * nL * P.wRpad * eb) : nullptr;
-      if (!dry) TTNN_TRY(launch_gemm(g, ns, part, st));
+      if (!dry) {
+        if (batch) batch->passes.push_back([g, ns, part](cudaStream_t s) { return launch_gemm(g, ns, part, s); });
+        else TTNN_TRY(launch_gemm(g, ns, part, st));
+      }
       ws.top = mark;
     }
     if (P.wL > 0) {
@@ -861,7 +887,10 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       const int ns = gemm_choose_split(g);
       const int64_t mark = ws.top;
       char* part = ns > 1 ? ws.alloc((int64_t)ns * nR * P.wLpad * eb) : nullptr;
-      if (!dry) TTNN_TRY(launch_gemm(g, ns, part, st));
+      if (!dry) {
+        if (batch) batch->passes.push_back([g, ns, part](cudaStream_t s) { return launch_gemm(g, ns, part, s); });
+        else TTNN_TRY(launch_gemm(g, ns, part, st));
+      }
       ws.top = mark;
     }
   }
@@ -999,7 +1028,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     TTNN_TRY(scatter_into(C, cur, state_at(C, acc, root.ps_off), os, lambda));
   }
   if (!dry) {
-    if (merge) merge->absorb(prog);
+    if (batch) batch->walks.absorb(prog);
     else TTNN_TRY(prog.run(st));
   }
   P.last_walk_ops = (int)prog.size();

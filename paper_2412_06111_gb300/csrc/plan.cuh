@@ -2,6 +2,7 @@
 #pragma once
 
 #include <array>
+#include <functional>
 #include <map>
 #include <vector>
 
@@ -112,11 +113,20 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
 ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need);
 // A real (non-dry) update first checks its workspace need against the plan's
 // workspace and returns TTNN_ENOMEM, launching nothing, when it does not fit.
-// merge != NULL: the tree-walk program is appended to *merge instead of run
-// (the caller runs it; the pass has been launched already).
+// Work of several dense updates recorded for joint launches: the box side
+// blocks cut from cached blocks (one batched gather), the first-level
+// passes (launched in order after the gathers), and the tree walks (one
+// merged program after the passes).
+struct UpdateBatch {
+  std::vector<GatherJob> gathers;
+  std::vector<std::function<ttnn_status(cudaStream_t)>> passes;
+  Program walks;
+  ttnn_status launch(cudaStream_t st);
+};
+// batch != NULL: nothing is launched; the update's work is appended to *batch.
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
-                             int64_t* peak, ttnn::Program* merge = nullptr);
+                             int64_t* peak, UpdateBatch* batch = nullptr);
 // CP term update (structured.cu): factors are d device pointers, n_mu x Q
 // row-major binary64; weights host [Q].
 ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weights,
@@ -129,9 +139,12 @@ ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores
 // Per-128x128-tile E4M3 quantisation of a binary32 rows x cols matrix (pass_cvt.cu).
 ttnn_status launch_quantize_fp8(const float* src, int64_t rows, int64_t cols, uint8_t* dst,
                                 float* scales, cudaStream_t st);
+// defer != NULL: a block that is a gather from the cached blocks is appended
+// to *defer instead of launched (blocks that need computing are launched).
 ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
-                      cudaStream_t st);
-ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st);
+                      cudaStream_t st, std::vector<GatherJob>* defer = nullptr);
+ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st,
+                         std::vector<GatherJob>* defer = nullptr);
 // records an event on `st` if profiling is on (returns nullptr otherwise)
 cudaEvent_t prof_event(ttnn_plan_s& P, cudaStream_t st);
 void prof_push(ttnn_plan_s& P, int phase, cudaEvent_t a, cudaEvent_t b);

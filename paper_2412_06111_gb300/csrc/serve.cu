@@ -9,10 +9,12 @@
 // every stream sees its requests in submission order -- launches the
 // first-level pass of every update in the batch, then runs the tree walks of
 // all of them as one merged program (each dependency level of every walk in
-// one launch), then the recoveries; completion is tracked by CUDA events, so
-// a worker records the next batch while the device runs the previous ones.  Streams are admitted while the device
-// memory of all open streams stays within the server's budget.  Every wait
-// of a caller is bounded.
+// one launch), then the recoveries; the box side blocks of the whole batch
+// are cut from the cached blocks in one gather launch first.  Completion is
+// tracked by CUDA events, so a worker records the next batch while the device
+// runs the previous ones.  Streams are admitted while the device memory of
+// all open streams stays within the server's budget.  Every wait of a
+// caller is bounded.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -209,16 +211,17 @@ void worker_main(ttnn_server_s* S, int k) {
     const size_t nb = f.reqs.size();
     f.st.assign(nb, TTNN_OK);
     f.msg.assign(nb, std::string());
-    // updates: every first-level pass now, the walks as one merged program
-    Program merged;
+    // updates: the batch's box side blocks in one gather, then every
+    // first-level pass, then the walks as one merged program
+    UpdateBatch ub;
     for (size_t i = 0; i < nb; ++i) {
       const Request& r = f.reqs[i];
       if (r.kind != 0) continue;
       f.st[i] = run_dense_update(*who[i].first, who[i].second->acc, r.data, r.box, r.scale,
-                                 r.lambda, W.st, false, nullptr, &merged);
+                                 r.lambda, W.st, false, nullptr, &ub);
       if (f.st[i] != TTNN_OK) f.msg[i] = last_error();
     }
-    const ttnn_status ms = merged.run(W.st);
+    const ttnn_status ms = ub.launch(W.st);
     if (ms != TTNN_OK) {
       const std::string m = last_error();
       for (size_t i = 0; i < nb; ++i)
