@@ -15,6 +15,7 @@ struct Contract {
   int64_t P = 1, NI = 1, NB = 1, Q = 1, J = 1;
   int64_t isP = 0, isI = 0, isQ = 0, isJ = 0;
   int64_t wsI = 0, wsB = 0, wsQ = 0, wsJ = 0;
+  int64_t wsP = 0;   // weight stride over the prefix index (a sketch axis shared from before)
   int64_t osP = 0, osB = 0, osQ = 0, osJ = 0;
   const void* in = nullptr;
   const void* w = nullptr;

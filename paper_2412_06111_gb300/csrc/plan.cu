@@ -468,6 +468,24 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
     c.wsQ = wsX;
     oax = in.ax;
     oax.erase(oax.begin() + k);
+  } else if (shared == 0 && k == 1) {
+    // the shared axis is the whole prefix: W(i, x) indexed by p
+    c.P = in.ax[0].size;
+    c.isP = vstride(in, 0);
+    c.wsP = wsX;
+    if (k < L) {
+      c.Q = 1;
+      for (int a = k + 1; a < L; ++a) c.Q *= in.ax[a].size;
+      c.isQ = (k < L - 1) ? vstride(in, L - 1) : 0;
+      c.J = in.ax[L].size;
+      c.isJ = 1;
+      if (k + 1 <= L - 1 && in.ld != in.ax[L].size) {
+        set_error("internal: non-contiguous column group");
+        return TTNN_EUNSUPPORTED;
+      }
+    }
+    oax = in.ax;
+    oax.erase(oax.begin() + k);
   } else {
     set_error("internal: unsupported shared axis");
     return TTNN_EUNSUPPORTED;
@@ -501,9 +519,55 @@ static const char* facY(Ctx& C, int mode) { return C.facw + (C.P.y_off[mode] + C
 // the modes (Sec. 7: Y_t = kr of its modes' Y_mu, columns shared).
 // With first_done the sketch axis already replaces mode hi - 1 (a shared
 // first mode product) and only the Khatri-Rao steps remain.
+// Mode of [lo, hi) at which a Khatri-Rao Y chain over `in` creates its sketch
+// axis: the mode with the largest extent when it is the view's first axis
+// (every later mode is then contracted against the sketch axis as the whole
+// prefix), else the last mode.  Creating the axis at a small mode (a slice's
+// fixed mode has extent 1) would multiply the intermediate by s.
+static int chain_first(const View& in, int lo, int hi) {
+  int best = hi - 1;
+  if (find_ax(in, AX_MODE, lo) == 0) {
+    int64_t big = -1;
+    for (int m = lo; m < hi; ++m) {
+      const int k = find_ax(in, AX_MODE, m);
+      if (k >= 0 && in.ax[k].size > big) {
+        big = in.ax[k].size;
+        best = m;
+      }
+    }
+    if (best != lo) best = hi - 1;
+    // keep the last mode when it is as large as the first
+    const int kl = find_ax(in, AX_MODE, hi - 1), k0 = find_ax(in, AX_MODE, lo);
+    if (kl >= 0 && k0 >= 0 && in.ax[kl].size >= in.ax[k0].size) best = hi - 1;
+  }
+  return best;
+}
+
+// Khatri-Rao contraction of the modes [lo, hi) of `in` with the Y factors,
+// producing one sketch axis (kind AX_SK, id = node) of size s at the place of
+// the modes (Sec. 7: Y_t = kr of its modes' Y_mu, columns shared).
+// With first_done the sketch axis already replaces mode hi - 1 (a shared
+// first mode product) and only the Khatri-Rao steps remain.
 static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int s, View* out,
                            bool first_done = false) {
   View cur = in;
+  const int first = first_done ? hi - 1 : chain_first(in, lo, hi);
+  if (first == lo && first != hi - 1) {
+    // sketch axis at the first (largest) mode, then the others against it
+    const int k0 = find_ax(cur, AX_MODE, lo);
+    Ax nax{AX_SK, node, s, 0};
+    View nx;
+    TTNN_TRY(contract_view(C, cur, k0, facY(C, lo), C.P.smax, 1, -1, &nax, &nx));
+    cur = nx;
+    for (int mode = lo + 1; mode < hi; ++mode) {
+      const int k = find_ax(cur, AX_MODE, mode);
+      if (k != 1) { set_error("internal: Khatri-Rao chain layout"); return TTNN_EUNSUPPORTED; }
+      TTNN_TRY(contract_view(C, cur, k, facY(C, mode), C.P.smax, 1, 0, nullptr, &nx));
+      cur = nx;
+    }
+    *out = cur;
+    return TTNN_OK;
+  }
   for (int mode = hi - 1; mode >= lo; --mode) {
     if (first_done && mode == hi - 1) continue;
     const int k = find_ax(cur, AX_MODE, mode);
@@ -610,7 +674,8 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
     // Omega_t and Psi_t both start by contracting t's last mode with the same
     // Y columns when the last child's sketch size equals s_t: do it once.
     const TNode* lastc = nd.leaf ? nullptr : &P.nodes[nd.ch.back()];
-    const bool share = v != P.ychild && lastc && !lastc->identity && lastc->s == nd.s;
+    const bool share = v != P.ychild && lastc && !lastc->identity && lastc->s == nd.s &&
+                       chain_first(Gt, nd.lo, nd.hi) == nd.hi - 1;
     View z;
     if (share) {
       const int k = find_ax(Gt, AX_MODE, nd.hi - 1);

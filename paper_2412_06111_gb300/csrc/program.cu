@@ -51,7 +51,8 @@ __device__ void dev_contract(const DevOp& op, int64_t blk) {
     const int64_t i1 = min(c.NI, i0 + op.chunk);
     const Tin* ip = (const Tin*)c.in + (int64_t)p * c.isP + (int64_t)q * c.isQ + (int64_t)j * c.isJ;
     if (c.w) {
-      const Tw* wp = (const Tw*)c.w + (int64_t)b * c.wsB + (int64_t)q * c.wsQ + (int64_t)j * c.wsJ;
+      const Tw* wp = (const Tw*)c.w + (int64_t)p * c.wsP + (int64_t)b * c.wsB + (int64_t)q * c.wsQ +
+                     (int64_t)j * c.wsJ;
 #pragma unroll 4
       for (int64_t i = i0 + lg; i < i1; i += g) acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
     } else {
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(kExecThreads) level_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 static bool mp_tiling(Op& op) {
   const Contract& c = op.c;
-  if (!c.w || c.wsQ != 0 || c.wsJ != 0 || c.NI < 8 || c.NB > 64) return false;
+  if (!c.w || c.wsQ != 0 || c.wsJ != 0 || c.wsP != 0 || c.NI < 8 || c.NB > 64) return false;
   if (!(op.tin == op.tw && op.tw == op.tout)) return false;
   if (op.tout == ET_F64) return false;    // few FP64 units per SM: spread FP64 work thin instead
   if (c.P * c.Q * c.NB * c.J < 8192) return false;
@@ -482,7 +483,7 @@ int64_t plan_contract(Op& op) {
     return 0;
   }
   // long reductions with few outputs: split-K through shared-memory tiles
-  if (c.w && c.wsQ == 0 && c.wsJ == 0 && op.tin == ET_F32 && op.tw == ET_F32 &&
+  if (c.w && c.wsQ == 0 && c.wsJ == 0 && c.wsP == 0 && op.tin == ET_F32 && op.tw == ET_F32 &&
       op.tout == ET_F32 && c.NI >= 2048 && c.NB <= 64 && c.J <= 64 &&
       c.NB * c.J <= 16 * kExecThreads && c.P * c.Q <= 64) {
     const int64_t items = c.P * c.Q;
