@@ -684,36 +684,3 @@ ttnn_status launch_finite_check(const void* data, int64_t n, int type, int* flag
 }
 
 }  // namespace ttnn
-
-namespace ttnn {
-
-template <typename T>
-__global__ void scatter_kernel(Scatter s) {
-  int64_t total = 1;
-  for (int a = 0; a < s.nd; ++a) total *= s.size[a];
-  const T* in = (const T*)s.in;
-  T* out = (T*)s.out;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = e, io = 0, oo = 0;
-    for (int a = s.nd - 1; a >= 0; --a) {
-      const int64_t i = rem % s.size[a];
-      rem /= s.size[a];
-      io += i * s.is[a];
-      oo += (s.off[a] + i) * s.os[a];
-    }
-    out[oo] = (T)(out[oo] + (T)s.alpha * in[io]);
-  }
-}
-
-ttnn_status launch_scatter_add(const Scatter& s, int f64, cudaStream_t st) {
-  int64_t total = 1;
-  for (int a = 0; a < s.nd; ++a) total *= s.size[a];
-  if (total == 0) return TTNN_OK;
-  const int64_t blocks = std::min<int64_t>(ceil_div(total, 256), (int64_t)num_sms() * 16);
-  if (f64) scatter_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(s);
-  else scatter_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(s);
-  return check_launch("scatter_kernel");
-}
-
-}  // namespace ttnn

@@ -113,14 +113,18 @@ constexpr int kMaxRecoverR = 64;
 }  // namespace ttnn
 
 namespace ttnn {
-// out[sum_a (off_a + i_a) * os_a] += alpha * in[sum_a i_a * is_a] over the
-// box of sizes `size` (up to 12 axes); in/out of the same type (f32 / f64).
+constexpr int kMaxColScales = 8;
+// out[sum_a (off_a + i_a) * os_a] += alpha * in[sum_a i_a * is_a] * prod_k
+// jsc[k][i_jaxis] over the box of sizes `size` (up to 12 axes); in/out/jsc of
+// the same type (f32 / f64).  The column scales are the rows X_mu[c, :] of
+// modes a box fixes, applied where the sketch is added.
 struct Scatter {
+  int njsc = 0, jaxis = -1;
+  const void* jsc[kMaxColScales] = {nullptr};
   int nd = 0;
   int64_t size[12] = {0}, is[12] = {0}, os[12] = {0}, off[12] = {0};
   const void* in = nullptr;
   void* out = nullptr;
   double alpha = 1.0;
 };
-ttnn_status launch_scatter_add(const Scatter& s, int f64, cudaStream_t st);
 }  // namespace ttnn

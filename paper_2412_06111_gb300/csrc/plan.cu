@@ -382,6 +382,11 @@ struct View {
   char* ptr;
   std::vector<Ax> ax;
   int64_t ld;      // stride of the next-to-last axis
+  // column scales not yet applied: the view's values times prod_k jsc[k][j]
+  // on the column axis (rows X_mu[c, :] of box-fixed modes; they commute
+  // with every contraction over the other axes and are applied by the
+  // scatter into the state)
+  std::vector<const char*> jsc;
 };
 
 static int64_t vstride(const View& v, int k) {
@@ -493,6 +498,7 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
   View o;
   o.ax = oax;
   o.ld = o.ax.back().size;
+  o.jsc = in.jsc;
   const int64_t total = vsize(o);
   o.ptr = C.ws.alloc(total * C.eb);
   c.out = o.ptr;
@@ -589,7 +595,18 @@ static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int
 static ttnn_status x_mode(Ctx& C, const View& in, int mode, View* out) {
   const int k = find_ax(in, AX_MODE, mode);
   if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
-  return contract_view(C, in, k, facX(C, mode), C.P.rmax, 1, (int)in.ax.size() - 1, nullptr, out);
+  const int L = (int)in.ax.size() - 1;
+  if (in.ax[k].size == 1 && k < L && in.jsc.size() < (size_t)kMaxColScales &&
+      in.ax[L].kind == AX_J) {
+    // a mode the box fixes: the contraction is a column scale by the row
+    // X_mu[c, :]; drop the axis (no data moves) and defer the scale
+    View o = in;
+    o.ax.erase(o.ax.begin() + k);
+    o.jsc.push_back(facX(C, mode));
+    *out = o;
+    return TTNN_OK;
+  }
+  return contract_view(C, in, k, facX(C, mode), C.P.rmax, 1, L, nullptr, out);
 }
 
 // STTNN: contraction of group s with E_s = Y_s XT_s (Y chain, then XT_s on
@@ -618,6 +635,15 @@ static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::ve
   s.in = v.ptr;
   s.out = base;
   s.alpha = alpha;
+  if (!v.jsc.empty()) {
+    s.jaxis = find_ax(v, AX_J, -1);
+    if (s.jaxis < 0 || v.jsc.size() > (size_t)kMaxColScales) {
+      set_error("internal: column scales without a column axis");
+      return TTNN_EUNSUPPORTED;
+    }
+    s.njsc = (int)v.jsc.size();
+    for (int k = 0; k < s.njsc; ++k) s.jsc[k] = v.jsc[k];
+  }
   Op op;
   op.kind = OP_SCATTER;
   op.tin = op.tw = op.tout = C.et;
