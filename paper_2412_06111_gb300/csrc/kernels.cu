@@ -244,6 +244,136 @@ ttnn_status launch_side_gather_batch(const GatherJob* jobs, int n, cudaStream_t 
   return TTNN_OK;
 }
 
+// ---------------------------------------------------------------------------
+// rank-one pass: a box whose other side is a single index
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float load_acc(const uint16_t* p, int64_t i, float) {
+  return __uint_as_float((uint32_t)p[i] << 16);   // bfloat16 -> binary32, exact
+}
+__device__ __forceinline__ float load_acc(const float* p, int64_t i, float) { return p[i]; }
+__device__ __forceinline__ double load_acc(const double* p, int64_t i, double) { return p[i]; }
+
+constexpr int kGemvCols = 8;
+
+template <typename Tm, typename Ts, typename Tacc>
+__global__ void __launch_bounds__(256) side_gemv_kernel(SideSpec s, const Ts* src, int64_t src_ld,
+                                                        int cut, const Tm* m, int64_t rows,
+                                                        int cols, int64_t rpb, Tacc* part) {
+  __shared__ Tacc red[8][kGemvCols];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * rpb;
+  const int64_t r1 = r0 + rpb < rows ? r0 + rpb : rows;
+  for (int c0 = 0; c0 < cols; c0 += kGemvCols) {
+    Tacc acc[kGemvCols];
+#pragma unroll
+    for (int k = 0; k < kGemvCols; ++k) acc[k] = 0;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+      int64_t f = row;
+      if (cut) {
+        int64_t rem = row, stride = 1;
+        f = 0;
+        for (int mm = s.nmodes - 1; mm >= 0; --mm) {
+          const int64_t i = rem % s.ext[mm];
+          rem /= s.ext[mm];
+          f += (s.off[mm] + i) * stride;
+          stride *= s.full[mm];
+        }
+      }
+      const Tacc mv = load_acc(m, row, Tacc(0));
+#pragma unroll
+      for (int k = 0; k < kGemvCols; ++k)
+        if (c0 + k < cols) acc[k] += mv * load_acc(src, (int64_t)(c0 + k) * src_ld + f, Tacc(0));
+    }
+#pragma unroll
+    for (int k = 0; k < kGemvCols; ++k) {
+      Tacc v = acc[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kGemvCols && c0 + (int)threadIdx.x < cols) {
+      Tacc t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+      part[(int64_t)blockIdx.x * cols + c0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename Tacc>
+__global__ void gemv_reduce_kernel(const Tacc* part, int nblk, int cols, int cols_pad, Tacc* D) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols_pad; c += gridDim.x * blockDim.x) {
+    Tacc t = 0;
+    if (c < cols)
+      for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * cols + c];
+    D[c] = t;
+  }
+}
+
+ttnn_status launch_side_gemv(const SideSpec& s, const void* src, int64_t src_ld, bool cut,
+                             const void* m, int m_store, int64_t rows, int cols, int cols_pad,
+                             void* D, int d_f64, void* part, int64_t part_bytes, cudaStream_t st,
+                             bool dry, int64_t* need) {
+  const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 1024), (int64_t)num_sms() * 4));
+  const int64_t rpb = ceil_div(rows, nblk);
+  const int64_t bytes = nblk * std::max(cols, 1) * (d_f64 ? 8 : 4);
+  if (dry) {
+    if (need) *need = bytes;
+    return TTNN_OK;
+  }
+  if (part_bytes < bytes) {
+    set_error("rank-one pass: scratch too small");
+    return TTNN_ENOMEM;
+  }
+  if (cols_pad == 0) return TTNN_OK;
+  if (d_f64) {
+    if (m_store != 0 || s.store != 0) {
+      set_error("rank-one pass: unsupported formats");
+      return TTNN_EUNSUPPORTED;
+    }
+    if (cols > 0)
+      side_gemv_kernel<double, double, double><<<(unsigned)nblk, 256, 0, st>>>(
+          s, (const double*)src, src_ld, cut ? 1 : 0, (const double*)m, rows, cols, rpb, (double*)part);
+  } else if (m_store == 1 && s.store == 1) {
+    if (cols > 0)
+      side_gemv_kernel<float, float, float><<<(unsigned)nblk, 256, 0, st>>>(
+          s, (const float*)src, src_ld, cut ? 1 : 0, (const float*)m, rows, cols, rpb, (float*)part);
+  } else if (m_store == 2 && s.store == 2) {
+    if (cols > 0)
+      side_gemv_kernel<uint16_t, uint16_t, float><<<(unsigned)nblk, 256, 0, st>>>(
+          s, (const uint16_t*)src, src_ld, cut ? 1 : 0, (const uint16_t*)m, rows, cols, rpb, (float*)part);
+  } else {
+    set_error("rank-one pass: unsupported formats");
+    return TTNN_EUNSUPPORTED;
+  }
+  if (cols > 0) TTNN_TRY(check_launch("side_gemv_kernel"));
+  const unsigned rb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cols_pad, 256), 64));
+  if (d_f64) gemv_reduce_kernel<double><<<rb, 256, 0, st>>>((const double*)part, (int)nblk, cols, cols_pad, (double*)D);
+  else gemv_reduce_kernel<float><<<rb, 256, 0, st>>>((const float*)part, (int)nblk, cols, cols_pad, (float*)D);
+  return check_launch("gemv_reduce_kernel");
+}
+
+template <typename Ts, typename Td>
+__global__ void to_walk_kernel(const Ts* src, Td* dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (Td)load_acc(src, e, Td(0));
+}
+
+ttnn_status launch_to_walk(const void* src, int src_store, void* dst, int d_f64, int64_t n,
+                           cudaStream_t st) {
+  if (n == 0) return TTNN_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+  if (!d_f64 && src_store == 2) to_walk_kernel<uint16_t, float><<<blocks, 256, 0, st>>>((const uint16_t*)src, (float*)dst, n);
+  else if (!d_f64 && src_store == 1) to_walk_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)src, (float*)dst, n);
+  else if (d_f64 && src_store == 0) to_walk_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)src, (double*)dst, n);
+  else {
+    set_error("walk copy: unsupported formats");
+    return TTNN_EUNSUPPORTED;
+  }
+  return check_launch("to_walk_kernel");
+}
+
 ttnn_status launch_side(const SideSpec& s, void* out, cudaStream_t st) {
   int64_t rows = 1;
   for (int m = 0; m < s.nmodes; ++m) rows *= s.ext[m];

@@ -90,6 +90,25 @@ struct GatherJob {
 };
 ttnn_status launch_side_gather_batch(const GatherJob* jobs, int n, cudaStream_t st);
 
+// Pass products of a box whose other side is a single index (every mode of
+// that side fixed): the product against the fixed side is rank one and is
+// left to the walk as a broadcast, and the product against this side is a
+// matrix-vector product with the side block.
+//   D[c] = sum_row m[row] * B[c][map(row)]   (c < cols; zero up to cols_pad)
+// m: the box's rows (storage format m_store: 0 f64, 1 f32, 2 bf16); B: a side
+// block [cols][...] with leading dimension src_ld in format s.store; map(row)
+// is the row's place in a whole-tensor block (s.ext/off/full) when `cut`,
+// else the row itself.  Accumulates in the walk type (f64 when d_f64) per
+// block of rows, then sums the block partials in a fixed order
+// (deterministic).  With dry, only reports the scratch bytes (`need`).
+ttnn_status launch_side_gemv(const SideSpec& s, const void* src, int64_t src_ld, bool cut,
+                             const void* m, int m_store, int64_t rows, int cols, int cols_pad,
+                             void* D, int d_f64, void* part, int64_t part_bytes, cudaStream_t st,
+                             bool dry, int64_t* need);
+// dst[e] = src[e] in the walk type (f32, or f64 when d_f64) for e < n.
+ttnn_status launch_to_walk(const void* src, int src_store, void* dst, int d_f64, int64_t n,
+                           cudaStream_t st);
+
 // misc
 ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st);
 ttnn_status launch_axpy(void* y, const void* x, double alpha, int64_t n, int is_f64, cudaStream_t st);
@@ -113,16 +132,22 @@ constexpr int kMaxRecoverR = 64;
 }  // namespace ttnn
 
 namespace ttnn {
-constexpr int kMaxColScales = 8;
-// out[sum_a (off_a + i_a) * os_a] += alpha * in[sum_a i_a * is_a] * prod_k
-// jsc[k][i_jaxis] over the box of sizes `size` (up to 12 axes); in/out/jsc of
-// the same type (f32 / f64).  The column scales are the rows X_mu[c, :] of
-// modes a box fixes, applied where the sketch is added.
+constexpr int kMaxScales = 8;
+// out[sum_a (off_a + i_a) * os_a] += alpha * v (or = alpha * v with
+// `assign`) over the box of sizes `size` (up to 12 axes), where
+// v = in[sum_a i_a * is_a] * prod_k sc_k[(e / scdiv_k) % scmod_k] and e is
+// the element's flat index (last axis fastest): scale k is a vector along
+// one axis.  in / out / scales share one type (f32 / f64).  The scales are
+// rows of the DRM factors of modes a box fixes (X_mu[c, :] on the column
+// axis, Y_mu[c, :] on a sketch axis), applied here instead of contracting
+// an extent-1 mode over a whole intermediate.
 struct Scatter {
-  int njsc = 0, jaxis = -1;
-  const void* jsc[kMaxColScales] = {nullptr};
-  int nd = 0;
-  int64_t size[12] = {0}, is[12] = {0}, os[12] = {0}, off[12] = {0};
+  int nd = 0, nsc = 0, assign = 0;
+  int32_t size[12] = {0}, off[12] = {0};
+  int64_t is[12] = {0}, os[12] = {0};
+  const void* sc[kMaxScales] = {nullptr};
+  int64_t scdiv[kMaxScales] = {0};
+  int32_t scmod[kMaxScales] = {0};
   const void* in = nullptr;
   void* out = nullptr;
   double alpha = 1.0;

@@ -172,13 +172,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = 0; u < nu && ok; ++u) {
         const int b = b0 + u, ub = u & 1;
         const int row = b * kTileM;
-        ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag);
-        if (!ok) break;
-        const uint32_t blb = bl_base + ub * bl_bytes;
-        mbar_expect_tx(smem_u32(&bar_blfull[ub]), bl_bytes);
-        tma_2d(blb, &mapBL, row, 0, smem_u32(&bar_blfull[ub]), pol_keep);
-        tma_2d(blb + bl_bytes / 2, &mapBL, row + 64, 0, smem_u32(&bar_blfull[ub]), pol_keep);
-        bl_last[ub] = (u >> 1) & 1;
+        if (p.wLpad > 0) {
+          ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag);
+          if (!ok) break;
+          const uint32_t blb = bl_base + ub * bl_bytes;
+          mbar_expect_tx(smem_u32(&bar_blfull[ub]), bl_bytes);
+          tma_2d(blb, &mapBL, row, 0, smem_u32(&bar_blfull[ub]), pol_keep);
+          tma_2d(blb + bl_bytes / 2, &mapBL, row + 64, 0, smem_u32(&bar_blfull[ub]), pol_keep);
+          bl_last[ub] = (u >> 1) & 1;
+        }
         for (int t = 0; t < nt; ++t) {
           ok = mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1, &abort_flag);
           if (!ok) break;
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = 0; u < nu && ok; ++u) {
         const int buf = u & 1;
         if (u >= 2) ok = mbar_wait(smem_u32(&bar_d1empty[buf]), ((u >> 1) - 1) & 1, &abort_flag);
-        if (ok) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag);
+        if (ok && p.wLpad > 0) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag);
         if (!ok) break;
         fence_after();
         const uint32_t blb = bl_base + buf * bl_bytes;
@@ -237,12 +239,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t db = sdesc(sbr + (kk >> 2) * (br_bytes / 2) + (kk & 3) * 32, 16, 1024);
             mma_bf16(d1, da, db, id1, (t | kk) != 0);
           }
-          const uint32_t d2 = tmem + d2_col + t * p.wLpad;
+          if (p.wLpad > 0) {
+            const uint32_t d2 = tmem + d2_col + t * p.wLpad;
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint64_t da = sdesc(sa + kk * 2048, a_bytes / 2, 1024);
-            const uint64_t db = sdesc(blb + (kk >> 2) * (bl_bytes / 2) + (kk & 3) * 32, 16, 1024);
-            mma_bf16(d2, da, db, id2, (u | kk) != 0);
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t da = sdesc(sa + kk * 2048, a_bytes / 2, 1024);
+              const uint64_t db = sdesc(blb + (kk >> 2) * (bl_bytes / 2) + (kk & 3) * 32, 16, 1024);
+              mma_bf16(d2, da, db, id2, (u | kk) != 0);
+            }
           }
           mma_commit(smem_u32(&bar_empty[stage]));
           if (++stage == S) {
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!ok) break;
-        mma_commit(smem_u32(&bar_blempty[buf]));
+        if (p.wLpad > 0) mma_commit(smem_u32(&bar_blempty[buf]));
         mma_commit(smem_u32(&bar_d1full[buf]));
       }
       if (!ok) {
@@ -370,8 +374,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       abort_flag = 1;
       atomicOr(p.err, 8);
     }
-    // D2 of the column chunk
-    if (nu == 0) {
+    // D2 of the column chunk (none when the plan has no left-side block)
+    if (p.wLpad == 0) {
+      // no D2 product to write
+    } else if (nu == 0) {
       for (int t = 0; t < p.tiles; ++t) {
         const int64_t col = col0 + t * kTileN + r_in;
         if (col >= p.nR) continue;
@@ -535,8 +541,10 @@ static int max_clusters(int C, size_t smem) {
 }
 
 static bool geometry(const ttnn_plan_s& P, int64_t nL, int64_t nR, Geometry* g) {
-  if (P.wRpad < 16 || P.wLpad < 16 || P.wRpad > 256 || P.wLpad > 256) return false;
-  int tiles = (512 - 2 * P.wRpad) / P.wLpad;
+  if (P.wRpad < 16 || (P.wLpad != 0 && P.wLpad < 16) || P.wRpad > 256 || P.wLpad > 256)
+    return false;
+  // without a D2 product (w_L = 0) TMEM holds only the double-buffered D1
+  int tiles = P.wLpad > 0 ? (512 - 2 * P.wRpad) / P.wLpad : kMaxTiles;
   tiles = std::min(tiles, kMaxTiles);
   const int64_t ntile = (nR + kTileN - 1) / kTileN;
   tiles = (int)std::min<int64_t>(tiles, ntile);
@@ -584,7 +592,7 @@ static bool geometry(const ttnn_plan_s& P, int64_t nL, int64_t nR, Geometry* g) 
 
 ttnn_status tc_pass_supported(const ttnn_plan_s& P, int64_t nL, int64_t nR) {
   if (P.dtype != TTNN_BF16 || P.pass_store != 2) return TTNN_EUNSUPPORTED;
-  if (P.wR <= 0 || P.wL <= 0) return TTNN_EUNSUPPORTED;
+  if (P.wR <= 0 || P.wL < 0) return TTNN_EUNSUPPORTED;
   if (nL % 8 != 0 || nR % 8 != 0) return TTNN_EUNSUPPORTED;   // 16-byte TMA row strides
   if (nL >= (int64_t(1) << 31) || nR >= (int64_t(1) << 31)) return TTNN_EUNSUPPORTED;
   tc::Geometry g;
@@ -618,7 +626,8 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
   CUtensorMap mA, mBR, mBL;
   TTNN_TRY(tc::make_map(&mA, A, nR, nL, tc::kTileM));
   TTNN_TRY(tc::make_map(&mBR, sR, nR, P.wRpad, P.wRpad));
-  TTNN_TRY(tc::make_map(&mBL, sL, nL, P.wLpad, P.wLpad));
+  if (P.wLpad > 0) TTNN_TRY(tc::make_map(&mBL, sL, nL, P.wLpad, P.wLpad));
+  else mBL = mBR;   // never read: the kernel forms no D2 product
   tc::Params prm;
   prm.nL = nL;
   prm.nR = nR;
@@ -661,9 +670,11 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
                                                  nL, P.wRpad, (float*)D1);
     TTNN_TRY(check_launch("reduce_partials(D1)"));
   }
-  tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
-                                               nR, P.wLpad, (float*)D2);
-  TTNN_TRY(check_launch("reduce_partials(D2)"));
+  if (P.wLpad > 0) {
+    tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
+                                                 nR, P.wLpad, (float*)D2);
+    TTNN_TRY(check_launch("reduce_partials(D2)"));
+  }
   return TTNN_OK;
 }
 

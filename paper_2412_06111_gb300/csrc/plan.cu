@@ -382,11 +382,21 @@ struct View {
   char* ptr;
   std::vector<Ax> ax;
   int64_t ld;      // stride of the next-to-last axis
-  // column scales not yet applied: the view's values times prod_k jsc[k][j]
-  // on the column axis (rows X_mu[c, :] of box-fixed modes; they commute
+  // scales not yet applied: the view's values times prod_k sc_k[index on the
+  // axis (kind, id)].  They are rows of the DRM factors of box-fixed modes
+  // (X_mu[c, :] on the column axis, Y_mu[c, :] on a sketch axis), commute
   // with every contraction over the other axes and are applied by the
-  // scatter into the state)
-  std::vector<const char*> jsc;
+  // scatter into the state (or by a scaled copy before their own axis is
+  // contracted).
+  struct Scale {
+    int kind, id;
+    const char* ptr;
+  };
+  std::vector<Scale> sc;
+  // > 0: the last axis is a broadcast of this logical size (the data holds
+  // one entry along it, ax.back().size == 1), as in the rank-one products of
+  // a box whose other pass side is a single index
+  int64_t bc = 0;
 };
 
 static int64_t vstride(const View& v, int k) {
@@ -425,9 +435,20 @@ static int find_ax(const View& v, int kind, int id) {
 // axis `nax` at position k, W(i, b) = W[i*wsI + b*wsX].  shared == last or
 // shared == k + 1: the reduction shares that axis' index x with W,
 // W(i, x) = W[i*wsI + x*wsX]; the axis stays.  The output is contiguous.
+static ttnn_status apply_scales(Ctx& C, const View& in, View* out);
+
 static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, int64_t wsI,
                                  int64_t wsX, int shared, const Ax* nax, View* out) {
   const int L = (int)in.ax.size() - 1;
+  bool expand = in.bc > 0 && (k == L || (shared == k + 1 && k + 1 == L));
+  for (const View::Scale& x : in.sc)
+    if (x.kind == in.ax[k].kind && x.id == in.ax[k].id) expand = true;
+  if (expand) {
+    // the contracted axis carries pending scales or a broadcast: apply them
+    View m;
+    TTNN_TRY(apply_scales(C, in, &m));
+    return contract_view(C, m, k, W, wsI, wsX, shared, nax, out);
+  }
   Contract c;
   c.P = 1;
   for (int a = 0; a < k; ++a) c.P *= in.ax[a].size;
@@ -455,11 +476,13 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
     c.Q = 1;
     for (int a = k + 1; a < L; ++a) c.Q *= in.ax[a].size;
     c.isQ = (k < L - 1) ? vstride(in, L - 1) : 0;
-    c.J = in.ax[L].size;
-    c.isJ = 1;
+    // a broadcast column axis becomes real here (W's columns differ)
+    c.J = in.bc > 0 ? in.bc : in.ax[L].size;
+    c.isJ = in.bc > 0 ? 0 : 1;
     c.wsJ = wsX;
     oax = in.ax;
     oax.erase(oax.begin() + k);
+    oax.back().size = c.J;
   } else if (shared == k + 1) {
     c.Q = in.ax[k + 1].size;
     c.isQ = vstride(in, k + 1);
@@ -498,7 +521,8 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
   View o;
   o.ax = oax;
   o.ld = o.ax.back().size;
-  o.jsc = in.jsc;
+  o.sc = in.sc;
+  o.bc = shared == L ? 0 : in.bc;
   const int64_t total = vsize(o);
   o.ptr = C.ws.alloc(total * C.eb);
   c.out = o.ptr;
@@ -520,69 +544,112 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
 static const char* facX(Ctx& C, int mode) { return C.facw + (C.P.x_off[mode] + C.box.off[mode] * C.P.rmax) * C.eb; }
 static const char* facY(Ctx& C, int mode) { return C.facw + (C.P.y_off[mode] + C.box.off[mode] * C.P.smax) * C.eb; }
 
-// Khatri-Rao contraction of the modes [lo, hi) of `in` with the Y factors,
-// producing one sketch axis (kind AX_SK, id = node) of size s at the place of
-// the modes (Sec. 7: Y_t = kr of its modes' Y_mu, columns shared).
-// With first_done the sketch axis already replaces mode hi - 1 (a shared
-// first mode product) and only the Khatri-Rao steps remain.
-// Mode of [lo, hi) at which a Khatri-Rao Y chain over `in` creates its sketch
-// axis: the mode with the largest extent when it is the view's first axis
-// (every later mode is then contracted against the sketch axis as the whole
-// prefix), else the last mode.  Creating the axis at a small mode (a slice's
-// fixed mode has extent 1) would multiply the intermediate by s.
-static int chain_first(const View& in, int lo, int hi) {
-  int best = hi - 1;
-  if (find_ax(in, AX_MODE, lo) == 0) {
+// Mode of `modes` (ascending, adjacent axes of `in`) at which a Khatri-Rao Y
+// chain creates its sketch axis: the mode with the largest extent when it is
+// the view's first axis (every later mode is then contracted against the
+// sketch axis as the whole prefix), else the last mode.
+static int chain_first(const View& in, const std::vector<int>& modes) {
+  const int lo = modes.front(), last = modes.back();
+  int best = last;
+  const int k0 = find_ax(in, AX_MODE, lo);
+  if (k0 == 0) {
     int64_t big = -1;
-    for (int m = lo; m < hi; ++m) {
+    for (int m : modes) {
       const int k = find_ax(in, AX_MODE, m);
       if (k >= 0 && in.ax[k].size > big) {
         big = in.ax[k].size;
         best = m;
       }
     }
-    if (best != lo) best = hi - 1;
+    if (best != lo) best = last;
     // keep the last mode when it is as large as the first
-    const int kl = find_ax(in, AX_MODE, hi - 1), k0 = find_ax(in, AX_MODE, lo);
-    if (kl >= 0 && k0 >= 0 && in.ax[kl].size >= in.ax[k0].size) best = hi - 1;
+    const int kl = find_ax(in, AX_MODE, last);
+    if (kl >= 0 && in.ax[kl].size >= in.ax[k0].size) best = last;
   }
   return best;
+}
+
+// Whether a Y chain over the modes [lo, hi) of `in` creates its sketch axis
+// at mode hi - 1 (extent > 1; box-fixed modes become scales, not steps).
+static bool chain_starts_last(const View& in, int lo, int hi) {
+  View v = in;
+  std::vector<int> modes;
+  for (int m = lo; m < hi; ++m) {
+    const int k = find_ax(v, AX_MODE, m);
+    if (k < 0) return false;
+    if (v.ax[k].size == 1) {
+      if (m == hi - 1) return false;
+      v.ax.erase(v.ax.begin() + k);
+      continue;
+    }
+    modes.push_back(m);
+  }
+  return chain_first(v, modes) == hi - 1;
 }
 
 // Khatri-Rao contraction of the modes [lo, hi) of `in` with the Y factors,
 // producing one sketch axis (kind AX_SK, id = node) of size s at the place of
 // the modes (Sec. 7: Y_t = kr of its modes' Y_mu, columns shared).
 // With first_done the sketch axis already replaces mode hi - 1 (a shared
-// first mode product) and only the Khatri-Rao steps remain.
+// first mode product) and only the Khatri-Rao steps remain.  Box-fixed modes
+// become deferred scales of the sketch axis (their axes are dropped: no data
+// moves).
 static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int s, View* out,
                            bool first_done = false) {
   View cur = in;
-  const int first = first_done ? hi - 1 : chain_first(in, lo, hi);
-  if (first == lo && first != hi - 1) {
+  const int top = first_done ? hi - 1 : hi;
+  // with first_done the sketch axis exists already; else one mode must create it
+  bool any_free = first_done;
+  for (int m = lo; m < top; ++m) {
+    const int k = find_ax(cur, AX_MODE, m);
+    if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
+    if (cur.ax[k].size > 1) any_free = true;
+  }
+  std::vector<int> modes;
+  for (int m = lo; m < top; ++m) {
+    const int k = find_ax(cur, AX_MODE, m);
+    const bool creates = !any_free && m == top - 1;
+    if (cur.ax[k].size == 1 && k < (int)cur.ax.size() - 1 && !creates &&
+        cur.sc.size() < (size_t)kMaxScales) {
+      cur.ax.erase(cur.ax.begin() + k);
+      cur.sc.push_back(View::Scale{AX_SK, node, facY(C, m)});
+      continue;
+    }
+    modes.push_back(m);
+  }
+  if (modes.empty()) {
+    *out = cur;
+    return TTNN_OK;
+  }
+  View nx;
+  const int first = first_done ? -1 : chain_first(cur, modes);
+  if (!first_done && first == modes.front() && first != modes.back()) {
     // sketch axis at the first (largest) mode, then the others against it
-    const int k0 = find_ax(cur, AX_MODE, lo);
+    const int k0 = find_ax(cur, AX_MODE, first);
     Ax nax{AX_SK, node, s, 0};
-    View nx;
-    TTNN_TRY(contract_view(C, cur, k0, facY(C, lo), C.P.smax, 1, -1, &nax, &nx));
+    TTNN_TRY(contract_view(C, cur, k0, facY(C, first), C.P.smax, 1, -1, &nax, &nx));
     cur = nx;
-    for (int mode = lo + 1; mode < hi; ++mode) {
-      const int k = find_ax(cur, AX_MODE, mode);
+    for (size_t i = 1; i < modes.size(); ++i) {
+      const int k = find_ax(cur, AX_MODE, modes[i]);
       if (k != 1) { set_error("internal: Khatri-Rao chain layout"); return TTNN_EUNSUPPORTED; }
-      TTNN_TRY(contract_view(C, cur, k, facY(C, mode), C.P.smax, 1, 0, nullptr, &nx));
+      TTNN_TRY(contract_view(C, cur, k, facY(C, modes[i]), C.P.smax, 1, 0, nullptr, &nx));
       cur = nx;
     }
     *out = cur;
     return TTNN_OK;
   }
-  for (int mode = hi - 1; mode >= lo; --mode) {
-    if (first_done && mode == hi - 1) continue;
+  for (int i = (int)modes.size() - 1; i >= 0; --i) {
+    const int mode = modes[i];
     const int k = find_ax(cur, AX_MODE, mode);
     if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
-    View nx;
-    if (mode == hi - 1) {
+    if (!first_done && i == (int)modes.size() - 1) {
       Ax nax{AX_SK, node, s, 0};
       TTNN_TRY(contract_view(C, cur, k, facY(C, mode), C.P.smax, 1, -1, &nax, &nx));
     } else {
+      if (k + 1 >= (int)cur.ax.size() || cur.ax[k + 1].kind != AX_SK || cur.ax[k + 1].id != node) {
+        set_error("internal: Khatri-Rao chain layout");
+        return TTNN_EUNSUPPORTED;
+      }
       TTNN_TRY(contract_view(C, cur, k, facY(C, mode), C.P.smax, 1, k + 1, nullptr, &nx));
     }
     cur = nx;
@@ -596,13 +663,13 @@ static ttnn_status x_mode(Ctx& C, const View& in, int mode, View* out) {
   const int k = find_ax(in, AX_MODE, mode);
   if (k < 0) { set_error("internal: mode axis missing"); return TTNN_EUNSUPPORTED; }
   const int L = (int)in.ax.size() - 1;
-  if (in.ax[k].size == 1 && k < L && in.jsc.size() < (size_t)kMaxColScales &&
+  if (in.ax[k].size == 1 && k < L && in.sc.size() < (size_t)kMaxScales &&
       in.ax[L].kind == AX_J) {
     // a mode the box fixes: the contraction is a column scale by the row
     // X_mu[c, :]; drop the axis (no data moves) and defer the scale
     View o = in;
     o.ax.erase(o.ax.begin() + k);
-    o.jsc.push_back(facX(C, mode));
+    o.sc.push_back(View::Scale{AX_J, -1, facX(C, mode)});
     *out = o;
     return TTNN_OK;
   }
@@ -620,29 +687,34 @@ static ttnn_status e_group(Ctx& C, const View& in, int s, View* out) {
   return contract_view(C, y, k, xt, C.P.rmax, 1, (int)y.ax.size() - 1, nullptr, out);
 }
 
-// Adds alpha * view into the state at `base` with per-axis output strides.
-static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::vector<int64_t>& os,
-                                double alpha) {
+static ttnn_status scatter_op(Ctx& C, const View& v, char* base, const std::vector<int64_t>& os,
+                              double alpha, bool assign, bool box_off) {
   Scatter s;
   s.nd = (int)v.ax.size();
   if (s.nd > 12) { set_error("internal: too many axes"); return TTNN_EUNSUPPORTED; }
   for (int a = 0; a < s.nd; ++a) {
-    s.size[a] = v.ax[a].size;
-    s.is[a] = vstride(v, a);
+    if (v.ax[a].size >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
+    const bool bcast = v.bc > 0 && a == s.nd - 1;
+    if (bcast && v.bc >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
+    s.size[a] = (int32_t)(bcast ? v.bc : v.ax[a].size);
+    s.is[a] = bcast ? 0 : vstride(v, a);
     s.os[a] = os[a];
-    s.off[a] = v.ax[a].kind == AX_MODE ? v.ax[a].off : 0;
+    s.off[a] = box_off && v.ax[a].kind == AX_MODE ? (int32_t)v.ax[a].off : 0;
   }
   s.in = v.ptr;
   s.out = base;
   s.alpha = alpha;
-  if (!v.jsc.empty()) {
-    s.jaxis = find_ax(v, AX_J, -1);
-    if (s.jaxis < 0 || v.jsc.size() > (size_t)kMaxColScales) {
-      set_error("internal: column scales without a column axis");
-      return TTNN_EUNSUPPORTED;
-    }
-    s.njsc = (int)v.jsc.size();
-    for (int k = 0; k < s.njsc; ++k) s.jsc[k] = v.jsc[k];
+  s.assign = assign ? 1 : 0;
+  if (v.sc.size() > (size_t)kMaxScales) { set_error("internal: too many scales"); return TTNN_EUNSUPPORTED; }
+  for (const View::Scale& x : v.sc) {
+    const int a = find_ax(v, x.kind, x.id);
+    if (a < 0) { set_error("internal: scale without its axis"); return TTNN_EUNSUPPORTED; }
+    int64_t div = 1;
+    for (int b = a + 1; b < s.nd; ++b) div *= s.size[b];
+    s.sc[s.nsc] = x.ptr;
+    s.scdiv[s.nsc] = div;
+    s.scmod[s.nsc] = s.size[a];
+    ++s.nsc;
   }
   Op op;
   op.kind = OP_SCATTER;
@@ -650,6 +722,27 @@ static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::ve
   op.s = s;
   plan_simple(op);
   C.prog->add(op, v.ptr);
+  return TTNN_OK;
+}
+
+// Adds alpha * view (its pending scales applied) into the state at `base`
+// with per-axis output strides (mode axes offset by the box).
+static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::vector<int64_t>& os,
+                                double alpha) {
+  return scatter_op(C, v, base, os, alpha, false, true);
+}
+
+// A contiguous copy of `in` with its pending scales applied.
+static ttnn_status apply_scales(Ctx& C, const View& in, View* out) {
+  View o;
+  o.ax = in.ax;
+  if (in.bc > 0) o.ax.back().size = in.bc;
+  o.ld = o.ax.back().size;
+  o.ptr = C.ws.alloc(vsize(o) * C.eb);
+  std::vector<int64_t> os(o.ax.size());
+  for (int a = 0; a < (int)o.ax.size(); ++a) os[a] = vstride(o, a);
+  TTNN_TRY(scatter_op(C, in, o.ptr, os, 1.0, true, false));
+  *out = o;
   return TTNN_OK;
 }
 
@@ -683,7 +776,8 @@ static std::vector<int64_t> psi_strides(Ctx& C, const View& v, const TNode& nd, 
 
 static View truncate_j(const View& v, int64_t j) {
   View o = v;
-  o.ax.back().size = std::min<int64_t>(o.ax.back().size, j);
+  if (o.bc > 0) o.bc = std::min<int64_t>(o.bc, j);
+  else o.ax.back().size = std::min<int64_t>(o.ax.back().size, j);
   return o;
 }
 
@@ -701,7 +795,7 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
     // Y columns when the last child's sketch size equals s_t: do it once.
     const TNode* lastc = nd.leaf ? nullptr : &P.nodes[nd.ch.back()];
     const bool share = v != P.ychild && lastc && !lastc->identity && lastc->s == nd.s &&
-                       chain_first(Gt, nd.lo, nd.hi) == nd.hi - 1;
+                       chain_starts_last(Gt, nd.lo, nd.hi);
     View z;
     if (share) {
       const int k = find_ax(Gt, AX_MODE, nd.hi - 1);
@@ -740,6 +834,8 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
           View zc = z;
           for (auto& a : zc.ax)
             if (a.kind == AX_SK && a.id == v) a.id = c.user;
+          for (auto& x : zc.sc)
+            if (x.kind == AX_SK && x.id == v) x.id = c.user;
           TTNN_TRY(y_chain(C, zc, c.user, c.lo, c.hi, c.s, &nx, true));
         } else {
           TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
@@ -889,20 +985,61 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   for (int m = P.Llo; m < P.Lhi; ++m) nL *= box.ext[m];
   for (int m = P.Rlo; m < P.Rhi; ++m) nR *= box.ext[m];
   const int sb = store_bytes(P.side_store);
+  // A box whose right (r1 = 1) or left (r1 = 2) pass side is a single index:
+  // the product against that side is rank one, M times one row of its side
+  // block, and is left to the walk as a broadcast with that row as a pending
+  // scale; the product against the other side is a matrix-vector product
+  // with its side block, read straight from the cached whole-tensor block
+  // when there is one (no box block is formed).
+  const bool r1_fmt = P.dtype == TTNN_F64 || P.dtype == TTNN_F32 || P.dtype == TTNN_BF16;
+  const int r1 = !r1_fmt || (P.flags & TTNN_FLAG_SIMT_PASS) ? 0
+                 : (nR == 1 && nL > 1)                       ? 1
+                 : (nL == 1 && nR > 1)                       ? 2
+                                                             : 0;
   // side blocks of the box
   const void* sR = nullptr;
   const void* sL = nullptr;
   if (box.full && P.sideR) sR = P.sideR;
   if (box.full && P.sideL) sL = P.sideL;
+  // the matrix-vector side of a rank-one box: source block, its leading
+  // dimension, and whether rows are cut from the whole-tensor block
+  const void* gsrc = nullptr;
+  int64_t gld = 0;
+  bool gcut = false;
+  if (r1) {
+    const bool right = r1 == 2;                 // the matrix-vector side is R
+    const void* cache = right ? P.sideR : P.sideL;
+    const int64_t rows = right ? nR : nL;
+    if (box.full && cache) {
+      gsrc = cache;
+      gld = rows;
+    } else if (cache) {
+      int64_t nfull = 1;
+      for (int m = right ? P.Rlo : P.Llo; m < (right ? P.Rhi : P.Lhi); ++m) nfull *= P.dims[m];
+      gsrc = cache;
+      gld = nfull;
+      gcut = true;
+    }
+    if (right) sR = gsrc;
+    else sL = gsrc;
+  }
   if (P.wR > 0 && !sR) {
     char* b = ws.alloc((int64_t)P.wRpad * nR * sb);
     if (!dry) TTNN_TRY(make_side(P, box, 0, b, nR, st, batch ? &batch->gathers : nullptr));
     sR = b;
+    if (r1 == 2) {
+      gsrc = b;
+      gld = nR;
+    }
   }
   if (P.wL > 0 && !sL) {
     char* b = ws.alloc((int64_t)P.wLpad * nL * sb);
     if (!dry) TTNN_TRY(make_side(P, box, 1, b, nL, st, batch ? &batch->gathers : nullptr));
     sL = b;
+    if (r1 == 1) {
+      gsrc = b;
+      gld = nL;
+    }
   }
   if (!P.nodes[P.ychild].identity) {
     const TNode& yc = P.nodes[P.ychild];
@@ -917,9 +1054,16 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       C.yw = b;
     }
   }
-  // first-level pass: D1 = M B_R^T (nL x wRpad), D2 = M^T B_L^T (nR x wLpad)
-  char* D1 = ws.alloc(nL * P.wRpad * eb);
-  char* D2 = ws.alloc(nR * P.wLpad * eb);
+  // first-level pass: D1 = M B_R^T (nL x wRpad), D2 = M^T B_L^T (nR x wLpad);
+  // for a rank-one box only the matrix-vector product (one row), plus walk
+  // copies of M and of the broadcast side row when the formats differ
+  char* D1 = r1 == 1 ? nullptr : ws.alloc(nL * P.wRpad * eb);
+  char* D2 = r1 == 2 ? nullptr : ws.alloc(nR * P.wLpad * eb);
+  const int64_t r1_rows = r1 == 1 ? nL : nR;
+  const int r1_bpad = r1 == 1 ? P.wRpad : P.wLpad;
+  const void* r1_brow = r1 == 1 ? sR : sL;
+  const char* Mw = r1 && P.pass_store == 2 ? ws.alloc(r1_rows * eb) : (const char*)data;
+  const char* bw = r1 && P.side_store == 2 ? ws.alloc((int64_t)r1_bpad * eb) : (const char*)r1_brow;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
   // the pass's own temporaries are released right after it and are not
   // program buffers: keep them out of the dependency registry
@@ -928,7 +1072,31 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   const bool use_tc = P.tc_ok && !(P.flags & TTNN_FLAG_SIMT_PASS) &&
                       (cvt ? cvt_pass_supported(P, nL, nR) : tc_pass_supported(P, nL, nR)) ==
                           TTNN_OK;
-  if (use_tc) {
+  if (r1) {
+    const int64_t mark = ws.top;
+    SideSpec gs;
+    if (r1 == 1) side_spec_common(P, box, P.Llo, P.Lhi, gs);
+    else side_spec_common(P, box, P.Rlo, P.Rhi, gs);
+    const int gcols = r1 == 1 ? P.wL : P.wR, gpad = r1 == 1 ? P.wLpad : P.wRpad;
+    void* Dout = r1 == 1 ? (void*)D2 : (void*)D1;
+    int64_t need = 0;
+    TTNN_TRY(launch_side_gemv(gs, nullptr, 0, false, nullptr, P.pass_store, r1_rows, gcols, gpad,
+                              nullptr, P.walk_f64, nullptr, 0, st, true, &need));
+    char* part = ws.alloc(need);
+    if (!dry) {
+      ++P.n_simt_pass;
+      const int pstore = P.pass_store, sstore = P.side_store, wf64 = P.walk_f64 ? 1 : 0;
+      auto go = [=](cudaStream_t s) -> ttnn_status {
+        if (Mw != (const char*)data) TTNN_TRY(launch_to_walk(data, pstore, (void*)Mw, wf64, r1_rows, s));
+        if (bw != (const char*)r1_brow) TTNN_TRY(launch_to_walk(r1_brow, sstore, (void*)bw, wf64, r1_bpad, s));
+        return launch_side_gemv(gs, gsrc, gld, gcut, data, pstore, r1_rows, gcols, gpad, Dout, wf64,
+                                part, need, s, false, nullptr);
+      };
+      if (batch) batch->passes.push_back(go);
+      else TTNN_TRY(go(st));
+    }
+    ws.top = mark;
+  } else if (use_tc) {
     auto launch = cvt ? launch_cvt_pass : launch_tc_pass;
     const int64_t mark = ws.top;
     int64_t need = 0;
@@ -995,11 +1163,21 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     for (int m = lo; m < hi; ++m) ax.push_back(Ax{AX_MODE, m, box.ext[m], box.off[m]});
     return ax;
   };
+  // a rank-one product: M (walk copy) with a broadcast last axis scaled by
+  // the row `scale` of the single-index side's block
+  auto bview = [&](int lo, int hi, Ax last, int64_t logical, const char* scale) {
+    View v{(char*)Mw, mode_axes(lo, hi), 1};
+    v.ax.push_back(last);
+    v.bc = logical;
+    v.sc.push_back(View::Scale{last.kind, last.id, scale});
+    return v;
+  };
   const TNode& root = P.nodes[P.root];
   // L side (both variants): G over L modes from D1's X part
   if (P.rXL > 0) {
     View GL{D1, mode_axes(P.Llo, P.Lhi), P.wRpad};
     GL.ax.push_back(Ax{AX_J, -1, P.rXL, 0});
+    if (r1 == 1) GL = bview(P.Llo, P.Lhi, Ax{AX_J, -1, 1, 0}, P.rXL, bw);
     for (size_t k = 0; k < P.Lch.size(); ++k) {
       const TNode& c = P.nodes[P.Lch[k]];
       if (c.rsub == 0) continue;
@@ -1020,6 +1198,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     if (P.rXR > 0) {
       View GR{D2, mode_axes(P.Rlo, P.Rhi), P.wLpad};
       GR.ax.push_back(Ax{AX_J, -1, P.rXR, 0});
+      if (r1 == 2) GR = bview(P.Rlo, P.Rhi, Ax{AX_J, -1, 1, 0}, P.rXR, bw);
       for (size_t k = 0; k < P.Rch.size(); ++k) {
         const TNode& c = P.nodes[P.Rch[k]];
         if (c.rsub == 0) continue;
@@ -1040,6 +1219,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     if (P.yside == 0) {
       View H{D1 + (int64_t)P.rXL * eb, mode_axes(P.Llo, P.Lhi), P.wRpad};
       H.ax.push_back(Ax{AX_SK, P.ychild, P.wYR, 0});
+      if (r1 == 1) H = bview(P.Llo, P.Lhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYR, bw + (int64_t)P.rXL * eb);
       View cur = H;
       for (int k = (int)P.Lch.size() - 1; k >= 0; --k) {
         const TNode& c = P.nodes[P.Lch[k]];
@@ -1055,6 +1235,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     } else {
       View H{D2 + (int64_t)P.rXR * eb, mode_axes(P.Rlo, P.Rhi), P.wLpad};
       H.ax.push_back(Ax{AX_SK, P.ychild, P.wYL, 0});
+      if (r1 == 2) H = bview(P.Rlo, P.Rhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYL, bw + (int64_t)P.rXR * eb);
       View cur = H;
       for (int k = (int)P.Rch.size() - 1; k >= 0; --k) {
         const TNode& c = P.nodes[P.Rch[k]];
@@ -1076,6 +1257,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     // STTNN: D2 = M^T Y_c1 (nR x s'_c1): R children and the root
     View H{D2, mode_axes(P.Rlo, P.Rhi), P.wLpad};
     H.ax.push_back(Ax{AX_SK, P.ychild, P.wYL, 0});
+    if (r1 == 2) H = bview(P.Rlo, P.Rhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYL, bw);
     const TNode& c1 = P.nodes[P.ychild];
     for (size_t k = 0; k < P.Rch.size(); ++k) {
       const TNode& c = P.nodes[P.Rch[k]];

@@ -318,18 +318,18 @@ __device__ void dev_scatter(const DevOp& op, int64_t blk) {
   const I e = (I)(blk * kExecThreads) + (I)threadIdx.x;
   if (e >= total) return;
   I rem = e;
-  int64_t io = 0, oo = 0, jj = 0;
+  int64_t io = 0, oo = 0;
   for (int a = s.nd - 1; a >= 0; --a) {
     const I i = rem % (I)s.size[a];
     rem /= (I)s.size[a];
     io += i * s.is[a];
-    oo += (s.off[a] + i) * s.os[a];
-    if (a == s.jaxis) jj = i;
+    oo += ((int64_t)s.off[a] + i) * s.os[a];
   }
   T v = ((const T*)s.in)[io];
-  for (int k = 0; k < s.njsc; ++k) v *= ((const T*)s.jsc[k])[jj];
+  for (int k = 0; k < s.nsc; ++k) v *= ((const T*)s.sc[k])[(e / (I)s.scdiv[k]) % (I)s.scmod[k]];
   T* out = (T*)s.out;
-  out[oo] = out[oo] + (T)s.alpha * v;
+  if (s.assign) out[oo] = (T)s.alpha * v;
+  else out[oo] = out[oo] + (T)s.alpha * v;
 }
 
 __device__ void dev_proj(const DevOp& op, int64_t blk) {

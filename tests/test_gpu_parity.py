@@ -227,6 +227,10 @@ TC_CASES = {
     "bin4_64x4096": (W.balanced_binary(4), [8, 8, 64, 64], 6, 4),
     # three chunks: no cluster shape, partial sums through global memory
     "bin4_80x2560": (W.balanced_binary(4), [8, 10, 40, 64], 6, 4),
+    # no left-side block (w_L = 0): the pass Y side is an identity leaf, so
+    # the pass forms D1 only (TTNN; the STTNN plans keep both products)
+    "tt4_wl0_1024x16": (W.tensor_train(4), [8, 16, 8, 16], 12, 6),
+    "tucker4_wl0_3072x16": (W.tucker(4), [24, 16, 8, 16], 16, 8),
 }
 
 
@@ -256,6 +260,79 @@ def test_tensor_core_pass_matches_oracle_and_simt(case, variant):
     finally:
         tc.close()
         simt.close()
+
+
+@pytest.mark.parametrize("case", ["tt4_wl0_1024x16", "tucker4_wl0_3072x16", "tt4_4096x24"])
+def test_tensor_core_slices_match_oracle_and_simt(case):
+    # one slice per mode (that mode fixed): slices whose pass matrix keeps
+    # 16-byte rows take the tensor-core pass, with or without a D2 product
+    tr, dims, r, p = TC_CASES[case]
+    n = len(tr[0])
+    t = _otree(tr, dims, r, p)
+    drm = O.Drm(t, 31, "bf16", "ttnn")
+    rng = np.random.default_rng(8)
+    for mu in range(len(dims)):
+        off, ext = [0] * len(dims), list(dims)
+        off[mu], ext[mu] = int(rng.integers(0, dims[mu])), 1
+        data = rng.standard_normal(ext)
+        dev, dq = _dev(data, api.BF16)
+        tc = Run(tr, dims, [r] * n, [p] * n, 31, dtype=api.BF16)
+        simt = Run(tr, dims, [r] * n, [p] * n, 31, dtype=api.BF16, flags=api.FLAG_SIMT_PASS)
+        try:
+            api.ttnn_update_dense(tc.state, dev, off, ext, lam=0.5)
+            api.ttnn_update_dense(simt.state, dev, off, ext, lam=0.5)
+            if mu < len(dims) - 1:
+                assert api.ttnn_plan_pass_counts(tc.plan) == (1, 0), mu
+            _compare_sketches(tc, t, 0.5 * W.embed_box(dims, off, ext, dq), drm,
+                              api.VARIANT_TTNN, 1e-5)
+            assert rel(tc.state_host(), simt.state_host()) <= 1e-5
+        finally:
+            tc.close()
+            simt.close()
+
+
+def _pass_sides(tr, variant):
+    """Modes of the two first-level pass sides: the root's children split
+    into a left group (all but the last child for TTNN with three or more
+    children, else the first child) and the rest."""
+    ch, modes = W.children_of(tr[0], tr[1])
+    kids = ch[list(tr[0]).index(-1)]
+    a = 1 if variant == api.VARIANT_STTNN or len(kids) == 2 else len(kids) - 1
+    left = sorted(m for c in kids[:a] for m in modes[c])
+    right = sorted(m for c in kids[a:] for m in modes[c])
+    return left, right
+
+
+@pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
+@pytest.mark.parametrize("case", ["binary4", "toy6", "tt5"])
+@pytest.mark.parametrize("dtype,tol", [(api.F64, 1e-12), (api.F32, 1e-5), (api.BF16, 1e-5)])
+def test_rank_one_boxes_match_oracle(case, variant, dtype, tol):
+    # boxes that fix every mode of one pass side: one product is rank one
+    # (a broadcast in the walk), the other a matrix-vector product read
+    # straight from the cached whole-tensor side block
+    tr, dims, r, p = CASES[case]
+    n = len(tr[0])
+    left, right = _pass_sides(tr, variant)
+    rng = np.random.default_rng(12)
+    t = _otree(tr, dims, r, p)
+    drm = O.Drm(t, 61, FMT[dtype], "sttnn" if variant else "ttnn")
+    for fixed in (right, left):
+        off = [int(rng.integers(0, d)) if mu in fixed else int(rng.integers(0, 2))
+               for mu, d in enumerate(dims)]
+        ext = [1 if mu in fixed else dims[mu] - off[mu] for mu in range(len(dims))]
+        data = rng.standard_normal(ext)
+        dev, dq = _dev(data, dtype)
+        run = Run(tr, dims, [r] * n, [p] * n, 61, dtype=dtype, variant=variant)
+        simt = Run(tr, dims, [r] * n, [p] * n, 61, dtype=dtype, variant=variant,
+                   flags=api.FLAG_SIMT_PASS)
+        try:
+            api.ttnn_update_dense(run.state, dev, off, ext, lam=-1.5)
+            api.ttnn_update_dense(simt.state, dev, off, ext, lam=-1.5)
+            _compare_sketches(run, t, -1.5 * W.embed_box(dims, off, ext, dq), drm, variant, tol)
+            assert rel(run.state_host(), simt.state_host()) <= tol
+        finally:
+            run.close()
+            simt.close()
 
 
 @pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
