@@ -377,6 +377,10 @@ struct Ax {
   int id;          // mode (AX_MODE) or child node (AX_SK)
   int64_t size;
   int64_t off;     // box offset (AX_MODE)
+  // > 0: a broadcast of this logical size (the data holds one entry along
+  // the axis, size == 1): the outer products with one row of a DRM block
+  // that a box fixing modes produces, left to the scatter
+  int64_t bc = 0;
 };
 struct View {
   char* ptr;
@@ -393,10 +397,6 @@ struct View {
     const char* ptr;
   };
   std::vector<Scale> sc;
-  // > 0: the last axis is a broadcast of this logical size (the data holds
-  // one entry along it, ax.back().size == 1), as in the rank-one products of
-  // a box whose other pass side is a single index
-  int64_t bc = 0;
 };
 
 static int64_t vstride(const View& v, int k) {
@@ -440,7 +440,9 @@ static ttnn_status apply_scales(Ctx& C, const View& in, View* out);
 static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, int64_t wsI,
                                  int64_t wsX, int shared, const Ax* nax, View* out) {
   const int L = (int)in.ax.size() - 1;
-  bool expand = in.bc > 0 && (k == L || (shared == k + 1 && k + 1 == L));
+  // a broadcast axis that is contracted or shared (other than the column axis
+  // in the shared == L form, which makes it real) is expanded first
+  bool expand = in.ax[k].bc > 0 || (shared >= 0 && shared != L && in.ax[shared].bc > 0);
   for (const View::Scale& x : in.sc)
     if (x.kind == in.ax[k].kind && x.id == in.ax[k].id) expand = true;
   if (expand) {
@@ -477,12 +479,13 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
     for (int a = k + 1; a < L; ++a) c.Q *= in.ax[a].size;
     c.isQ = (k < L - 1) ? vstride(in, L - 1) : 0;
     // a broadcast column axis becomes real here (W's columns differ)
-    c.J = in.bc > 0 ? in.bc : in.ax[L].size;
-    c.isJ = in.bc > 0 ? 0 : 1;
+    c.J = in.ax[L].bc > 0 ? in.ax[L].bc : in.ax[L].size;
+    c.isJ = in.ax[L].bc > 0 ? 0 : 1;
     c.wsJ = wsX;
     oax = in.ax;
     oax.erase(oax.begin() + k);
     oax.back().size = c.J;
+    oax.back().bc = 0;
   } else if (shared == k + 1) {
     c.Q = in.ax[k + 1].size;
     c.isQ = vstride(in, k + 1);
@@ -522,7 +525,6 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
   o.ax = oax;
   o.ld = o.ax.back().size;
   o.sc = in.sc;
-  o.bc = shared == L ? 0 : in.bc;
   const int64_t total = vsize(o);
   o.ptr = C.ws.alloc(total * C.eb);
   c.out = o.ptr;
@@ -609,9 +611,14 @@ static ttnn_status y_chain(Ctx& C, const View& in, int node, int lo, int hi, int
   for (int m = lo; m < top; ++m) {
     const int k = find_ax(cur, AX_MODE, m);
     const bool creates = !any_free && m == top - 1;
-    if (cur.ax[k].size == 1 && k < (int)cur.ax.size() - 1 && !creates &&
-        cur.sc.size() < (size_t)kMaxScales) {
-      cur.ax.erase(cur.ax.begin() + k);
+    if (cur.ax[k].size == 1 && k < (int)cur.ax.size() - 1 && cur.sc.size() < (size_t)kMaxScales) {
+      if (creates) {
+        // every mode fixed: the sketch axis is the outer product with the
+        // row, a broadcast in place of the mode (no data moves)
+        cur.ax[k] = Ax{AX_SK, node, 1, 0, s};
+      } else {
+        cur.ax.erase(cur.ax.begin() + k);
+      }
       cur.sc.push_back(View::Scale{AX_SK, node, facY(C, m)});
       continue;
     }
@@ -694,9 +701,9 @@ static ttnn_status scatter_op(Ctx& C, const View& v, char* base, const std::vect
   if (s.nd > 12) { set_error("internal: too many axes"); return TTNN_EUNSUPPORTED; }
   for (int a = 0; a < s.nd; ++a) {
     if (v.ax[a].size >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
-    const bool bcast = v.bc > 0 && a == s.nd - 1;
-    if (bcast && v.bc >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
-    s.size[a] = (int32_t)(bcast ? v.bc : v.ax[a].size);
+    const bool bcast = v.ax[a].bc > 0;
+    if (v.ax[a].bc >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
+    s.size[a] = (int32_t)(bcast ? v.ax[a].bc : v.ax[a].size);
     s.is[a] = bcast ? 0 : vstride(v, a);
     s.os[a] = os[a];
     s.off[a] = box_off && v.ax[a].kind == AX_MODE ? (int32_t)v.ax[a].off : 0;
@@ -736,7 +743,11 @@ static ttnn_status scatter_into(Ctx& C, const View& v, char* base, const std::ve
 static ttnn_status apply_scales(Ctx& C, const View& in, View* out) {
   View o;
   o.ax = in.ax;
-  if (in.bc > 0) o.ax.back().size = in.bc;
+  for (Ax& a : o.ax)
+    if (a.bc > 0) {
+      a.size = a.bc;
+      a.bc = 0;
+    }
   o.ld = o.ax.back().size;
   o.ptr = C.ws.alloc(vsize(o) * C.eb);
   std::vector<int64_t> os(o.ax.size());
@@ -776,7 +787,7 @@ static std::vector<int64_t> psi_strides(Ctx& C, const View& v, const TNode& nd, 
 
 static View truncate_j(const View& v, int64_t j) {
   View o = v;
-  if (o.bc > 0) o.bc = std::min<int64_t>(o.bc, j);
+  if (o.ax.back().bc > 0) o.ax.back().bc = std::min<int64_t>(o.ax.back().bc, j);
   else o.ax.back().size = std::min<int64_t>(o.ax.back().size, j);
   return o;
 }
@@ -1167,8 +1178,8 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   // the row `scale` of the single-index side's block
   auto bview = [&](int lo, int hi, Ax last, int64_t logical, const char* scale) {
     View v{(char*)Mw, mode_axes(lo, hi), 1};
+    last.bc = logical;
     v.ax.push_back(last);
-    v.bc = logical;
     v.sc.push_back(View::Scale{last.kind, last.id, scale});
     return v;
   };

@@ -3,6 +3,9 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "program.cuh"
 
 namespace ttnn {
@@ -315,21 +318,24 @@ __device__ void dev_scatter(const DevOp& op, int64_t blk) {
   const Scatter& s = op.s;
   I total = 1;
   for (int a = 0; a < s.nd; ++a) total *= (I)s.size[a];
-  const I e = (I)(blk * kExecThreads) + (I)threadIdx.x;
-  if (e >= total) return;
-  I rem = e;
-  int64_t io = 0, oo = 0;
-  for (int a = s.nd - 1; a >= 0; --a) {
-    const I i = rem % (I)s.size[a];
-    rem /= (I)s.size[a];
-    io += i * s.is[a];
-    oo += ((int64_t)s.off[a] + i) * s.os[a];
+  // op.chunk elements per thread, consecutive threads on consecutive elements
+  for (int it = 0; it < op.chunk; ++it) {
+    const I e = (I)((blk * op.chunk + it) * kExecThreads) + (I)threadIdx.x;
+    if (e >= total) return;
+    I rem = e;
+    int64_t io = 0, oo = 0;
+    for (int a = s.nd - 1; a >= 0; --a) {
+      const I i = rem % (I)s.size[a];
+      rem /= (I)s.size[a];
+      io += i * s.is[a];
+      oo += ((int64_t)s.off[a] + i) * s.os[a];
+    }
+    T v = ((const T*)s.in)[io];
+    for (int k = 0; k < s.nsc; ++k) v *= ((const T*)s.sc[k])[(e / (I)s.scdiv[k]) % (I)s.scmod[k]];
+    T* out = (T*)s.out;
+    if (s.assign) out[oo] = (T)s.alpha * v;
+    else out[oo] = out[oo] + (T)s.alpha * v;
   }
-  T v = ((const T*)s.in)[io];
-  for (int k = 0; k < s.nsc; ++k) v *= ((const T*)s.sc[k])[(e / (I)s.scdiv[k]) % (I)s.scmod[k]];
-  T* out = (T*)s.out;
-  if (s.assign) out[oo] = (T)s.alpha * v;
-  else out[oo] = out[oo] + (T)s.alpha * v;
 }
 
 __device__ void dev_proj(const DevOp& op, int64_t blk) {
@@ -520,6 +526,10 @@ void plan_simple(Op& op) {
   if (op.kind == OP_SCATTER) {
     total = 1;
     for (int a = 0; a < op.s.nd; ++a) total *= op.s.size[a];
+    // large scatters: several elements per thread (fewer, fuller blocks)
+    op.chunk = total >= (int64_t)exec_sms() * kExecThreads * 32 ? 8 : 1;
+    op.blocks = ceil_div(total, (int64_t)kExecThreads * op.chunk);
+    return;
   } else if (op.kind == OP_EYE) {
     total = op.eye_n * op.eye_n;
   } else if (op.kind == OP_REDUCE) {
@@ -603,12 +613,21 @@ static DevOp to_dev(const Op& o) {
   if (o.kind == OP_SCATTER) {
     int64_t st = 1;
     for (int a = 0; a < o.s.nd; ++a) st *= std::max<int64_t>(o.s.size[a], 1);
-    m = std::max(m, st);
+    m = std::max(m, st + (int64_t)kExecThreads * std::max<int64_t>(o.chunk, 1));
   }
   m = std::max(m, o.eye_n * o.eye_n);
   m = std::max(m, o.blocks * kExecThreads);
   d.idx32 = m < lim;
   return d;
+}
+
+// TTNN_DUMP_PROGRAM=1 prints every executed op (level, kind, shape) to stderr.
+static bool dump_program() {
+  static const bool on = [] {
+    const char* e = getenv("TTNN_DUMP_PROGRAM");
+    return e && e[0] == '1';
+  }();
+  return on;
 }
 
 ttnn_status Program::run(cudaStream_t st) {
@@ -633,6 +652,18 @@ ttnn_status Program::run(cudaStream_t st) {
     };
     for (const Op& o : ops_) {
       if (o.level != lvl || o.blocks == 0) continue;
+      if (dump_program()) {
+        if (o.kind == OP_SCATTER)
+          fprintf(stderr, "[ttnn] L%d scatter nd %d nsc %d blocks %lld\n", lvl, o.s.nd, o.s.nsc,
+                  (long long)o.blocks);
+        else
+          fprintf(stderr,
+                  "[ttnn] L%d kind %d P %lld NI %lld NB %lld Q %lld J %lld isJ %lld wsJ %lld wsQ %lld "
+                  "wsP %lld g %d nsplit %d blocks %lld\n",
+                  lvl, (int)o.kind, (long long)o.c.P, (long long)o.c.NI, (long long)o.c.NB,
+                  (long long)o.c.Q, (long long)o.c.J, (long long)o.c.isJ, (long long)o.c.wsJ,
+                  (long long)o.c.wsQ, (long long)o.c.wsP, o.g, o.nsplit, (long long)o.blocks);
+      }
       if (lb.nops == kMaxLevelOps) TTNN_TRY(flush());
       lb.ops[lb.nops] = to_dev(o);
       lb.start[lb.nops + 1] = lb.start[lb.nops] + o.blocks;
