@@ -458,6 +458,23 @@ def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
     wall = time.perf_counter() - t0
     rep = api.ttnn_server_stats(srv)
     dev_bytes = rep["device_bytes"]
+    # capacity: the same kind of slices submitted back to back (queues full),
+    # completion rate until the last one is done
+    api.ttnn_server_stats(srv, reset=True)
+    burst = [(s, mu, idx) for (_, s, mu, idx) in arrivals[:20000]]
+    tickets = []
+    t1 = time.perf_counter()
+    for (s, mu, idx) in burst:
+        dm = dims_of[s]
+        off = [0] * len(dm)
+        ext = list(dm)
+        off[mu], ext[mu] = idx, 1
+        tickets.append(api.ttnn_server_submit(srv, sids[s], buf, off, ext))
+    for t in tickets:
+        if api.ttnn_server_wait(srv, t, 120_000_000) != 0:
+            failed += 1
+    cap_s = time.perf_counter() - t1
+    cap = api.ttnn_server_stats(srv)
     api.ttnn_server_destroy(srv)
     return {"workload": f"{n_streams} streams (d 3-6, n in 16..128, binary/TT/Tucker, r 4-32, "
                         f"p=r/2, BF16), Poisson slices at {rate:.0f}/s for {seconds:.0f} s",
@@ -467,7 +484,10 @@ def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
             "latency_us": {"p50": rep["p50_us"], "p99": rep["p99_us"], "max": rep["max_us"]},
             "batches": rep["batches"], "late_submits": late, "open_s": open_s,
             "worker_host_s": rep["worker_host_s"], "wall_s": wall, "errors": errors,
-            "device_gb": dev_bytes / 1e9}
+            "device_gb": dev_bytes / 1e9,
+            "capacity": {"note": "the first slices of the same arrival list submitted back to back",
+                         "updates": cap["completed_updates"], "per_s": cap["completed_updates"] / cap_s,
+                         "batches": cap["batches"], "p99_us": cap["p99_us"]}}
 
 
 def cpu_oracle_sample(max_seconds=25.0):

@@ -133,23 +133,35 @@ constexpr int kMaxRecoverR = 64;
 
 namespace ttnn {
 constexpr int kMaxScales = 8;
-// out[sum_a (off_a + i_a) * os_a] += alpha * v (or = alpha * v with
-// `assign`) over the box of sizes `size` (up to 12 axes), where
-// v = in[sum_a i_a * is_a] * prod_k sc_k[(e / scdiv_k) % scmod_k] and e is
-// the element's flat index (last axis fastest): scale k is a vector along
-// one axis.  in / out / scales share one type (f32 / f64).  The scales are
+// out[sum_a i_a * os_a] += alpha * v (or = alpha * v with `assign`) over
+// the box of sizes `size` (up to 12 axes, last fastest), where
+// v = in[sum_a i_a * is_a] * prod_k sc_k[i_{scax_k}]: scale k is a vector
+// along axis scax_k.  in / out / scales share one type (f32 / f64).  The scales are
 // rows of the DRM factors of modes a box fixes (X_mu[c, :] on the column
 // axis, Y_mu[c, :] on a sketch axis), applied here instead of contracting
 // an extent-1 mode over a whole intermediate.
 struct Scatter {
   int nd = 0, nsc = 0, assign = 0;
-  int32_t size[12] = {0}, off[12] = {0};
+  int32_t size[12] = {0};
   int64_t is[12] = {0}, os[12] = {0};
+  // division by size[a] as a multiply-high and shift (32-bit indices)
+  uint32_t mag[12] = {0};
+  uint8_t shf[12] = {0};
+  int8_t scax[kMaxScales] = {0};   // axis of each scale
   const void* sc[kMaxScales] = {nullptr};
-  int64_t scdiv[kMaxScales] = {0};
-  int32_t scmod[kMaxScales] = {0};
   const void* in = nullptr;
   void* out = nullptr;
   double alpha = 1.0;
 };
+
+// Multiplier and shift that divide any 32-bit unsigned n by d (1 <= d < 2^31)
+// as q = (umulhi(n, mag) + n) >> shf, the sum taken in 64 bits (division by
+// invariant integers, Granlund and Montgomery 1994: l = ceil(log2 d),
+// mag = floor(2^32 (2^l - d) / d) + 1).
+inline void div_magic(uint32_t d, uint32_t* mag, uint8_t* shf) {
+  int l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  *mag = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+  *shf = (uint8_t)l;
+}
 }  // namespace ttnn

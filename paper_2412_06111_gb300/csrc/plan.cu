@@ -423,6 +423,9 @@ struct Ctx {
   const char* yw;       // walk-type copy of the pass Y block (rows of the Y child, box)
   int64_t yw_ld;
   Program* prog;
+  // rank-one box with the Y child on the matrix-vector side: Y^T m, the Y
+  // child's Omega before its broadcast column factor (walk type, s entries)
+  const char* yom = nullptr;
 };
 
 static int find_ax(const View& v, int kind, int id) {
@@ -696,33 +699,65 @@ static ttnn_status e_group(Ctx& C, const View& in, int s, View* out) {
 
 static ttnn_status scatter_op(Ctx& C, const View& v, char* base, const std::vector<int64_t>& os,
                               double alpha, bool assign, bool box_off) {
+  const int nd = (int)v.ax.size();
+  // per axis: logical size, strides, scale (box offsets fold into the base)
+  struct A {
+    int64_t size, is, os;
+    int scaled;   // carries scales (never merged)
+    int orig;     // the view axis (scaled axes)
+  };
+  std::vector<A> ax(nd);
+  int64_t boff = 0;
+  for (int a = 0; a < nd; ++a) {
+    const bool bcast = v.ax[a].bc > 0;
+    ax[a] = A{bcast ? v.ax[a].bc : v.ax[a].size, bcast ? 0 : vstride(v, a), os[a], 0, a};
+    if (ax[a].size < 1) return TTNN_OK;   // nothing to add
+    if (box_off && v.ax[a].kind == AX_MODE) boff += v.ax[a].off * os[a];
+  }
+  if (v.sc.size() > (size_t)kMaxScales) { set_error("internal: too many scales"); return TTNN_EUNSUPPORTED; }
+  for (size_t k = 0; k < v.sc.size(); ++k) {
+    const int a = find_ax(v, v.sc[k].kind, v.sc[k].id);
+    if (a < 0) { set_error("internal: scale without its axis"); return TTNN_EUNSUPPORTED; }
+    ax[a].scaled = 1;
+  }
+  // merge neighbouring unscaled axes whose strides chain (fewer index
+  // divisions per element); extent-1 axes without a scale drop out
+  std::vector<A> m;
+  for (int a = nd - 1; a >= 0; --a) {
+    const A& x = ax[a];
+    if (x.size == 1 && !x.scaled) continue;
+    if (!m.empty()) {
+      A& in = m.back();
+      if (!x.scaled && !in.scaled && x.is == in.is * in.size && x.os == in.os * in.size) {
+        in.size *= x.size;
+        continue;
+      }
+    }
+    m.push_back(x);
+  }
+  if (m.empty()) m.push_back(A{1, 0, 0, 0, -1});
+  std::reverse(m.begin(), m.end());
   Scatter s;
-  s.nd = (int)v.ax.size();
+  s.nd = (int)m.size();
   if (s.nd > 12) { set_error("internal: too many axes"); return TTNN_EUNSUPPORTED; }
   for (int a = 0; a < s.nd; ++a) {
-    if (v.ax[a].size >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
-    const bool bcast = v.ax[a].bc > 0;
-    if (v.ax[a].bc >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
-    s.size[a] = (int32_t)(bcast ? v.ax[a].bc : v.ax[a].size);
-    s.is[a] = bcast ? 0 : vstride(v, a);
-    s.os[a] = os[a];
-    s.off[a] = box_off && v.ax[a].kind == AX_MODE ? (int32_t)v.ax[a].off : 0;
+    if (m[a].size >= (int64_t(1) << 31)) { set_error("internal: axis too long"); return TTNN_EUNSUPPORTED; }
+    s.size[a] = (int32_t)m[a].size;
+    s.is[a] = m[a].is;
+    s.os[a] = m[a].os;
+    div_magic((uint32_t)s.size[a], &s.mag[a], &s.shf[a]);
+    if (!m[a].scaled) continue;
+    for (const View::Scale& x : v.sc)
+      if (find_ax(v, x.kind, x.id) == m[a].orig) {
+        s.sc[s.nsc] = x.ptr;
+        s.scax[s.nsc] = (int8_t)a;
+        ++s.nsc;
+      }
   }
   s.in = v.ptr;
-  s.out = base;
+  s.out = base + boff * C.eb;
   s.alpha = alpha;
   s.assign = assign ? 1 : 0;
-  if (v.sc.size() > (size_t)kMaxScales) { set_error("internal: too many scales"); return TTNN_EUNSUPPORTED; }
-  for (const View::Scale& x : v.sc) {
-    const int a = find_ax(v, x.kind, x.id);
-    if (a < 0) { set_error("internal: scale without its axis"); return TTNN_EUNSUPPORTED; }
-    int64_t div = 1;
-    for (int b = a + 1; b < s.nd; ++b) div *= s.size[b];
-    s.sc[s.nsc] = x.ptr;
-    s.scdiv[s.nsc] = div;
-    s.scmod[s.nsc] = s.size[a];
-    ++s.nsc;
-  }
   Op op;
   op.kind = OP_SCATTER;
   op.tin = op.tw = op.tout = C.et;
@@ -813,7 +848,14 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) 
       Ax nax{AX_SK, v, nd.s, 0};
       TTNN_TRY(contract_view(C, Gt, k, facY(C, nd.hi - 1), P.smax, 1, -1, &nax, &z));
     }
-    if (v == P.ychild) {
+    if (v == P.ychild && C.yom && Gt.ax.back().bc > 0) {
+      // rank-one box: G = m (x) x, so Omega = (Y^T m) (x) x, and Y^T m is
+      // the Y part of the pass's matrix-vector product
+      om.ptr = (char*)C.yom;
+      om.ax = {Ax{AX_SK, v, nd.s, 0}, Gt.ax.back()};
+      om.ld = 1;
+      om.sc = Gt.sc;
+    } else if (v == P.ychild) {
       // Y of the pass-side root child is the stored (rounded) block
       View mg = Gt;
       int64_t nb = 1;
@@ -1052,7 +1094,10 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
       gld = nL;
     }
   }
-  if (!P.nodes[P.ychild].identity) {
+  // rank-one box whose Y child lies on the matrix-vector side: the walk takes
+  // the Y child's Omega from that product and needs no Y block
+  const bool y_from_gemv = (r1 == 1 && P.yside == 1) || (r1 == 2 && P.yside == 0);
+  if (!P.nodes[P.ychild].identity && !y_from_gemv) {
     const TNode& yc = P.nodes[P.ychild];
     int64_t ny = 1;
     for (int m = yc.lo; m < yc.hi; ++m) ny *= box.ext[m];
@@ -1075,6 +1120,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   const void* r1_brow = r1 == 1 ? sR : sL;
   const char* Mw = r1 && P.pass_store == 2 ? ws.alloc(r1_rows * eb) : (const char*)data;
   const char* bw = r1 && P.side_store == 2 ? ws.alloc((int64_t)r1_bpad * eb) : (const char*)r1_brow;
+  if (y_from_gemv) C.yom = r1 == 1 ? D2 + (int64_t)P.rXR * eb : D1 + (int64_t)P.rXL * eb;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
   // the pass's own temporaries are released right after it and are not
   // program buffers: keep them out of the dependency registry
@@ -1230,7 +1276,14 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     if (P.yside == 0) {
       View H{D1 + (int64_t)P.rXL * eb, mode_axes(P.Llo, P.Lhi), P.wRpad};
       H.ax.push_back(Ax{AX_SK, P.ychild, P.wYR, 0});
-      if (r1 == 1) H = bview(P.Llo, P.Lhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYR, bw + (int64_t)P.rXL * eb);
+      if (r1 == 1 && P.yR_ident && P.Rhi - P.Rlo == 1) {
+        // identity Y child: its row is one-hot, so only the fixed index of
+        // the state is touched (a raw mode axis at the box offset)
+        H = View{(char*)Mw, mode_axes(P.Llo, P.Lhi), 1};
+        H.ax.push_back(Ax{AX_MODE, P.Rlo, 1, box.off[P.Rlo]});
+      } else if (r1 == 1) {
+        H = bview(P.Llo, P.Lhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYR, bw + (int64_t)P.rXL * eb);
+      }
       View cur = H;
       for (int k = (int)P.Lch.size() - 1; k >= 0; --k) {
         const TNode& c = P.nodes[P.Lch[k]];
@@ -1246,7 +1299,12 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     } else {
       View H{D2 + (int64_t)P.rXR * eb, mode_axes(P.Rlo, P.Rhi), P.wLpad};
       H.ax.push_back(Ax{AX_SK, P.ychild, P.wYL, 0});
-      if (r1 == 2) H = bview(P.Rlo, P.Rhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYL, bw + (int64_t)P.rXR * eb);
+      if (r1 == 2 && P.yL_ident && P.Lhi - P.Llo == 1) {
+        H = View{(char*)Mw, mode_axes(P.Rlo, P.Rhi), 1};
+        H.ax.push_back(Ax{AX_MODE, P.Llo, 1, box.off[P.Llo]});
+      } else if (r1 == 2) {
+        H = bview(P.Rlo, P.Rhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYL, bw + (int64_t)P.rXR * eb);
+      }
       View cur = H;
       for (int k = (int)P.Rch.size() - 1; k >= 0; --k) {
         const TNode& c = P.nodes[P.Rch[k]];

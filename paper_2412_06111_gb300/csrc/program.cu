@@ -313,28 +313,81 @@ __device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
   }
 }
 
+template <typename I>
+__device__ __forceinline__ I scatter_div(const Scatter& s, int a, I n) {
+  if (sizeof(I) == 4) {
+    const uint32_t r = (uint32_t)n;
+    return (I)(uint32_t)(((uint64_t)__umulhi(r, s.mag[a]) + r) >> s.shf[a]);
+  }
+  return n / (I)s.size[a];
+}
+
+// Element e's offsets in `in` and `out` and its index on every scaled axis.
+template <typename I>
+__device__ __forceinline__ void scatter_decode(const Scatter& s, I e, int64_t* io, int64_t* oo,
+                                               I* si) {
+  int64_t ii = 0, o = 0;
+  I rem = e;
+  for (int a = s.nd - 1; a >= 0; --a) {
+    const I q = scatter_div(s, a, rem);
+    const I i = rem - q * (I)s.size[a];
+    rem = q;
+    ii += i * s.is[a];
+    o += i * s.os[a];
+#pragma unroll
+    for (int k = 0; k < kMaxScales; ++k)
+      if (k < s.nsc && s.scax[k] == a) si[k] = i;
+  }
+  *io = ii;
+  *oo = o;
+}
+
 template <typename T, typename I>
 __device__ void dev_scatter(const DevOp& op, int64_t blk) {
   const Scatter& s = op.s;
   I total = 1;
   for (int a = 0; a < s.nd; ++a) total *= (I)s.size[a];
-  // op.chunk elements per thread, consecutive threads on consecutive elements
-  for (int it = 0; it < op.chunk; ++it) {
-    const I e = (I)((blk * op.chunk + it) * kExecThreads) + (I)threadIdx.x;
-    if (e >= total) return;
-    I rem = e;
-    int64_t io = 0, oo = 0;
-    for (int a = s.nd - 1; a >= 0; --a) {
-      const I i = rem % (I)s.size[a];
-      rem /= (I)s.size[a];
-      io += i * s.is[a];
-      oo += ((int64_t)s.off[a] + i) * s.os[a];
-    }
-    T v = ((const T*)s.in)[io];
-    for (int k = 0; k < s.nsc; ++k) v *= ((const T*)s.sc[k])[(e / (I)s.scdiv[k]) % (I)s.scmod[k]];
-    T* out = (T*)s.out;
+  // op.chunk elements per thread, kExecThreads apart: after the first, a
+  // step stays on the last axis' row while it can (no full decode)
+  const int L = s.nd - 1;
+  const I nl = (I)s.size[L];
+  const int64_t isl = s.is[L], osl = s.os[L];
+  int lk = -1;   // the scale on the last axis, if any
+  for (int k = 0; k < s.nsc; ++k)
+    if (s.scax[k] == L) lk = k;
+  I e = (I)(blk * op.chunk * kExecThreads) + (I)threadIdx.x;
+  if (e >= total) return;
+  int64_t io, oo;
+  I si[kMaxScales];
+#pragma unroll
+  for (int k = 0; k < kMaxScales; ++k) si[k] = 0;
+  scatter_decode(s, e, &io, &oo, si);
+  I il = e - scatter_div(s, L, e) * nl;
+  const T* in = (const T*)s.in;
+  T* out = (T*)s.out;
+  for (int it = 0;;) {
+    T v = in[io];
+#pragma unroll
+    for (int k = 0; k < kMaxScales; ++k)
+      if (k < s.nsc) v *= ((const T*)s.sc[k])[si[k]];
     if (s.assign) out[oo] = (T)s.alpha * v;
     else out[oo] = out[oo] + (T)s.alpha * v;
+    if (++it == op.chunk) return;
+    e += (I)kExecThreads;
+    if (e >= total) return;
+    il += (I)kExecThreads;
+    if (il < nl) {
+      io += (int64_t)kExecThreads * isl;
+      oo += (int64_t)kExecThreads * osl;
+      if (lk >= 0) {
+#pragma unroll
+        for (int k = 0; k < kMaxScales; ++k)
+          if (k == lk) si[k] = il;
+      }
+    } else {
+      scatter_decode(s, e, &io, &oo, si);
+      il = e - scatter_div(s, L, e) * nl;
+    }
   }
 }
 
