@@ -124,8 +124,8 @@ struct QrJob {
   double* rp;
   int s, r;
 };
-ttnn_status launch_qr_pinv(const QrJob* jobs_dev, int njobs, int state_f64, double eps_factor,
-                           double u, int* kept_dev, cudaStream_t st);
+ttnn_status launch_qr_pinv(const QrJob* jobs_dev, int njobs, int rmax, int state_f64,
+                           double eps_factor, double u, int* kept_dev, cudaStream_t st);
 constexpr int kMaxRecoverS = 128;
 constexpr int kMaxRecoverR = 64;
 

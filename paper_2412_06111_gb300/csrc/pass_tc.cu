@@ -41,6 +41,8 @@ struct Params {
   float* D1p;      // [C][nb*128][wRpad] chunk partials (C > 1, no cluster)
   float* D2p;      // [G][C*tiles*128][wLpad]
   int* err;
+  int* cnt;        // [nb][4] chunk arrivals per row block and epilogue warp (C > 1, no cluster), zero at launch
+  int discard;     // partial rows are whole 128-byte lines: drop them from L2 once summed
 };
 
 // --- thread-block cluster (distributed shared memory) helpers
@@ -278,8 +280,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_after();
       const int64_t row = (int64_t)(b0 + u) * kTileM + r_in;
       if (!p.cluster) {
-        // C == 1: D1 directly; C > 1: this chunk's partial, summed in chunk
-        // order by reduce_partials after the kernel (deterministic)
+        // C == 1: D1 directly; C > 1: this chunk's partial.  The chunk CTA
+        // that finishes a row block last sums its C partials in chunk order
+        // into D1 (deterministic: the order does not depend on who is last)
         float* dst = p.C == 1 ? p.D1 + row * p.wRpad
                               : p.D1p + ((int64_t)c * p.nb * kTileM + row) * p.wRpad;
         for (int cg = 0; cg < p.wRpad; cg += 16) {
@@ -297,6 +300,63 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
+        if (p.C > 1) {
+          // per epilogue warp (its 32 rows): arrival after its own stores
+          __threadfence();
+          __syncwarp();
+          int last = 0;
+          if (lane == 0) last = atomicAdd(&p.cnt[(int64_t)(b0 + u) * 4 + q], 1) == p.C - 1;
+          last = __shfl_sync(0xffffffffu, last, 0);
+          if (last) {
+            // the warp's 32 rows are contiguous in every chunk's partial:
+            // coalesced float4 loads, several in flight per lane
+            __threadfence();
+            const int per = p.wRpad / 4;                        // float4 per row
+            const int64_t cs4 = (int64_t)p.nb * kTileM * per;   // chunk stride
+            const int64_t row0 = (int64_t)(b0 + u) * kTileM + 32 * q;
+            const int64_t lim = (p.nL - row0) * per;            // valid float4 of the 32 rows
+            const float4* src = reinterpret_cast<const float4*>(p.D1p) + row0 * per;
+            float4* out = reinterpret_cast<float4*>(p.D1) + row0 * per;
+            const int n4 = 32 * per;
+            for (int e0 = lane; e0 < n4; e0 += 128) {
+              float4 acc[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int e = e0 + 32 * j;
+                acc[j] = e < n4 ? __ldcg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+              for (int cc = 1; cc < p.C; ++cc) {
+                float4 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const int e = e0 + 32 * j;
+                  v[j] = e < n4 ? __ldcg(src + cc * cs4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  acc[j].x += v[j].x;
+                  acc[j].y += v[j].y;
+                  acc[j].z += v[j].z;
+                  acc[j].w += v[j].w;
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int e = e0 + 32 * j;
+                if (e < n4 && e < lim) out[e] = acc[j];
+              }
+            }
+            if (p.discard) {
+              // the partial rows are dead: no write-back of their lines
+              const int lines = 32 * p.wRpad * 4 / 128;
+              for (int cc = 0; cc < p.C; ++cc)
+                for (int l = lane; l < lines; l += 32)
+                  asm volatile("discard.global.L2 [%0], 128;" ::"l"(
+                                   (const char*)(src + cc * cs4) + (int64_t)l * 128)
+                               : "memory");
+            }
+          }
+        }
         continue;
       }
       // cluster: partial tile -> own shared memory, then every CTA sums its
@@ -610,7 +670,9 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
     set_error("tensor-core pass: unsupported geometry");
     return TTNN_EUNSUPPORTED;
   }
-  const int64_t need = (g.d1p_elems + g.d2p_elems) * 4 + 512;
+  const bool fold = !g.cluster && g.C > 1;   // D1 partials summed inside the kernel
+  const int64_t cnt_bytes = fold ? ((int64_t)g.nb * 16 + 255) / 256 * 256 : 0;
+  const int64_t need = (g.d1p_elems + g.d2p_elems) * 4 + cnt_bytes + 512;
   if (dry) {
     if (ws_need) *ws_need = need;
     return TTNN_OK;
@@ -644,6 +706,11 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
   prm.D2p = (float*)ws + g.d1p_elems;
 
   prm.err = P.err_dev;
+  prm.cnt = fold ? (int*)((char*)ws + (g.d1p_elems + g.d2p_elems) * 4 + 256 -
+                          (((uintptr_t)ws + (g.d1p_elems + g.d2p_elems) * 4) & 255))
+                 : nullptr;
+  prm.discard = (P.wRpad * 4) % 128 == 0 && ((uintptr_t)prm.D1p & 127) == 0;
+  if (fold) TTNN_TRY_CUDA(cudaMemsetAsync(prm.cnt, 0, (size_t)g.nb * 16, st));
   TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_kernel, 0));
   if (g.cluster) {
     cudaLaunchConfig_t cfg = {};
@@ -665,11 +732,6 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
     TTNN_TRY(check_launch("tc pass_kernel"));
   }
   const int sms = tc::sm_count();
-  if (!g.cluster && g.C > 1) {
-    tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D1p, g.C, (int64_t)g.nb * tc::kTileM * P.wRpad,
-                                                 nL, P.wRpad, (float*)D1);
-    TTNN_TRY(check_launch("reduce_partials(D1)"));
-  }
   if (P.wLpad > 0) {
     tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
                                                  nR, P.wLpad, (float*)D2);

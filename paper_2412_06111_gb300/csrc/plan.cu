@@ -3,6 +3,7 @@
 // that turns its two products into every node's Omega_v and Psi_v, and the
 // binary64 core assembly.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdio>
 #include <functional>
@@ -1689,9 +1690,13 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
     job_node.push_back(v);
   }
   if (!dry && !jobs.empty()) {
-    TTNN_TRY_CUDA(cudaMemcpyAsync(P.jobs_dev, jobs.data(), jobs.size() * sizeof(QrJob),
-                                  cudaMemcpyHostToDevice, st));
-    TTNN_TRY(launch_qr_pinv(P.jobs_dev, (int)jobs.size(), P.walk_f64, P.eps_factor, P.u,
+    if (jobs.size() != P.jobs_host.size() ||
+        memcmp(jobs.data(), P.jobs_host.data(), jobs.size() * sizeof(QrJob)) != 0) {
+      TTNN_TRY_CUDA(cudaMemcpyAsync(P.jobs_dev, jobs.data(), jobs.size() * sizeof(QrJob),
+                                    cudaMemcpyHostToDevice, st));
+      P.jobs_host = jobs;
+    }
+    TTNN_TRY(launch_qr_pinv(P.jobs_dev, (int)jobs.size(), P.rmax, P.walk_f64, P.eps_factor, P.u,
                             P.kept_dev, st));
   }
   ws.prog = &prog;   // Q and R_eps^+ above are produced before the program (level 0)

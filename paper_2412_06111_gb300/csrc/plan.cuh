@@ -70,6 +70,7 @@ struct ttnn_plan_s {
   // workspace bytes a dense update needs, by box extents (+ whole-tensor flag)
   std::map<std::vector<int64_t>, int64_t> ws_need_cache;
   ttnn::QrJob* jobs_dev = nullptr;
+  std::vector<ttnn::QrJob> jobs_host;   // what jobs_dev holds (upload skipped when unchanged)
   int* kept_dev = nullptr;
   int* err_dev = nullptr;       // device error word of bounded waits (tensor-core pass)
   // read-back of the last recovery: kept ranks, Jacobi sweeps, error word
