@@ -41,6 +41,8 @@ struct CvtParams {
   const float* scale;    // FP8: [ceil(nL/128)][ncolt]
   float* D1;             // [nL][wRpad] (C == 1)
   float* D1p;            // [C][nb*128][wRpad] chunk partials (C > 1)
+  int* cnt;              // [nb][4] chunk arrivals per row block and epilogue warp, zero at launch
+  int discard;           // partial rows are whole 128-byte lines
   float* D2p;            // [G][C*tiles*128][wLpad]
   int* err;
 };
@@ -385,6 +387,9 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
+      if (p.C > 1)
+        fold_d1_rows(&p.cnt[(int64_t)(b0 + u) * 4 + q], p.C, p.D1p, p.D1, p.nb, p.wRpad,
+                     (int64_t)(b0 + u) * kTileM + 32 * q, p.nL, p.discard, lane);
     }
     if (!ok) {
       abort_flag = 1;
@@ -534,7 +539,8 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
     set_error("tensor-core pass (converted formats): unsupported geometry");
     return TTNN_EUNSUPPORTED;
   }
-  const int64_t need = (g.d1p_elems + g.d2p_elems) * 4 + 512;
+  const int64_t cnt_bytes = g.C > 1 ? ((int64_t)g.nb * 16 + 255) / 256 * 256 : 0;
+  const int64_t need = (g.d1p_elems + g.d2p_elems) * 4 + cnt_bytes + 512;
   if (dry) {
     if (ws_need) *ws_need = need;
     return TTNN_OK;
@@ -578,6 +584,11 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
   prm.D1p = (float*)ws;
   prm.D2p = (float*)ws + g.d1p_elems;
   prm.err = P.err_dev;
+  prm.cnt = g.C > 1 ? (int*)((char*)ws + (g.d1p_elems + g.d2p_elems) * 4 + 256 -
+                            (((uintptr_t)ws + (g.d1p_elems + g.d2p_elems) * 4) & 255))
+                    : nullptr;
+  prm.discard = (P.wRpad * 4) % 128 == 0 && ((uintptr_t)prm.D1p & 127) == 0;
+  if (g.C > 1) TTNN_TRY_CUDA(cudaMemsetAsync(prm.cnt, 0, (size_t)g.nb * 16, st));
   if (mode == tc::MODE_SPLIT) {
     TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_SPLIT>, 1));
     tc::pass_cvt_kernel<tc::MODE_SPLIT><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
@@ -587,11 +598,6 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
   }
   TTNN_TRY(check_launch("tc pass_cvt_kernel"));
   const int sms = tc::sm_count();
-  if (g.C > 1) {
-    tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D1p, g.C, (int64_t)g.nb * tc::kTileM * P.wRpad,
-                                                 nL, P.wRpad, (float*)D1);
-    TTNN_TRY(check_launch("reduce_partials(D1)"));
-  }
   tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
                                                nR, P.wLpad, (float*)D2);
   TTNN_TRY(check_launch("reduce_partials(D2)"));

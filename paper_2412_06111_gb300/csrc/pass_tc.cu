@@ -300,63 +300,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
-        if (p.C > 1) {
-          // per epilogue warp (its 32 rows): arrival after its own stores
-          __threadfence();
-          __syncwarp();
-          int last = 0;
-          if (lane == 0) last = atomicAdd(&p.cnt[(int64_t)(b0 + u) * 4 + q], 1) == p.C - 1;
-          last = __shfl_sync(0xffffffffu, last, 0);
-          if (last) {
-            // the warp's 32 rows are contiguous in every chunk's partial:
-            // coalesced float4 loads, several in flight per lane
-            __threadfence();
-            const int per = p.wRpad / 4;                        // float4 per row
-            const int64_t cs4 = (int64_t)p.nb * kTileM * per;   // chunk stride
-            const int64_t row0 = (int64_t)(b0 + u) * kTileM + 32 * q;
-            const int64_t lim = (p.nL - row0) * per;            // valid float4 of the 32 rows
-            const float4* src = reinterpret_cast<const float4*>(p.D1p) + row0 * per;
-            float4* out = reinterpret_cast<float4*>(p.D1) + row0 * per;
-            const int n4 = 32 * per;
-            for (int e0 = lane; e0 < n4; e0 += 128) {
-              float4 acc[4];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const int e = e0 + 32 * j;
-                acc[j] = e < n4 ? __ldcg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-              }
-              for (int cc = 1; cc < p.C; ++cc) {
-                float4 v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const int e = e0 + 32 * j;
-                  v[j] = e < n4 ? __ldcg(src + cc * cs4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  acc[j].x += v[j].x;
-                  acc[j].y += v[j].y;
-                  acc[j].z += v[j].z;
-                  acc[j].w += v[j].w;
-                }
-              }
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const int e = e0 + 32 * j;
-                if (e < n4 && e < lim) out[e] = acc[j];
-              }
-            }
-            if (p.discard) {
-              // the partial rows are dead: no write-back of their lines
-              const int lines = 32 * p.wRpad * 4 / 128;
-              for (int cc = 0; cc < p.C; ++cc)
-                for (int l = lane; l < lines; l += 32)
-                  asm volatile("discard.global.L2 [%0], 128;" ::"l"(
-                                   (const char*)(src + cc * cs4) + (int64_t)l * 128)
-                               : "memory");
-            }
-          }
-        }
+        if (p.C > 1)
+          fold_d1_rows(&p.cnt[(int64_t)(b0 + u) * 4 + q], p.C, p.D1p, p.D1, p.nb, p.wRpad,
+                       (int64_t)(b0 + u) * kTileM + 32 * q, p.nL, p.discard, lane);
         continue;
       }
       // cluster: partial tile -> own shared memory, then every CTA sums its

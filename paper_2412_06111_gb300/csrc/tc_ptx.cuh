@@ -135,5 +135,67 @@ int sm_count();
 __global__ void reduce_partials(const float* P, int K, int64_t stride_k, int64_t rows, int wpad,
                                 float* D);
 
+// D1 of a pass split into C column chunks: every chunk CTA writes its partial
+// rows of a row block (D1p = [C][nb*128][wRpad]) and then, per epilogue warp
+// (its 32 rows row0..row0+31), counts its arrival in *slot.  The warp that
+// arrives last sums the C partials in chunk order (the same order as
+// reduce_partials, whoever is last) into D1, with coalesced loads of the 32
+// contiguous rows, and drops the dead partial lines from L2 (`discard`: rows
+// are whole 128-byte lines).  Called by all 32 lanes after their own stores;
+// no thread waits on another.
+__device__ __forceinline__ void fold_d1_rows(int* slot, int C, const float* D1p, float* D1,
+                                             int64_t nb, int wRpad, int64_t row0, int64_t nL,
+                                             int discard, int lane) {
+  __threadfence();
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) last = atomicAdd(slot, 1) == C - 1;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  const int per = wRpad / 4;                       // float4 per row
+  const int64_t cs4 = nb * kTileM * per;           // chunk stride
+  const int64_t lim = (nL - row0) * per;           // valid float4 of the 32 rows
+  const float4* src = reinterpret_cast<const float4*>(D1p) + row0 * per;
+  float4* out = reinterpret_cast<float4*>(D1) + row0 * per;
+  const int n4 = 32 * per;
+  for (int e0 = lane; e0 < n4; e0 += 128) {
+    float4 acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = e0 + 32 * j;
+      acc[j] = e < n4 ? __ldcg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int cc = 1; cc < C; ++cc) {
+      float4 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = e0 + 32 * j;
+        v[j] = e < n4 ? __ldcg(src + cc * cs4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[j].x += v[j].x;
+        acc[j].y += v[j].y;
+        acc[j].z += v[j].z;
+        acc[j].w += v[j].w;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = e0 + 32 * j;
+      if (e < n4 && e < lim) out[e] = acc[j];
+    }
+  }
+  if (discard) {
+    const int lines = 32 * wRpad * 4 / 128;
+    for (int cc = 0; cc < C; ++cc)
+      for (int l = lane; l < lines; l += 32)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"((const char*)(src + cc * cs4) +
+                                                            (int64_t)l * 128)
+                     : "memory");
+  }
+}
+
 }  // namespace tc
 }  // namespace ttnn
