@@ -539,8 +539,10 @@ def main():
                     help="leave out the streamed-update and serving-mix legs (extra keys)")
     ap.add_argument("--nmode", type=int, default=NMODE, help="mode size (64 = the stated workload)")
     ap.add_argument("--headline-only", action="store_true",
-                    help="time only the BF16 TTNN step (no other forms, e2e or serving legs; "
-                         "holds just the BF16 tensor on the device, e.g. for profiling)")
+                    help="time only one form's step (default the BF16 TTNN headline; no other "
+                         "forms, e2e or serving legs; e.g. for profiling)")
+    ap.add_argument("--form", default="bf16", choices=["bf16", "sttnn", "fp32", "bf16x2", "fp8"],
+                    help="the form --headline-only times")
     args = ap.parse_args()
     NMODE = args.nmode
     warmup = max(3, args.warmup)
@@ -575,25 +577,36 @@ def main():
     hbm, bf16_tf, peak_src = _peaks()
     N = NMODE ** D
     a32 = W.inv_sum_slab_torch(D, NMODE, ws, rank, "cuda", torch.float32)
-    a16 = a32.to(torch.bfloat16)
     if args.headline_only:
+        # one form, holding only the tensor that form reads
+        dt, var, narrow, quant = {"bf16": (api.BF16, api.VARIANT_TTNN, True, False),
+                                  "sttnn": (api.BF16, api.VARIANT_STTNN, True, False),
+                                  "fp32": (api.F32, api.VARIANT_TTNN, False, False),
+                                  "bf16x2": (api.BF16X2, api.VARIANT_TTNN, False, False),
+                                  "fp8": (api.E4M3, api.VARIANT_TTNN, False, True)}[args.form]
+        data = a32.to(torch.bfloat16) if narrow else a32
         del a32
         torch.cuda.empty_cache()
-    log("tensor ready", N)
-    with Clocks(dev) as clk:
-        bf = run_form(api, W, api.BF16, api.VARIANT_TTNN, args.steps, warmup, ws, torch, a16,
-                      rank=rank)
-    if args.headline_only:
+        with Clocks(dev) as clk:
+            bf = run_form(api, W, dt, var, args.steps, warmup, ws, torch, data, quantize=quant,
+                          rank=rank)
         ms = _max_over_ranks(bf["ms_per_step"], ws)
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": N * 2 * ws / (ms * 1e-3) / 1e9,
+            eb, dts = {"bf16": (2, "bf16"), "sttnn": (2, "bf16"), "fp32": (4, "f32"),
+                       "bf16x2": (4, "f32"), "fp8": (1, "e4m3")}[args.form]
+            print(json.dumps({"metric": METRIC, "value": N * eb * ws / (ms * 1e-3) / 1e9,
                               "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
-                              "warmup": warmup, "ms_per_step": ms, "dtype": "bf16",
-                              "headline_only": True,
+                              "warmup": warmup, "ms_per_step": ms, "dtype": dts,
+                              "headline_only": True, "form": args.form,
                               "phases_ms": {"pass": bf["pass_ms"], "walk": bf["walk_ms"],
                                             "recover": bf["recover_ms"]},
                               "clocks": clk.summary()}))
         return
+    a16 = a32.to(torch.bfloat16)
+    log("tensor ready", N)
+    with Clocks(dev) as clk:
+        bf = run_form(api, W, api.BF16, api.VARIANT_TTNN, args.steps, warmup, ws, torch, a16,
+                      rank=rank)
     k = max(3, args.steps // 2)
     f32 = run_form(api, W, api.F32, api.VARIANT_TTNN, k, warmup, ws, torch, a32, rank=rank)
     x2 = run_form(api, W, api.BF16X2, api.VARIANT_TTNN, k, warmup, ws, torch, a32, rank=rank)
