@@ -418,7 +418,7 @@ def run_streaming(api, W, torch, n_updates=4096, n_lat=256):
             "recover_ms": rec_ms}
 
 
-def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
+def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=3.0):
     """Serving mix: n_streams resident BF16 streams of mixed order, sizes,
     trees and ranks (workloads.serving_stream_spec; streams whose device
     footprint exceeds 512 MiB are redrawn), fed a Poisson stream of N(0,1)
@@ -502,7 +502,8 @@ def run_serving(api, W, torch, n_streams=256, rate=20000.0, seconds=3.0):
     api.ttnn_server_destroy(srv)
     return {"workload": f"{n_streams} streams (d 3-6, n in 16..128, binary/TT/Tucker, r 4-32, "
                         f"p=r/2, BF16), Poisson slices at {rate:.0f}/s for {seconds:.0f} s",
-            "offered_per_s": len(arrivals) / seconds, "completed": rep["completed_updates"],
+            "offered_per_s": len(arrivals) / seconds, "target_per_s": 20000,
+            "drain_s": wall - seconds, "completed": rep["completed_updates"],
             "completed_per_s": rep["completed_updates"] / wall, "failed": failed + rep["failed"],
             "update_gbs": rep["update_bytes"] / wall / 1e9,
             "latency_us": {"p50": rep["p50_us"], "p99": rep["p99_us"], "max": rep["max_us"]},

@@ -251,7 +251,9 @@ ttnn_status ttnn_update_ttn(ttnn_state_t state, const double* const* cores_in,
 
 /* ttnn_recover -- A9 [Sec. 4 recovery phase, Algorithm 2, stabilised least
  * squares with eps = eps_factor * u * ||R_v||_2]: QR of every Omega_v
- * (diag R >= 0), eps-pseudo-inverse of R_v by one-sided Jacobi SVD, then
+ * (diag R >= 0; CholeskyQR2 when both Gram matrices are safely positive
+ * definite, else Householder), eps-pseudo-inverse of R_v (R_v^-1 when
+ * sigma_min(R_v) > eps is certified, else by one-sided Jacobi SVD), then
  * B_v = (kron_c Q_c)^T Psi_v R_v,eps^+ (children's Q), leaf B_v = Psi_v
  * R_v,eps^+, root B = (kron_c Q_c)^T Psi_root; all in binary64.
  * cores: device, core_elems binary64 values at the per-node offsets.
