@@ -623,13 +623,34 @@ __device__ __forceinline__ Tacc load_as(const Tin* p) { return (Tacc)to_f32(*p);
 template <>
 __device__ __forceinline__ double load_as<double, double>(const double* p) { return *p; }
 
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+constexpr int GB_M = 128, GB_N = 64, GB_K = 16;
+constexpr int GB_PAD = 4;   // keeps 16-byte rows for the vector reads
 
-// 256 threads; each computes a 4 x 4 block of the 64 x 64 output tile.
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float* p, float* v) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void load(const double* p, double* v) {
+    const double2 x = reinterpret_cast<const double2*>(p)[0];
+    const double2 y = reinterpret_cast<const double2*>(p)[1];
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+};
+
+// 256 threads; each computes an 8 x 4 block of the 128 x 64 output tile.
+// The next k-tile's elements are fetched into registers while the current
+// one is multiplied out of shared memory.
 template <typename Tin, typename Tacc>
 __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t kchunk, Tacc* partial) {
-  __shared__ Tacc As[GB_K][GB_M + 1];
-  __shared__ Tacc Bs[GB_K][GB_N + 1];
+  __shared__ __align__(16) Tacc As[GB_K][GB_M + GB_PAD];
+  __shared__ __align__(16) Tacc Bs[GB_K][GB_N + GB_PAD];
   const Tin* A = (const Tin*)g.A;
   const Tin* B = (const Tin*)g.B;
   const int tid = threadIdx.x;
@@ -638,41 +659,57 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
   const int split = blockIdx.z;
   const int64_t kb = split * kchunk;
   const int64_t ke = min(g.K, kb + kchunk);
-  const int ty = tid / 16, tx = tid % 16;   // output rows ty*4.., cols tx*4..
-  Tacc acc[4][4];
+  const int ty = tid / 16, tx = tid % 16;   // output rows ty*8.., cols tx*4..
+  Tacc acc[8][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
   const bool a_k_contig = (g.ask == 1);
   const bool b_k_contig = (g.bsk == 1);
-  for (int64_t k0 = kb; k0 < ke; k0 += GB_K) {
-    // 64 x 16 tiles: 1024 elements, 4 per thread
+  // this thread's elements of a tile: A 128 x 16 (8 each), B 64 x 16 (4 each)
+  int aii[8], akk[8], bjj[4], bkk[4];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    const int e = tid + l * 256;
+    if (a_k_contig) { aii[l] = e / GB_K; akk[l] = e % GB_K; }
+    else { akk[l] = e / GB_M; aii[l] = e % GB_M; }
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int e = tid + l * 256;
+    if (b_k_contig) { bjj[l] = e / GB_K; bkk[l] = e % GB_K; }
+    else { bkk[l] = e / GB_N; bjj[l] = e % GB_N; }
+  }
+  Tacc ra[8], rb[4];
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int64_t gi = i0 + aii[l], gk = k0 + akk[l];
+      ra[l] = (gi < g.I && gk < ke) ? load_as<Tin, Tacc>(A + gi * g.asi + gk * g.ask) : (Tacc)0;
+    }
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-      const int e = tid + l * 256;
-      int ii, kk;
-      if (a_k_contig) { ii = e / GB_K; kk = e % GB_K; }
-      else { kk = e / GB_M; ii = e % GB_M; }
-      const int64_t gi = i0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < g.I && gk < ke) ? load_as<Tin, Tacc>(A + gi * g.asi + gk * g.ask) : (Tacc)0;
-      int jj, kk2;
-      if (b_k_contig) { jj = e / GB_K; kk2 = e % GB_K; }
-      else { kk2 = e / GB_N; jj = e % GB_N; }
-      const int64_t gj = j0 + jj, gk2 = k0 + kk2;
-      Bs[kk2][jj] = (gj < g.Jn && gk2 < ke) ? load_as<Tin, Tacc>(B + gj * g.bsj + gk2 * g.bsk) : (Tacc)0;
+      const int64_t gj = j0 + bjj[l], gk = k0 + bkk[l];
+      rb[l] = (gj < g.Jn && gk < ke) ? load_as<Tin, Tacc>(B + gj * g.bsj + gk * g.bsk) : (Tacc)0;
     }
+  };
+  if (kb < ke) fetch(kb);
+  for (int64_t k0 = kb; k0 < ke; k0 += GB_K) {
+#pragma unroll
+    for (int l = 0; l < 8; ++l) As[akk[l]][aii[l]] = ra[l];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) Bs[bkk[l]][bjj[l]] = rb[l];
     __syncthreads();
+    if (k0 + GB_K < ke) fetch(k0 + GB_K);
 #pragma unroll
     for (int kk = 0; kk < GB_K; ++kk) {
-      Tacc a[4], b[4];
+      Tacc a[8], b[4];
+      Vec4<Tacc>::load(&As[kk][ty * 8], a);
+      Vec4<Tacc>::load(&As[kk][ty * 8 + 4], a + 4);
+      Vec4<Tacc>::load(&Bs[kk][tx * 4], b);
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        a[x] = As[kk][ty * 4 + x];
-        b[x] = Bs[kk][tx * 4 + x];
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < 8; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
     }
@@ -680,8 +717,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
   }
   Tacc* C = nsplit > 1 ? partial + (int64_t)split * g.I * g.ldc : (Tacc*)g.C;
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int64_t gi = i0 + ty * 4 + x;
+  for (int x = 0; x < 8; ++x) {
+    const int64_t gi = i0 + ty * 8 + x;
     if (gi >= g.I) continue;
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
