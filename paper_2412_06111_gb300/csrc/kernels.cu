@@ -255,10 +255,33 @@ __device__ __forceinline__ double load_acc(const double* p, int64_t i, double) {
 
 constexpr int kGemvCols = 8;
 
-template <typename Tm, typename Ts, typename Tacc>
+// The value the passes sketch for element `i` of the box's rows, per format:
+// plain (f64 / f32 / bf16), BF16x2 (hi + lo with hi = bf16(x), lo = bf16(x -
+// hi)) or E4M3 (bf16(f32(q) * s), s the binary32 scale of the element's 128-
+// element tile of these rows).
+enum { RV_PLAIN = 0, RV_SPLIT = 1, RV_FP8 = 2 };
+template <int MODE, typename Tm, typename Tacc>
+__device__ __forceinline__ Tacc row_value(const Tm* m, int64_t i, const float* scale) {
+  if constexpr (MODE == RV_SPLIT) {
+    const float x = ((const float*)m)[i];
+    const float h = __bfloat162float(__float2bfloat16_rn(x));
+    const float l = __bfloat162float(__float2bfloat16_rn(x - h));
+    return (Tacc)(h + l);
+  } else if constexpr (MODE == RV_FP8) {
+    __nv_fp8_e4m3 q;
+    q.__x = ((const uint8_t*)m)[i];
+    const float v = __fmul_rn(static_cast<float>(q), scale[i >> 7]);
+    return (Tacc)__bfloat162float(__float2bfloat16_rn(v));
+  } else {
+    return load_acc(m, i, Tacc(0));
+  }
+}
+
+template <typename Tm, typename Ts, typename Tacc, int MODE = RV_PLAIN>
 __global__ void __launch_bounds__(256) side_gemv_kernel(SideSpec s, const Ts* src, int64_t src_ld,
                                                         int cut, const Tm* m, int64_t rows,
-                                                        int cols, int64_t rpb, Tacc* part) {
+                                                        int cols, int64_t rpb, Tacc* part,
+                                                        const float* scale) {
   __shared__ Tacc red[8][kGemvCols];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * rpb;
@@ -279,7 +302,7 @@ __global__ void __launch_bounds__(256) side_gemv_kernel(SideSpec s, const Ts* sr
           stride *= s.full[mm];
         }
       }
-      const Tacc mv = load_acc(m, row, Tacc(0));
+      const Tacc mv = row_value<MODE, Tm, Tacc>(m, row, scale);
 #pragma unroll
       for (int k = 0; k < kGemvCols; ++k)
         if (c0 + k < cols) acc[k] += mv * load_acc(src, (int64_t)(c0 + k) * src_ld + f, Tacc(0));
@@ -311,9 +334,9 @@ __global__ void gemv_reduce_kernel(const Tacc* part, int nblk, int cols, int col
 }
 
 ttnn_status launch_side_gemv(const SideSpec& s, const void* src, int64_t src_ld, bool cut,
-                             const void* m, int m_store, int64_t rows, int cols, int cols_pad,
-                             void* D, int d_f64, void* part, int64_t part_bytes, cudaStream_t st,
-                             bool dry, int64_t* need) {
+                             const void* m, int m_store, const float* scale, int64_t rows,
+                             int cols, int cols_pad, void* D, int d_f64, void* part,
+                             int64_t part_bytes, cudaStream_t st, bool dry, int64_t* need) {
   const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 1024), (int64_t)num_sms() * 4));
   const int64_t rpb = ceil_div(rows, nblk);
   const int64_t bytes = nblk * std::max(cols, 1) * (d_f64 ? 8 : 4);
@@ -333,15 +356,28 @@ ttnn_status launch_side_gemv(const SideSpec& s, const void* src, int64_t src_ld,
     }
     if (cols > 0)
       side_gemv_kernel<double, double, double><<<(unsigned)nblk, 256, 0, st>>>(
-          s, (const double*)src, src_ld, cut ? 1 : 0, (const double*)m, rows, cols, rpb, (double*)part);
+          s, (const double*)src, src_ld, cut ? 1 : 0, (const double*)m, rows, cols, rpb,
+          (double*)part, scale);
   } else if (m_store == 1 && s.store == 1) {
     if (cols > 0)
       side_gemv_kernel<float, float, float><<<(unsigned)nblk, 256, 0, st>>>(
-          s, (const float*)src, src_ld, cut ? 1 : 0, (const float*)m, rows, cols, rpb, (float*)part);
+          s, (const float*)src, src_ld, cut ? 1 : 0, (const float*)m, rows, cols, rpb,
+          (float*)part, scale);
   } else if (m_store == 2 && s.store == 2) {
     if (cols > 0)
       side_gemv_kernel<uint16_t, uint16_t, float><<<(unsigned)nblk, 256, 0, st>>>(
-          s, (const uint16_t*)src, src_ld, cut ? 1 : 0, (const uint16_t*)m, rows, cols, rpb, (float*)part);
+          s, (const uint16_t*)src, src_ld, cut ? 1 : 0, (const uint16_t*)m, rows, cols, rpb,
+          (float*)part, scale);
+  } else if (m_store == kStoreSplit && s.store == 2) {
+    if (cols > 0)
+      side_gemv_kernel<float, uint16_t, float, RV_SPLIT><<<(unsigned)nblk, 256, 0, st>>>(
+          s, (const uint16_t*)src, src_ld, cut ? 1 : 0, (const float*)m, rows, cols, rpb,
+          (float*)part, scale);
+  } else if (m_store == kStoreFp8 && s.store == 2 && scale) {
+    if (cols > 0)
+      side_gemv_kernel<uint8_t, uint16_t, float, RV_FP8><<<(unsigned)nblk, 256, 0, st>>>(
+          s, (const uint16_t*)src, src_ld, cut ? 1 : 0, (const uint8_t*)m, rows, cols, rpb,
+          (float*)part, scale);
   } else {
     set_error("rank-one pass: unsupported formats");
     return TTNN_EUNSUPPORTED;
@@ -353,20 +389,27 @@ ttnn_status launch_side_gemv(const SideSpec& s, const void* src, int64_t src_ld,
   return check_launch("gemv_reduce_kernel");
 }
 
-template <typename Ts, typename Td>
-__global__ void to_walk_kernel(const Ts* src, Td* dst, int64_t n) {
+template <typename Ts, typename Td, int MODE = RV_PLAIN>
+__global__ void to_walk_kernel(const Ts* src, Td* dst, int64_t n, const float* scale) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = (Td)load_acc(src, e, Td(0));
+    dst[e] = row_value<MODE, Ts, Td>(src, e, scale);
 }
 
-ttnn_status launch_to_walk(const void* src, int src_store, void* dst, int d_f64, int64_t n,
-                           cudaStream_t st) {
+ttnn_status launch_to_walk(const void* src, int src_store, const float* scale, void* dst,
+                           int d_f64, int64_t n, cudaStream_t st) {
   if (n == 0) return TTNN_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
-  if (!d_f64 && src_store == 2) to_walk_kernel<uint16_t, float><<<blocks, 256, 0, st>>>((const uint16_t*)src, (float*)dst, n);
-  else if (!d_f64 && src_store == 1) to_walk_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)src, (float*)dst, n);
-  else if (d_f64 && src_store == 0) to_walk_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)src, (double*)dst, n);
+  if (!d_f64 && src_store == 2)
+    to_walk_kernel<uint16_t, float><<<blocks, 256, 0, st>>>((const uint16_t*)src, (float*)dst, n, scale);
+  else if (!d_f64 && src_store == 1)
+    to_walk_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)src, (float*)dst, n, scale);
+  else if (d_f64 && src_store == 0)
+    to_walk_kernel<double, double><<<blocks, 256, 0, st>>>((const double*)src, (double*)dst, n, scale);
+  else if (!d_f64 && src_store == kStoreSplit)
+    to_walk_kernel<float, float, RV_SPLIT><<<blocks, 256, 0, st>>>((const float*)src, (float*)dst, n, scale);
+  else if (!d_f64 && src_store == kStoreFp8 && scale)
+    to_walk_kernel<uint8_t, float, RV_FP8><<<blocks, 256, 0, st>>>((const uint8_t*)src, (float*)dst, n, scale);
   else {
     set_error("walk copy: unsupported formats");
     return TTNN_EUNSUPPORTED;

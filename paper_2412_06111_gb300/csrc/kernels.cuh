@@ -95,19 +95,26 @@ ttnn_status launch_side_gather_batch(const GatherJob* jobs, int n, cudaStream_t 
 // left to the walk as a broadcast, and the product against this side is a
 // matrix-vector product with the side block.
 //   D[c] = sum_row m[row] * B[c][map(row)]   (c < cols; zero up to cols_pad)
-// m: the box's rows (storage format m_store: 0 f64, 1 f32, 2 bf16); B: a side
+// m: the box's rows (format m_store: 0 f64, 1 f32, 2 bf16, kStoreSplit,
+// kStoreFp8 with `scale`); B: a side
 // block [cols][...] with leading dimension src_ld in format s.store; map(row)
 // is the row's place in a whole-tensor block (s.ext/off/full) when `cut`,
 // else the row itself.  Accumulates in the walk type (f64 when d_f64) per
 // block of rows, then sums the block partials in a fixed order
 // (deterministic).  With dry, only reports the scratch bytes (`need`).
+// Row formats of launch_side_gemv / launch_to_walk beyond the storage codes
+// 0 f64, 1 f32, 2 bf16: binary32 rows sketched as bf16 hi + lo (BF16x2
+// plans), and E4M3 rows with one binary32 scale per 128 consecutive rows,
+// sketched as bf16(f32(q) * s) (E4M3 plans; `scale` required).
+constexpr int kStoreFp8 = 3, kStoreSplit = 4;
 ttnn_status launch_side_gemv(const SideSpec& s, const void* src, int64_t src_ld, bool cut,
-                             const void* m, int m_store, int64_t rows, int cols, int cols_pad,
-                             void* D, int d_f64, void* part, int64_t part_bytes, cudaStream_t st,
-                             bool dry, int64_t* need);
-// dst[e] = src[e] in the walk type (f32, or f64 when d_f64) for e < n.
-ttnn_status launch_to_walk(const void* src, int src_store, void* dst, int d_f64, int64_t n,
-                           cudaStream_t st);
+                             const void* m, int m_store, const float* scale, int64_t rows,
+                             int cols, int cols_pad, void* D, int d_f64, void* part,
+                             int64_t part_bytes, cudaStream_t st, bool dry, int64_t* need);
+// dst[e] = the value sketched for src[e] (format src_store as above) in the
+// walk type (f32, or f64 when d_f64) for e < n.
+ttnn_status launch_to_walk(const void* src, int src_store, const float* scale, void* dst,
+                           int d_f64, int64_t n, cudaStream_t st);
 
 // misc
 ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st);

@@ -1020,6 +1020,10 @@ ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need) {
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
                              int64_t* peak, UpdateBatch* batch) {
+  if (!dry && P.dtype == TTNN_E4M3 && (!tile_scale || ((uintptr_t)tile_scale & 3))) {
+    set_error("E4M3 updates need their tile scales (4-byte aligned)");
+    return TTNN_EINVAL;
+  }
   if (!dry) {
     int64_t need = 0;
     TTNN_TRY(dense_update_need(P, box, &need));
@@ -1045,7 +1049,8 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   // scale; the product against the other side is a matrix-vector product
   // with its side block, read straight from the cached whole-tensor block
   // when there is one (no box block is formed).
-  const bool r1_fmt = P.dtype == TTNN_F64 || P.dtype == TTNN_F32 || P.dtype == TTNN_BF16;
+  const bool r1_fmt = P.dtype == TTNN_F64 || P.dtype == TTNN_F32 || P.dtype == TTNN_BF16 ||
+                      P.dtype == TTNN_BF16X2 || P.dtype == TTNN_E4M3;
   const int r1 = !r1_fmt || (P.flags & TTNN_FLAG_SIMT_PASS) ? 0
                  : (nR == 1 && nL > 1)                       ? 1
                  : (nL == 1 && nR > 1)                       ? 2
@@ -1119,7 +1124,13 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   const int64_t r1_rows = r1 == 1 ? nL : nR;
   const int r1_bpad = r1 == 1 ? P.wRpad : P.wLpad;
   const void* r1_brow = r1 == 1 ? sR : sL;
-  const char* Mw = r1 && P.pass_store == 2 ? ws.alloc(r1_rows * eb) : (const char*)data;
+  // the rows' format for the rank-one kernels (BF16x2 rows are split, E4M3
+  // rows dequantised with their tile scales)
+  const int r1_store = P.dtype == TTNN_BF16X2 ? kStoreSplit
+                       : P.dtype == TTNN_E4M3 ? kStoreFp8
+                                              : P.pass_store;
+  const bool r1_copy = r1_store == 2 || r1_store == kStoreSplit || r1_store == kStoreFp8;
+  const char* Mw = r1 && r1_copy ? ws.alloc(r1_rows * eb) : (const char*)data;
   const char* bw = r1 && P.side_store == 2 ? ws.alloc((int64_t)r1_bpad * eb) : (const char*)r1_brow;
   if (y_from_gemv) C.yom = r1 == 1 ? D2 + (int64_t)P.rXR * eb : D1 + (int64_t)P.rXL * eb;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
@@ -1138,17 +1149,19 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     const int gcols = r1 == 1 ? P.wL : P.wR, gpad = r1 == 1 ? P.wLpad : P.wRpad;
     void* Dout = r1 == 1 ? (void*)D2 : (void*)D1;
     int64_t need = 0;
-    TTNN_TRY(launch_side_gemv(gs, nullptr, 0, false, nullptr, P.pass_store, r1_rows, gcols, gpad,
-                              nullptr, P.walk_f64, nullptr, 0, st, true, &need));
+    TTNN_TRY(launch_side_gemv(gs, nullptr, 0, false, nullptr, r1_store, nullptr, r1_rows, gcols,
+                              gpad, nullptr, P.walk_f64, nullptr, 0, st, true, &need));
     char* part = ws.alloc(need);
     if (!dry) {
       ++P.n_simt_pass;
-      const int pstore = P.pass_store, sstore = P.side_store, wf64 = P.walk_f64 ? 1 : 0;
+      const int pstore = r1_store, sstore = P.side_store, wf64 = P.walk_f64 ? 1 : 0;
       auto go = [=](cudaStream_t s) -> ttnn_status {
-        if (Mw != (const char*)data) TTNN_TRY(launch_to_walk(data, pstore, (void*)Mw, wf64, r1_rows, s));
-        if (bw != (const char*)r1_brow) TTNN_TRY(launch_to_walk(r1_brow, sstore, (void*)bw, wf64, r1_bpad, s));
-        return launch_side_gemv(gs, gsrc, gld, gcut, data, pstore, r1_rows, gcols, gpad, Dout, wf64,
-                                part, need, s, false, nullptr);
+        if (Mw != (const char*)data)
+          TTNN_TRY(launch_to_walk(data, pstore, tile_scale, (void*)Mw, wf64, r1_rows, s));
+        if (bw != (const char*)r1_brow)
+          TTNN_TRY(launch_to_walk(r1_brow, sstore, nullptr, (void*)bw, wf64, r1_bpad, s));
+        return launch_side_gemv(gs, gsrc, gld, gcut, data, pstore, tile_scale, r1_rows, gcols,
+                                gpad, Dout, wf64, part, need, s, false, nullptr);
       };
       if (batch) batch->passes.push_back(go);
       else TTNN_TRY(go(st));

@@ -176,3 +176,45 @@ def test_narrow_formats_reject_unsupported_shapes():
         assert not np.any(run.state_host())
     finally:
         run.close()
+
+
+@pytest.mark.parametrize("variant", [api.VARIANT_TTNN, api.VARIANT_STTNN])
+@pytest.mark.parametrize("fixed", ["right", "left"])
+def test_rank_one_boxes_narrow_formats(fixed, variant):
+    # boxes fixing every mode of one pass side take the rank-one path in the
+    # BF16x2 (split rows) and E4M3 (dequantised rows) formats as well
+    tr, dims, r, p = CASES["bin4_80x2560"]      # left modes {0, 1}, right {2, 3}
+    n = len(tr[0])
+    t = _otree(tr, dims, r, p)
+    rng = np.random.default_rng(9)
+    fix = [2, 3] if fixed == "right" else [0, 1]
+    off = [int(rng.integers(0, d)) if mu in fix else 1 for mu, d in enumerate(dims)]
+    ext = [1 if mu in fix else dims[mu] - 1 for mu in range(4)]
+    B = rng.standard_normal(ext).astype(np.float32).astype(np.float64)
+    nlb = ext[0] * ext[1]
+    # BF16x2
+    run = Run(tr, dims, [r] * n, [p] * n, 41, dtype=api.BF16X2, variant=variant)
+    try:
+        api.ttnn_update_dense(run.state, torch.from_numpy(B.astype(np.float32)).cuda(), off, ext,
+                              lam=0.5)
+        hi, lo = Q.split_bf16x2(B)
+        drm = O.Drm(t, 41, "bf16", "sttnn" if variant else "ttnn")
+        want = _sketch(variant, 0.5 * W.embed_box(dims, off, ext, hi + lo), t, drm)
+        assert _worst(run, want) <= 1e-5
+    finally:
+        run.close()
+    # E4M3, quantised over the box's own pass matrix
+    run = Run(tr, dims, [r] * n, [p] * n, 42, dtype=api.E4M3, variant=variant)
+    try:
+        src = torch.from_numpy(B.astype(np.float32)).cuda()
+        dst = torch.empty(B.size, dtype=torch.uint8, device="cuda")
+        ntile = -(-nlb // 128) * -(-(B.size // nlb) // 128)
+        sc = torch.empty(ntile, dtype=torch.float32, device="cuda")
+        api.ttnn_fp8_quantize(run.plan, src, dst, sc, extent=ext)
+        api.ttnn_update_dense(run.state, dst, off, ext, tile_scale=sc)
+        q, s = Q.fp8_tile_quantize(B.reshape(nlb, -1))
+        D = W.embed_box(dims, off, ext, Q.fp8_dequantize_bf16(q, s).reshape(ext))
+        drm = O.Drm(t, 42, "e4m3", "sttnn" if variant else "ttnn")
+        assert _worst(run, _sketch(variant, D, t, drm)) <= 1e-5
+    finally:
+        run.close()
