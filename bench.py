@@ -525,7 +525,7 @@ def cpu_oracle_sample(max_seconds=25.0):
     from oracle.tree import Tree
     tr = W.balanced_binary(D)
     n = len(tr[0])
-    slab = 16
+    slab = min(16, NMODE)
     ext = [slab] + [NMODE] * (D - 1)
     full = 1.0 + np.arange(NMODE) / (NMODE - 1)
     x0 = full[:slab]
@@ -548,7 +548,7 @@ def cpu_oracle_sample(max_seconds=25.0):
     nbytes = T.size * 4
     return {"value": nbytes / sec / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"{slab}x64^4 slab of the 64^5 tensor (FP32 values, {T.size} entries), TTNN "
+            "sample": f"{slab}x{NMODE}^4 slab of the {NMODE}^5 tensor (FP32 values, {T.size} entries), TTNN "
                       f"sketch + recovery in FP64 numpy, mean of {reps} run(s), {sec:.2f} s each"}
 
 
@@ -585,8 +585,9 @@ def main():
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": 0,
                           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "order-5 64^5 inv-sum, binary tree, r=20 l=10 "
-                                                 "(bounded 16x64^4 slab per step on host cores)"},
+                          "config": {"workload": f"order-5 {NMODE}^5 inv-sum, binary tree, r=20 "
+                                                 f"l=10 (bounded {min(16, NMODE)}x{NMODE}^4 slab "
+                                                 "per step on host cores)"},
                           "cpu_baseline": cb,
                           "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
