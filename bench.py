@@ -12,7 +12,7 @@ eps-pseudo-inverse, core assembly).  The headline `value` is the BF16 form's
 tensor bytes streamed per second; the FP32 plain form and STTNN (BF16) are
 measured the same way and reported beside it.
 
---impl reference times the FP64 CPU oracle (the reference arm for this build)
+--impl reference times the FP64 CPU oracle (the reference arm)
 on a bounded sample of the same workload on the host cores.
 """
 import argparse

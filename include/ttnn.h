@@ -69,7 +69,7 @@ typedef enum {
   TTNN_ENUMERIC = 4,     /* non-finite values met (e.g. NaN in an update) */
   TTNN_ETIMEOUT = 5,     /* a bounded device wait ran out */
   TTNN_EBUSY = 6,        /* resource in use (serving: no free slot) */
-  TTNN_EUNSUPPORTED = 7  /* valid request this build does not implement */
+  TTNN_EUNSUPPORTED = 7  /* valid request this library does not implement */
 } ttnn_status;
 
 /* Number formats of the tensor and of the pass-side DRM blocks. */
@@ -294,7 +294,7 @@ ttnn_status ttnn_round(ttnn_plan_t plan, const double* const* cores_in, const in
 ttnn_status ttnn_fp8_quantize(ttnn_plan_t plan, const float* src, const int64_t* extent,
                               uint8_t* dst, float* scales, void* stream);
 
-/* Profiling (no counterpart in the paper; this build's instrumentation):
+/* Profiling (no counterpart in the paper; this library's instrumentation):
  * with enable != 0 every later update / recovery on this plan records CUDA
  * events around its phases on the stream it runs on.  ttnn_profile_read
  * synchronises those events and returns the summed milliseconds and the

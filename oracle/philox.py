@@ -18,7 +18,7 @@ here from published methods only:
   only (no fused multiply-add), so any IEEE machine evaluating the same
   operation sequence gets the same bits.
 
-Counter layout (this build's own): element (i, j) of a factor of kind K with
+Counter layout (this library's own): element (i, j) of a factor of kind K with
 identifier ID takes counter (i, j >> 1, (K << 24) | ID, 0) and key
 (seed mod 2^32, seed >> 32); even j takes z0, odd j takes z1.  An element's
 value therefore does not depend on the matrix width, so a DRM with r columns

@@ -2,7 +2,7 @@
 formats.  ORACLE: test infrastructure only.
 
 The paper computes in binary64 throughout (MATLAB, Sec. 8).  The precision
-forms of this build store the tensor and the tensor-core side of the DRMs in a
+forms of this library store the tensor and the tensor-core side of the DRMs in a
 narrower format; the DRM *is* the rounded matrix, so the oracle rounds the same
 way and then computes exactly.  Definition used (IEEE-754 round to nearest,
 ties to even, at p significand bits, with gradual underflow at exponent emin):
@@ -13,7 +13,7 @@ ties to even, at p significand bits, with gradual underflow at exponent emin):
 fp32: p = 24, emin = -126, overflow -> inf.
 bf16: p = 8,  emin = -126, overflow -> inf.
 e4m3: p = 4,  emin = -6,   largest finite 448, overflow saturates to +-448
-      (OCP FP8 E4M3 has no infinity; saturation is this build's reading).
+      (OCP FP8 E4M3 has no infinity; saturation is this library's reading).
 """
 import numpy as np
 

@@ -1,7 +1,7 @@
 """TTNN: DRMs, sketch phase, recovery phase, reconstruction, projector form.
 ORACLE: test infrastructure only.
 
-Layout convention of this build (the paper's matricization, Sec. 3, is
+Layout convention of this library (the paper's matricization, Sec. 3, is
 column-major; every sketch below is defined by index sums, so the convention
 only fixes how indices are flattened): tensors are row-major (last mode
 fastest); the unfolding T^(t) has rows indexed by t's modes and columns by the
