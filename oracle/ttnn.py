@@ -58,6 +58,15 @@ def contract_axis(A, axis, M):
 # ---------------------------------------------------------------------------
 # DRMs
 # ---------------------------------------------------------------------------
+def pass_block(factors, fmt):
+    """A Khatri-Rao block that multiplies the dense tensor on the tensor cores
+    (Sec. 7 Khatri-Rao DRMs, stored in the plan's format): the exact binary64
+    product of the (already rounded) per-mode factors, rounded once to fmt.
+    Each entry is within fmt's unit roundoff (relative, normal range) of the
+    exact product; for fmt = "f64" it is the exact product."""
+    return quant.round_to(kr(factors), fmt)
+
+
 class Drm:
     """Per-mode factors and the per-node DRMs of one plan (Sec. 7)."""
 
@@ -85,15 +94,15 @@ class Drm:
         self.Rmodes = list(range(tree.node(ch[a]).lo, tree.node(ch[-1]).hi))
         # "round": sketches of a TTN input (Sec. 7) never multiply a dense A
         # on the tensor cores, so no KR block is rounded a second time
-        qs = (lambda a: a) if variant == "round" else q
-        self.BRX = qs(kr([self.X[mu] for mu in self.Rmodes]))
-        self.BLX = qs(kr([self.X[mu] for mu in self.Lmodes]))
+        blk = (lambda f: kr(f)) if variant == "round" else (lambda f: pass_block(f, fmt))
+        self.BRX = blk([self.X[mu] for mu in self.Rmodes])
+        self.BLX = blk([self.X[mu] for mu in self.Lmodes])
         ygrp = self.Rch if yside == "R" else self.Lch
         self.ychild = ygrp[0] if len(ygrp) == 1 else None
         self.Yside = None
         if self.ychild is not None and not tree.node(self.ychild).identity:
             c = tree.node(self.ychild)
-            self.Yside = qs(kr([self.Y[mu] for mu in range(c.lo, c.hi)]))
+            self.Yside = blk([self.Y[mu] for mu in range(c.lo, c.hi)])
 
     def in_left(self, v):
         return self.tree.node(v).lo < self.Rmodes[0]

@@ -157,15 +157,3 @@ def test_ttn_input_sketch_equals_dense_sketch(tr, dims):
     for v in t.sketched():
         assert _rel(a[0][v], b[0][v]) < 1e-12 and _rel(a[1][v], b[1][v]) < 1e-12
     assert _rel(a[2], b[2]) < 1e-12
-
-
-def test_pass_side_blocks_are_rounded_kr():
-    tr = W.balanced_binary(4)
-    dims = [6, 5, 6, 5]
-    t = Tree(tr[0], tr[1], dims, [3] * 7, [2] * 7, tr[2])
-    d64, d16 = O.Drm(t, 3, "f64"), O.Drm(t, 3, "bf16")
-    for mu in range(4):
-        assert np.array_equal(d16.X[mu], round_to(d64.X[mu], "bf16"))
-    exact = O.kr([d16.X[mu] for mu in d16.Rmodes])
-    assert np.array_equal(d16.BRX, round_to(exact, "bf16"))
-    assert np.max(np.abs(d16.BRX - exact) / np.abs(exact)) <= 2.0 ** -8
