@@ -215,20 +215,36 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     tr = W.balanced_binary(D)
     n = len(tr[0])
     dims, (off, ext) = _geometry(ws, rank)
+    # the passes leave a few SMs free for the recovery that overlaps them
     plan = api.ttnn_plan_create(tr, dims, [RANK] * n, [OVERSAMPLE] * n, SEED, variant=variant,
-                                sketch_dtype=dtype)
+                                sketch_dtype=dtype, flags=api.FLAG_RESERVE_SMS)
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    upd_done = torch.cuda.Event()
+    rec_done = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in rec_done:
+        e.record(main)
 
-    def step(sync=False):
-        api.ttnn_state_zero(state)
-        api.ttnn_update_dense(state, data, off, ext, tile_scale=scale)
+    def step(k=0, sync=False):
+        """One whole-path step on state k % 2.  Pipelined (sync=False): the
+        update runs on the main stream, the recovery of its state on a side
+        stream, overlapping the next step's update (on the other state)."""
+        st = states[k % 2]
+        main.wait_event(rec_done[k % 2])           # the recovery that last read this state
+        api.ttnn_state_zero(st)
+        api.ttnn_update_dense(st, data, off, ext, tile_scale=scale)
         if ws > 1:
-            shard.allreduce_state_(plan, state)    # the one exchange: sum of sketches
+            shard.allreduce_state_(plan, st)       # the one exchange: sum of sketches
         if sync:
-            api.ttnn_recover(state, cores)          # waits, reads the kept ranks back
-        else:
-            api.ttnn_recover_async(state, cores)    # the next step is recorded meanwhile
+            api.ttnn_recover(st, cores)            # waits, reads the kept ranks back
+            return
+        upd_done.record(main)
+        side.wait_event(upd_done)
+        api.ttnn_recover_async(st, cores, stream=side)
+        rec_done[k % 2].record(side)
 
-    state = api.ttnn_state_create(plan)
+    states = [api.ttnn_state_create(plan), api.ttnn_state_create(plan)]
+    state = states[0]
     scale, quant_ms = None, None
     if quantize:
         nl = NMODE ** ((D + 1) // 2)        # the slab's pass-matrix rows (mode 0 is in L)
@@ -248,8 +264,8 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     cores = torch.zeros(ce, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     log("plan and state ready")
-    for _ in range(warmup):
-        step()
+    for k in range(warmup):
+        step(k)
     torch.cuda.synchronize()
     log("warm-up done")
     api.ttnn_profile(plan, True)
@@ -260,8 +276,10 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        step()
+    for k in range(steps):
+        step(k)
+    for e in rec_done:
+        stream.wait_event(e)                       # the last recoveries are inside the region
     e1.record(stream)
     torch.cuda.synchronize()
     api.ttnn_plan_sync(plan)
@@ -278,7 +296,8 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     api.ttnn_profile(plan, False)
     prof = [api.ttnn_profile_read(plan, ph) for ph in range(3)]
     err = _ttn_sample_error(api, plan, tr, cores, ws, rank) if NMODE == 64 else None
-    api.ttnn_state_destroy(state)
+    for st in states:
+        api.ttnn_state_destroy(st)
     api.ttnn_plan_destroy(plan)
     lat.sort()
     return {"ms_per_step": ms, "launches": launches, "tc_passes": passes[0], "simt_passes": passes[1],
@@ -416,6 +435,90 @@ def run_streaming(api, W, torch, n_updates=4096, n_lat=256):
             "launches_per_update": launches / n_updates,
             "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
             "recover_ms": rec_ms}
+
+
+def _ttn_inner(parent, ch, A, B):
+    """Frobenius inner product of two TTNs on one tree (cores: root
+    (R_c..), transfer (R_v, R_c..), leaf (R_v, n..)): Gram matrices of the
+    two networks' node bases, leaves first, then the root's scalar."""
+    order, stack = [], [parent.index(-1)]
+    while stack:
+        v = stack.pop()
+        order.append(v)
+        stack.extend(ch[v])
+    M = {}
+    for v in reversed(order):
+        a, b = np.asarray(A[v]), np.asarray(B[v])
+        if not ch[v]:
+            M[v] = a.reshape(a.shape[0], -1) @ b.reshape(b.shape[0], -1).T
+            continue
+        head = 0 if parent[v] < 0 else 1
+        x = b
+        for k, c in enumerate(ch[v]):          # B's child axes into A's rank spaces
+            x = np.moveaxis(np.tensordot(M[c], x, axes=([1], [head + k])), 0, head + k)
+        if head:
+            M[v] = np.tensordot(a, x, axes=(list(range(1, a.ndim)), list(range(1, a.ndim))))
+        else:
+            M[v] = np.array(np.sum(a * x))
+    return float(M[order[0]])
+
+
+def run_rounding(api, W, torch, steps=5, warmup=3):
+    """TTN rounding (Sec. 7, sketches of a tensor already in TTN format):
+    order 8, modes 64, balanced binary tree, every edge of rank 200 (a
+    dominant rank-30 network, norm 100, in direct sum with a rank-170 noise
+    network, norm 1), recompressed to ranks 30 with p = 15.  One step =
+    ttnn_update_ttn of the whole network into a zeroed state + recovery,
+    binary64 cores resident on the device; BF16 and FP32 plans (binary32
+    walk in both; the BF16 plan's DRM factors are bfloat16 values)."""
+    d, n, rdom, rnoise, r, p = 8, 64, 30, 170, 30, 15
+    tr = W.balanced_binary(d)
+    nn = len(tr[0])
+    dims = [n] * d
+    cores = W.rounding_input(tr, dims, rdom, rnoise, 1005)
+    dev = [torch.from_numpy(np.ascontiguousarray(cores[v])).cuda() for v in range(nn)]
+    in_bytes = sum(c.numel() * 8 for c in dev)
+    walk_bytes = 2 * sum(c.numel() for c in dev) * 4      # two sweeps over binary32 copies
+    ch, _ = W.children_of(tr[0], tr[1])
+    tt = _ttn_inner(tr[0], ch, cores, cores)
+    out = {"workload": f"TTN order {d}, modes {n}, balanced binary tree, edge ranks {rdom + rnoise} "
+                       f"({rdom} dominant x100 + {rnoise} noise) -> ranks {r}, p = {p}",
+           "input_bytes": in_bytes, "walk_bytes": walk_bytes}
+    for name, dt in (("bf16", api.BF16), ("fp32", api.F32)):
+        plan = api.ttnn_plan_create(tr, dims, [r] * nn, [p] * nn, SEED + 5, sketch_dtype=dt,
+                                    flags=api.FLAG_STRUCTURED_ONLY)
+        st = api.ttnn_state_create(plan)
+        ce = api.ttnn_plan_sizes(plan)[2]
+        outc = torch.zeros(ce, dtype=torch.float64, device="cuda")
+
+        def step():
+            api.ttnn_state_zero(st)
+            api.ttnn_update_ttn(st, dev, [rdom + rnoise] * nn)
+            api.ttnn_recover_async(st, outc)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        api.ttnn_plan_sync(plan)
+        ms = e0.elapsed_time(e1) / steps
+        host = outc.cpu().numpy()
+        nodes = [api.ttnn_plan_node(plan, v) for v in range(nn)]
+        got = {nd["user_index"]: host[nd["core_offset"]:nd["core_offset"] + nd["core_elems"]]
+               .reshape(nd["core_shape"]) for nd in nodes}
+        err = float(np.sqrt(max(tt - 2 * _ttn_inner(tr[0], ch, cores, got) +
+                                _ttn_inner(tr[0], ch, got, got), 0.0) / tt))
+        out[name] = {"ms_per_rounding": ms, "input_gbs": in_bytes / (ms * 1e-3) / 1e9,
+                     "walk_gbs": walk_bytes / (ms * 1e-3) / 1e9, "rel_error": err}
+        api.ttnn_state_destroy(st)
+        api.ttnn_plan_destroy(plan)
+    out["noise_level"] = 0.01
+    return out
 
 
 def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=3.0):
@@ -692,6 +795,8 @@ def main():
         out["streaming"] = run_streaming(api, W, torch)
         log("serving leg")
         out["serving"] = run_serving(api, W, torch)
+        log("rounding leg")
+        out["rounding"] = run_rounding(api, W, torch)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_sample()
     if rank == 0:

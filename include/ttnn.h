@@ -18,8 +18,13 @@
  *   TTNN_ECUDA the state content is unspecified.  ttnn_last_error() returns a
  *   one-line message for the calling thread's last failure.
  * - Calls on one plan (and the states made from it) are serialised by the
- *   caller: they share the plan's device workspace.  Different plans may run
- *   concurrently on different streams.
+ *   caller, with one exception: the plan keeps one workspace for updates and
+ *   another for recoveries, so a recovery (ttnn_recover / _async) of one state
+ *   may run on another stream while an update of another state of the same
+ *   plan runs (the caller orders the two with events; updates among
+ *   themselves, and recoveries among themselves, stay on one stream or are
+ *   otherwise serialised).  Different plans may run concurrently on
+ *   different streams.
  * - Work is enqueued on the given stream; a call returns once its work is
  *   enqueued unless stated otherwise.
  *
@@ -107,6 +112,18 @@ typedef struct {
 #define TTNN_FLAG_CLUSTER_REDUCE 4u /* tensor-core pass: sum the column-chunk partials of D1
                                        across a thread-block cluster (distributed shared
                                        memory) instead of by the last CTA of each row block */
+#define TTNN_FLAG_DUMP_PROGRAM 16u  /* debugging: run every tree-walk / assembly op as its own
+                                       launch, synchronise, and print its time, level, kind,
+                                       shape and blocks to stderr */
+#define TTNN_FLAG_RESERVE_SMS 64u   /* the tensor-core first-level passes leave max(8, sketched
+                                       nodes) SMs (at most a quarter) free, so that a recovery
+                                       of another state issued on another stream runs beside
+                                       the next update's pass instead of after it */
+#define TTNN_FLAG_WAIT_TEST 32u     /* testing the bounded-wait error path: the pipeline waits
+                                       of the tensor-core passes give up at once, so a dense
+                                       update on this plan is abandoned on the device and the
+                                       next ttnn_recover / ttnn_plan_sync returns TTNN_ETIMEOUT
+                                       (the plan and its CUDA context stay usable) */
 
 typedef struct ttnn_plan_s* ttnn_plan_t;
 typedef struct ttnn_state_s* ttnn_state_t;
@@ -135,6 +152,15 @@ const char* ttnn_status_string(ttnn_status s);
  * to n bytes) into buf (host).  Returns TTNN_OK. */
 ttnn_status ttnn_last_error(char* buf, size_t n);
 
+/* ttnn_debug_fail_alloc -- allocation-failure injection for tests (the paper
+ * has no counterpart).  nth >= 1: the nth device allocation the library makes
+ * from now on (in any thread) fails as if cudaMalloc had run out of memory;
+ * nth = 0 disarms.  The failing call returns TTNN_ENOMEM and leaves every
+ * existing plan and state as it was (a plan creation frees what it had
+ * allocated; a workspace that would have grown keeps its old block).
+ * EINVAL: nth < 0. */
+ttnn_status ttnn_debug_fail_alloc(int32_t nth);
+
 /* ttnn_philox_gaussian -- the DRM generator [Sec. 7 per-mode factors; the
  * paper draws N(0,1) entries].  Writes rows x cols binary64 N(0,1) values to
  * dst (device, row-major): element (i, j) is Box-Muller output (j & 1) of
@@ -161,6 +187,13 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
                              const int32_t* ranks, const int32_t* oversample, uint64_t seed,
                              const ttnn_opts* opts, void* stream, ttnn_plan_t* out);
 void ttnn_plan_destroy(ttnn_plan_t plan);
+
+/* ttnn_plan_device_bytes -- the plan's device footprint (no counterpart in
+ * the paper): *total = bytes of device memory the plan holds (DRM factors,
+ * cached pass blocks, workspace, recovery buffers; states are separate),
+ * *workspace = its workspace block, which dense / TTN-format updates grow on
+ * demand.  Either pointer may be NULL.  EINVAL: null plan. */
+ttnn_status ttnn_plan_device_bytes(ttnn_plan_t P, int64_t* total, int64_t* workspace);
 
 /* Sizes: state elements (binary64 for TTNN_F64 plans, binary32 otherwise),
  * bytes per state element, total binary64 elements of all cores, number of
@@ -209,13 +242,18 @@ ttnn_status ttnn_update_dense(ttnn_state_t state, const void* data, const int64_
  * not let cudaMalloc / cudaFree synchronise the device mid-stream.  The paper
  * has no counterpart: this is an interface of this library only.
  * Its scratch is one fixed block of static device memory of 32 MiB per device
- * (not the plan's workspace); the call allocates no device memory.
+ * (not the plan's workspace); the call allocates no device memory.  The
+ * block is part of the library's device module: once that module is loaded on
+ * a device (at the first call here, or at context creation under
+ * CUDA_MODULE_LOADING=EAGER) the 32 MiB stay resident there until the process
+ * exits, whether or not this entry point is ever called.
  * EINVAL (before any work is enqueued) if the update needs more scratch than
  * that; otherwise as ttnn_update_dense.  The block's address is looked up on
- * the first call made with a device current: make that call before any stream
- * capture begins.  Calls that overlap in time (any plan, any stream, any host
- * thread of the process) share the block and race: serialise them.  No
- * profiling intervals are recorded. */
+ * the first call made with a device current, and again when that device's
+ * current context has changed (e.g. after cudaDeviceReset): make the first
+ * call before any stream capture begins.  Calls that overlap in time (any
+ * plan, any stream, any host thread of the process) share the block and race:
+ * serialise them.  No profiling intervals are recorded. */
 ttnn_status ttnn_update_dense_static(ttnn_state_t state, const void* data, const int64_t* offset,
                                      const int64_t* extent, const float* tile_scale,
                                      double lambda, void* stream);
@@ -326,7 +364,9 @@ ttnn_status ttnn_kernel_launches(int64_t* count);
 typedef struct ttnn_server_s* ttnn_server_t;
 
 typedef struct {
-  int64_t hbm_budget_bytes;  /* device memory all open streams may hold (plans + states) */
+  int64_t hbm_budget_bytes;  /* device memory all open streams may hold (plans + states);
+                                the library's 32 MiB static scratch block (resident once
+                                its module is loaded) is counted against it: must exceed it */
   int32_t max_batch;         /* requests per batch; <= 0: 64 */
   int32_t queue_capacity;    /* pending requests; <= 0: 65536 */
   int32_t workers;           /* worker threads, each with its own CUDA stream; <= 0: 4 */

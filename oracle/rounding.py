@@ -115,3 +115,54 @@ def sketch_ttn_input(cores_in, tree, drm):
     root = tree.node(tree.root)
     Pr = _psi(C[tree.root], None, [uy(c) for c in root.children])
     return Om, Ps, Pr
+
+
+# ---------------------------------------------------------------------------
+# TTN-format inner products and entries (tensors too large to form densely)
+# ---------------------------------------------------------------------------
+def ttn_inner(tree, A, B):
+    """<T_A, T_B> of two TTNs on the same tree (cores in the axis order
+    above; edge ranks may differ between A and B), by contracting leaves
+    upward: M_t[a, a'] = sum A_t[a, ..] B_t[a', ..] prod_c M_c[b_c, b'_c]
+    (leaf: A_t B_t^T over its modes), and at the root the scalar with no
+    parent axis.  Definition: the Frobenius inner product of the two dense
+    tensors (Def. "Tree tensor network format")."""
+    M = {}
+    for v in reversed(tree.lex):
+        nd = tree.node(v)
+        a = np.asarray(A[v], dtype=np.float64)
+        b = np.asarray(B[v], dtype=np.float64)
+        if nd.is_leaf:
+            M[v] = a.reshape(a.shape[0], -1) @ b.reshape(b.shape[0], -1).T
+            continue
+        m = len(nd.children)
+        head = "" if v == tree.root else "a"
+        headb = "" if v == tree.root else "z"
+        bl, br = _B[:m], _O[:m]
+        ins = [head + bl, headb + br] + [bl[k] + br[k] for k in range(m)]
+        ops = [a, b] + [M[c] for c in nd.children]
+        out = head + headb
+        M[v] = np.einsum(",".join(ins) + "->" + out, *ops, optimize=True)
+    return float(M[tree.root])
+
+
+def ttn_entries(tree, cores, idx):
+    """Entries of the TTN at the multi-indices idx (k x d integer array):
+    each leaf core read at the leaf's modes, then each transfer tensor
+    contracted with its children's vectors, per sample."""
+    idx = np.asarray(idx)
+    dims = tree.dims
+
+    def val(v):
+        nd = tree.node(v)
+        C = np.asarray(cores[v], dtype=np.float64)
+        if nd.is_leaf:
+            flat = np.ravel_multi_index(tuple(idx[:, nd.lo:nd.hi].T), dims[nd.lo:nd.hi])
+            return C.reshape(C.shape[0], -1)[:, flat].T            # (k, R_v)
+        vecs = [val(c) for c in nd.children]
+        m = len(vecs)
+        head = "" if v == tree.root else "a"
+        spec = head + _B[:m] + "," + ",".join("s" + _B[k] for k in range(m)) + "->s" + head
+        return np.einsum(spec, C, *vecs, optimize=True)
+
+    return val(tree.root)

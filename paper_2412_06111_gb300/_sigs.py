@@ -41,10 +41,12 @@ class TtnnServerReport(C.Structure):
 SIGS = {
     "ttnn_status_string": (C.c_char_p, [c_i32]),
     "ttnn_last_error": (c_i32, [C.c_char_p, c_sz]),
+    "ttnn_debug_fail_alloc": (c_i32, [c_i32]),
     "ttnn_philox_gaussian": (c_i32, [c_u64, c_i32, c_i32, c_i64, c_i64, c_i32, c_vp, c_vp]),
     "ttnn_plan_create": (c_i32, [C.POINTER(TtnnTree), c_i32, C.POINTER(c_i64), C.POINTER(c_i32),
                                  C.POINTER(c_i32), c_u64, C.POINTER(TtnnOpts), c_vp, C.POINTER(c_vp)]),
     "ttnn_plan_destroy": (None, [c_vp]),
+    "ttnn_plan_device_bytes": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
     "ttnn_plan_sizes": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i32), C.POINTER(c_i64),
                                 C.POINTER(c_i32)]),
     "ttnn_plan_node": (c_i32, [c_vp, c_i32, C.POINTER(TtnnNodeInfo)]),

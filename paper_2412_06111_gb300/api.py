@@ -13,6 +13,7 @@ from ._sigs import TtnnNodeInfo, TtnnOpts, TtnnTree
 F64, F32, BF16, E4M3, BF16X2 = 0, 1, 2, 3, 4
 VARIANT_TTNN, VARIANT_STTNN = 0, 1
 FLAG_NO_SIDE_CACHE, FLAG_SIMT_PASS, FLAG_CLUSTER_REDUCE, FLAG_STRUCTURED_ONLY = 1, 2, 4, 8
+FLAG_DUMP_PROGRAM, FLAG_WAIT_TEST, FLAG_RESERVE_SMS = 16, 32, 64
 KIND_X, KIND_Y, KIND_XT = 1, 2, 3
 
 
@@ -75,6 +76,12 @@ class Tree:
                           None if self.ident is None else C.cast(self.ident, C.POINTER(C.c_uint8)))
 
 
+def ttnn_debug_fail_alloc(nth):
+    """Testing: the nth device allocation of the library from now on fails
+    (TTNN_ENOMEM); 0 disarms."""
+    _check(_lib().ttnn_debug_fail_alloc(int(nth)))
+
+
 def ttnn_philox_gaussian(seed, kind, ident, rows, cols, round_dtype, dst, stream=None):
     _check(_lib().ttnn_philox_gaussian(seed, kind, ident, rows, cols, round_dtype, _ptr(dst),
                                        _stream(stream)))
@@ -96,6 +103,13 @@ def ttnn_plan_create(tree, dims, ranks, oversample, seed, variant=VARIANT_TTNN, 
 
 def ttnn_plan_destroy(plan):
     _lib().ttnn_plan_destroy(plan)
+
+
+def ttnn_plan_device_bytes(plan):
+    """(total device bytes held by the plan, its workspace bytes)."""
+    t, w = C.c_int64(), C.c_int64()
+    _check(_lib().ttnn_plan_device_bytes(plan, C.byref(t), C.byref(w)))
+    return t.value, w.value
 
 
 def ttnn_plan_sizes(plan):

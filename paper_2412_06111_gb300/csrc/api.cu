@@ -1,4 +1,5 @@
 // C ABI entry points (declared in include/ttnn.h).
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -22,9 +23,17 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return g_err; }
 
+// Allocation-failure injection for tests (ttnn_debug_fail_alloc): the
+// device allocation that brings this counter from 1 to 0 fails.
+static std::atomic<int> g_fail_alloc{0};
+
 static ttnn_status dev_alloc(void** p, int64_t bytes) {
   *p = nullptr;
   if (bytes <= 0) return TTNN_OK;
+  if (g_fail_alloc.load(std::memory_order_relaxed) > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+    set_error("cudaMalloc(%lld) failed: injected allocation failure", (long long)bytes);
+    return TTNN_ENOMEM;
+  }
   cudaError_t e = cudaMalloc(p, (size_t)bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -49,6 +58,7 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->sideL);
   cudaFree(P->yW);
   cudaFree(P->ws);
+  cudaFree(P->ws_rec);
   cudaFree(P->jobs_dev);
   cudaFree(P->kept_dev);
   cudaFree(P->err_dev);
@@ -57,16 +67,17 @@ static void free_plan(ttnn_plan_s* P) {
   delete P;
 }
 
-// Replaces the plan workspace by a larger one (cudaFree / cudaMalloc
-// synchronise the device, so no earlier work still uses the old block).
+// Replaces the plan workspace by a larger one.  The new block is allocated
+// first, so a failed allocation leaves the plan as it was (TTNN_ENOMEM, no
+// work launched); cudaFree synchronises the device, so no earlier work still
+// uses the old block when it is released.
 static ttnn_status grow_workspace(ttnn_plan_s& P, int64_t bytes) {
+  char* fresh = nullptr;
+  TTNN_TRY(dev_alloc((void**)&fresh, bytes));
   cudaFree(P.ws);
-  P.dev_bytes -= P.ws_bytes;
-  P.ws = nullptr;
-  P.ws_bytes = 0;
-  TTNN_TRY(dev_alloc((void**)&P.ws, bytes));
+  P.dev_bytes += bytes - P.ws_bytes;
+  P.ws = fresh;
   P.ws_bytes = bytes;
-  P.dev_bytes += bytes;
   return TTNN_OK;
 }
 
@@ -107,6 +118,12 @@ const char* ttnn_status_string(ttnn_status s) {
     case TTNN_EUNSUPPORTED: return "unsupported";
   }
   return "unknown status";
+}
+
+ttnn_status ttnn_debug_fail_alloc(int32_t nth) {
+  TTNN_CHECK_ARG(nth >= 0, "nth must be >= 0");
+  g_fail_alloc.store(nth);
+  return TTNN_OK;
 }
 
 ttnn_status ttnn_last_error(char* buf, size_t n) {
@@ -191,9 +208,10 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
       if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
     }
   }
-  // workspace: the larger of a whole-tensor update (cached DRM blocks), an
-  // update of a box as large as the tensor (blocks generated into the
-  // workspace: bounds every box update) and a recovery
+  // workspaces: updates -- the larger of a whole-tensor update (cached DRM
+  // blocks), an update of a box as large as the tensor (blocks generated into
+  // the workspace: bounds every box update) and a CP update; TTN-format
+  // updates grow it on demand -- and, apart, the recovery's
   int64_t need_u = 0, need_r = 0;
   if (dense) {
     if ((s = dense_update_need(P, fb, &need_u))) return fail(s);
@@ -203,9 +221,12 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
     if ((s = dense_update_need(P, bb, &need_b))) return fail(s);
     need_u = std::max(need_u, need_b);
   }
+  if (P.variant == TTNN_VARIANT_TTNN) need_u = std::max(need_u, cp_update_need(P));
   if ((s = run_recover(P, nullptr, nullptr, st, true, &need_r))) return fail(s);
-  P.ws_bytes = std::max(need_u, need_r) + 4096;
+  P.ws_bytes = need_u + 4096;
   if ((s = palloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
+  P.ws_rec_bytes = need_r + 4096;
+  if ((s = palloc((void**)&P.ws_rec, P.ws_rec_bytes)) != TTNN_OK) return fail(s);
   if ((s = palloc((void**)&P.jobs_dev, std::max(1, P.n_sketched) * (int64_t)sizeof(QrJob))) != TTNN_OK) return fail(s);
   if ((s = palloc((void**)&P.kept_dev, 2 * std::max(1, P.n_sketched) * (int64_t)sizeof(int))) != TTNN_OK) return fail(s);
   if ((s = palloc((void**)&P.err_dev, sizeof(int))) != TTNN_OK) return fail(s);
@@ -227,6 +248,13 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
 }
 
 void ttnn_plan_destroy(ttnn_plan_t plan) { free_plan(plan); }
+
+ttnn_status ttnn_plan_device_bytes(ttnn_plan_t P, int64_t* total, int64_t* workspace) {
+  TTNN_CHECK_ARG(P, "null plan");
+  if (total) *total = P->dev_bytes;
+  if (workspace) *workspace = P->ws_bytes;
+  return TTNN_OK;
+}
 
 ttnn_status ttnn_plan_sizes(ttnn_plan_t P, int64_t* state_elems, int32_t* state_elem_bytes,
                             int64_t* core_elems, int32_t* n_nodes) {

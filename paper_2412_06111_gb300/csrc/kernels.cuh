@@ -22,6 +22,13 @@ struct Contract {
   void* out = nullptr;
   double alpha = 1.0;
   int accumulate = 0;
+  // Khatri-Rao weight (nkr > 0, w == nullptr; binary32 walk ops only):
+  // W(i, b) = prod_f kr[f][d_f * wsI + b * wsB] where (d_0, .., d_{nkr-1})
+  // are the digits of i in the mixed radix krn (d_0 slowest): the columns of
+  // several per-mode factors multiplied entrywise, never materialised.
+  int nkr = 0;
+  int32_t krn[4] = {0, 0, 0, 0};
+  const void* kr[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // element type codes for the contraction

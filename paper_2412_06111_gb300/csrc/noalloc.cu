@@ -16,9 +16,14 @@
 //  - The scratch is one block per device and per process: calls that
 //    overlap in time (other host threads, or work still running on another
 //    stream) race on it and give wrong results.  Serialise them.
-//  - The block's address is looked up once per device, on the first call
-//    made with that device current; make that first call before any stream
-//    capture begins.
+//  - The block's address is looked up on the first call made with a device
+//    current, and again whenever that device's current CUDA context has
+//    changed since (e.g. after cudaDeviceReset); make the first call before
+//    any stream capture begins.
+//  - The block is device memory of the library's module: once the module is
+//    loaded on a device (at the first call here, or at context creation under
+//    CUDA_MODULE_LOADING=EAGER) the 32 MiB stay resident there until the
+//    process exits, whether or not this entry point is ever called.
 //  - Nothing in the scratch has to start at zero: every buffer an update
 //    uses is written in full before it is read.
 //  - Profiling intervals are not recorded by this call.
@@ -35,8 +40,36 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 static std::mutex g_static_mu;
 static void* g_static_addr[kMaxDevices] = {nullptr};
+static void* g_static_ctx[kMaxDevices] = {nullptr};
 
-// Device address of g_static_scratch in the current device's context.
+typedef int (*CtxGetCurrentFn)(void**);
+
+// The current CUDA context (driver API cuCtxGetCurrent, reached through the
+// runtime's entry-point query so that no driver library is linked).
+static ttnn_status current_context(void** ctx) {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !ptr) {
+      cudaGetLastError();
+      set_error("static scratch: cuCtxGetCurrent unavailable");
+      return TTNN_ECUDA;
+    }
+    fn = (CtxGetCurrentFn)ptr;
+  }
+  *ctx = nullptr;
+  if (fn(ctx) != 0) {
+    set_error("static scratch: cuCtxGetCurrent failed");
+    return TTNN_ECUDA;
+  }
+  return TTNN_OK;
+}
+
+// Device address of g_static_scratch in the current device's context, looked
+// up again when the context is not the one the cached address belongs to.
 static ttnn_status static_scratch(void** out) {
   int dev = 0;
   TTNN_TRY_CUDA(cudaGetDevice(&dev));
@@ -45,7 +78,9 @@ static ttnn_status static_scratch(void** out) {
     return TTNN_EUNSUPPORTED;
   }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  void* ctx = nullptr;
+  if (g_static_addr[dev]) TTNN_TRY(current_context(&ctx));
+  if (!g_static_addr[dev] || ctx != g_static_ctx[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p) {
@@ -54,11 +89,16 @@ static ttnn_status static_scratch(void** out) {
                 cudaGetErrorString(e));
       return TTNN_ECUDA;
     }
+    // the symbol lookup made the primary context current if none was
+    TTNN_TRY(current_context(&ctx));
     g_static_addr[dev] = p;
+    g_static_ctx[dev] = ctx;
   }
   *out = g_static_addr[dev];
   return TTNN_OK;
 }
+
+int64_t static_scratch_resident_bytes() { return kStaticScratchBytes; }
 
 }  // namespace ttnn
 
@@ -88,9 +128,9 @@ ttnn_status ttnn_update_dense_static(ttnn_state_t S, const void* data, const int
     return TTNN_EUNSUPPORTED;
   }
   const cudaStream_t st = (cudaStream_t)stream;
-  // size the scratch of this update by recording it without launching
+  // the scratch this update needs (recorded once per box shape, then cached)
   int64_t need = 0;
-  TTNN_TRY(run_dense_update(P, nullptr, nullptr, b, nullptr, 1.0, st, true, &need));
+  TTNN_TRY(dense_update_need(P, b, &need));
   TTNN_CHECK_ARG(need <= kStaticScratchBytes,
                  "this update needs %lld bytes of scratch; ttnn_update_dense_static has %lld "
                  "(use ttnn_update_dense or a smaller box)",

@@ -461,7 +461,7 @@ static bool cvt_geometry(int mode, const ttnn_plan_s& P, int64_t nL, int64_t nR,
   g->smem = (size_t)(1024 + stages * stage_bytes + bl);
   g->C = (int)((nR + tiles * kTileN - 1) / (tiles * kTileN));
   g->nb = (int)((nL + kTileM - 1) / kTileM);
-  const int sms = sm_count();
+  const int sms = pass_sms(P);
   g->G = std::max(1, std::min(sms / g->C, g->nb));
   if (sms < g->C) g->G = 1;
   g->grid = g->C * g->G;

@@ -43,6 +43,7 @@ struct Params {
   int* err;
   int* cnt;        // [nb][4] chunk arrivals per row block and epilogue warp (C > 1, no cluster), zero at launch
   int discard;     // partial rows are whole 128-byte lines: drop them from L2 once summed
+  uint64_t wait_ns;  // limit of each pipeline wait (drains of own copies keep the 2 s limit)
 };
 
 // --- thread-block cluster (distributed shared memory) helpers
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = b0 + u, ub = u & 1;
         const int row = b * kTileM;
         if (p.wLpad > 0) {
-          ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag);
+          ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag, p.wait_ns);
           if (!ok) break;
           const uint32_t blb = bl_base + ub * bl_bytes;
           mbar_expect_tx(smem_u32(&bar_blfull[ub]), bl_bytes);
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           bl_last[ub] = (u >> 1) & 1;
         }
         for (int t = 0; t < nt; ++t) {
-          ok = mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1, &abort_flag);
+          ok = mbar_wait(smem_u32(&bar_empty[stage]), ph ^ 1, &abort_flag, p.wait_ns);
           if (!ok) break;
           const uint32_t sb = base + stage * stage_bytes;
           const int col = (int)(col0 + t * kTileN);
@@ -223,14 +224,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int u = 0; u < nu && ok; ++u) {
         const int buf = u & 1;
-        if (u >= 2) ok = mbar_wait(smem_u32(&bar_d1empty[buf]), ((u >> 1) - 1) & 1, &abort_flag);
-        if (ok && p.wLpad > 0) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag);
+        if (u >= 2) ok = mbar_wait(smem_u32(&bar_d1empty[buf]), ((u >> 1) - 1) & 1, &abort_flag, p.wait_ns);
+        if (ok && p.wLpad > 0) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag, p.wait_ns);
         if (!ok) break;
         fence_after();
         const uint32_t blb = bl_base + buf * bl_bytes;
         const uint32_t d1 = tmem + d1_col + buf * p.wRpad;
         for (int t = 0; t < nt; ++t) {
-          ok = mbar_wait(smem_u32(&bar_full[stage]), ph, &abort_flag);
+          ok = mbar_wait(smem_u32(&bar_full[stage]), ph, &abort_flag, p.wait_ns);
           if (!ok) break;
           fence_after();
           const uint32_t sa = base + stage * stage_bytes;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int u = 0; u < nu && ok; ++u) {
       const int buf = u & 1;
-      ok = mbar_wait(smem_u32(&bar_d1full[buf]), (u >> 1) & 1, &abort_flag);
+      ok = mbar_wait(smem_u32(&bar_d1full[buf]), (u >> 1) & 1, &abort_flag, p.wait_ns);
       if (!ok) break;
       fence_after();
       const int64_t row = (int64_t)(b0 + u) * kTileM + r_in;
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float* dst = p.D2p + ((int64_t)g * p.C * cw + col) * p.wLpad;
         for (int k = 0; k < p.wLpad; ++k) dst[k] = 0.f;
       }
-    } else if (ok && mbar_wait(smem_u32(&bar_d2full), 0, &abort_flag)) {
+    } else if (ok && mbar_wait(smem_u32(&bar_d2full), 0, &abort_flag, p.wait_ns)) {
       fence_after();
       for (int t = 0; t < nt; ++t) {
         const int64_t col = col0 + t * kTileN + r_in;
@@ -525,6 +526,13 @@ int sm_count() {
   return n;
 }
 
+int pass_sms(const ttnn_plan_s& P) {
+  const int sms = sm_count();
+  if (!(P.flags & TTNN_FLAG_RESERVE_SMS)) return sms;
+  const int keep = std::min(std::max(8, P.n_sketched), sms / 4);
+  return sms - keep;
+}
+
 static int max_clusters(int C, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C * 64, 1, 1);
@@ -563,7 +571,7 @@ static bool geometry(const ttnn_plan_s& P, int64_t nL, int64_t nR, Geometry* g) 
   g->tiles = tiles;
   g->C = (int)((nR + tiles * kTileN - 1) / (tiles * kTileN));
   g->nb = (int)((nL + kTileM - 1) / kTileM);
-  const int sms = sm_count();
+  const int sms = pass_sms(P);
   // cluster path: C in {2, 4, 8}, D1 partial tiles fit beside >= 3 stages
   g->cluster = 0;
   const int64_t parts = 2 * (int64_t)kTileM * P.wRpad * 4;
@@ -652,6 +660,7 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
   prm.D2p = (float*)ws + g.d1p_elems;
 
   prm.err = P.err_dev;
+  prm.wait_ns = (P.flags & TTNN_FLAG_WAIT_TEST) ? 0 : tc::kTimeoutNs;
   prm.cnt = fold ? (int*)((char*)ws + (g.d1p_elems + g.d2p_elems) * 4 + 256 -
                           (((uintptr_t)ws + (g.d1p_elems + g.d2p_elems) * 4) & 255))
                  : nullptr;

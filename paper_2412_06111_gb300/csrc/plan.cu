@@ -441,8 +441,18 @@ static int find_ax(const View& v, int kind, int id) {
 // W(i, x) = W[i*wsI + x*wsX]; the axis stays.  The output is contiguous.
 static ttnn_status apply_scales(Ctx& C, const View& in, View* out);
 
+// A Khatri-Rao weight of up to four per-mode factors (walk type): W(i, b) =
+// prod_f f[f][d_f * wsI + b * wsX], d_f the digits of i over `rows` (first
+// factor slowest).  Only binary32 walks, sketch sizes <= 32.
+struct KrSpec {
+  int n = 0;
+  const char* f[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t rows[4] = {0, 0, 0, 0};
+};
+
 static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, int64_t wsI,
-                                 int64_t wsX, int shared, const Ax* nax, View* out) {
+                                 int64_t wsX, int shared, const Ax* nax, View* out,
+                                 const KrSpec* kr = nullptr) {
   const int L = (int)in.ax.size() - 1;
   // a broadcast axis that is contracted or shared (other than the column axis
   // in the shared == L form, which makes it real) is expanded first
@@ -453,9 +463,21 @@ static ttnn_status contract_view(Ctx& C, const View& in, int k, const void* W, i
     // the contracted axis carries pending scales or a broadcast: apply them
     View m;
     TTNN_TRY(apply_scales(C, in, &m));
-    return contract_view(C, m, k, W, wsI, wsX, shared, nax, out);
+    return contract_view(C, m, k, W, wsI, wsX, shared, nax, out, kr);
   }
   Contract c;
+  if (kr) {
+    if (shared >= 0 || C.et != ET_F32 || nax->size > 32 || kr->n < 1 || kr->n > 4) {
+      set_error("internal: Khatri-Rao weight outside its form");
+      return TTNN_EUNSUPPORTED;
+    }
+    c.nkr = kr->n;
+    for (int f = 0; f < kr->n; ++f) {
+      c.kr[f] = kr->f[f];
+      c.krn[f] = kr->rows[f];
+    }
+    W = nullptr;
+  }
   c.P = 1;
   for (int a = 0; a < k; ++a) c.P *= in.ax[a].size;
   c.isP = k > 0 ? vstride(in, k - 1) : 0;
@@ -687,6 +709,70 @@ static ttnn_status x_mode(Ctx& C, const View& in, int mode, View* out) {
   return contract_view(C, in, k, facX(C, mode), C.P.rmax, 1, L, nullptr, out);
 }
 
+// The Y chain of `node` over the modes [lo, hi) of `in` whose sketch axis is
+// already the view's first axis (a Khatri-Rao prefix contracted before, with
+// the same columns): each remaining mode, in turn the view's second axis, is
+// contracted against it.  The sketch axis is relabelled to `node`.
+static ttnn_status y_chain_rest(Ctx& C, const View& in, int node, int lo, int hi, View* out) {
+  View cur = in;
+  if (cur.ax.empty() || cur.ax[0].kind != AX_SK) {
+    set_error("internal: Khatri-Rao prefix layout");
+    return TTNN_EUNSUPPORTED;
+  }
+  const int old = cur.ax[0].id;
+  cur.ax[0].id = node;
+  for (auto& x : cur.sc)
+    if (x.kind == AX_SK && x.id == old) x.id = node;
+  for (int m = lo; m < hi; ++m) {
+    if (find_ax(cur, AX_MODE, m) != 1) {
+      set_error("internal: Khatri-Rao prefix layout");
+      return TTNN_EUNSUPPORTED;
+    }
+    View nx;
+    TTNN_TRY(contract_view(C, cur, 1, facY(C, m), C.P.smax, 1, 0, nullptr, &nx));
+    cur = nx;
+  }
+  *out = cur;
+  return TTNN_OK;
+}
+
+// Contraction of the leading modes [lo, hi) of `in` (its first axes, no
+// broadcasts or pending scales on them) with kr(Y_mu, mu in [lo, hi))[:, :s]
+// as one long reduction over their merged index; the new sketch axis (kind
+// AX_SK, id `node`, size s) replaces them.
+static ttnn_status kr_prefix(Ctx& C, const View& in, int node, int lo, int hi, int s, View* out) {
+  const int m = hi - lo;
+  View v = in;
+  int64_t n = 1;
+  KrSpec kr;
+  kr.n = m;
+  for (int k = 0; k < m; ++k) {
+    const Ax& a = in.ax[k];
+    if (a.kind != AX_MODE || a.id != lo + k || a.bc > 0) {
+      set_error("internal: Khatri-Rao prefix layout");
+      return TTNN_EUNSUPPORTED;
+    }
+    n *= a.size;
+    kr.f[k] = facY(C, lo + k);
+    kr.rows[k] = (int32_t)a.size;
+  }
+  for (const View::Scale& x : in.sc)
+    for (int k = 0; k < m; ++k)
+      if (x.kind == in.ax[k].kind && x.id == in.ax[k].id) {
+        set_error("internal: Khatri-Rao prefix with a pending scale");
+        return TTNN_EUNSUPPORTED;
+      }
+  // the prefix axes are contiguous (row-major): one merged axis
+  v.ax.erase(v.ax.begin(), v.ax.begin() + m);
+  v.ax.insert(v.ax.begin(), Ax{AX_MODE, lo, n, 0});
+  if (v.ax.size() < 2) {
+    set_error("internal: Khatri-Rao prefix without columns");
+    return TTNN_EUNSUPPORTED;
+  }
+  Ax nax{AX_SK, node, s, 0};
+  return contract_view(C, v, 0, nullptr, C.P.smax, 1, -1, &nax, out, &kr);
+}
+
 // STTNN: contraction of group s with E_s = Y_s XT_s (Y chain, then XT_s on
 // the new sketch axis sharing the column axis).
 static ttnn_status e_group(Ctx& C, const View& in, int s, View* out) {
@@ -831,11 +917,30 @@ static View truncate_j(const View& v, int64_t j) {
 static char* state_at(Ctx& C, void* acc, int64_t elem_off) { return (char*)acc + elem_off * C.eb; }
 
 // Node v with G_v = T^(v) X_v over the box (axes: v's modes, then columns).
-static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda) {
+// pre (optional): G_v with the modes of v's first child already contracted
+// with that child's Khatri-Rao Y (sketch axis first, same columns as Y_v's
+// leading factors): Omega_v and Psi_v start from it.
+static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda,
+                        const View* pre = nullptr) {
   ttnn_plan_s& P = C.P;
   const TNode& nd = P.nodes[v];
   if (nd.rsub == 0) return TTNN_OK;
-  if (nd.sketched()) {
+  if (nd.sketched() && pre) {
+    const TNode& c1 = P.nodes[nd.ch.front()];
+    const View pt = truncate_j(*pre, nd.r);
+    View om;
+    TTNN_TRY(y_chain_rest(C, pt, v, c1.hi, nd.hi, &om));
+    TTNN_TRY(scatter_into(C, om, state_at(C, acc, nd.om_off), {(int64_t)nd.r, 1}, lambda));
+    View cur = pt;
+    for (int k = (int)nd.ch.size() - 1; k >= 1; --k) {
+      const TNode& c = P.nodes[nd.ch[k]];
+      if (c.identity) continue;
+      View nx;
+      TTNN_TRY(y_chain(C, cur, c.user, c.lo, c.hi, c.s, &nx));
+      cur = nx;
+    }
+    TTNN_TRY(scatter_into(C, cur, state_at(C, acc, nd.ps_off), psi_strides(C, cur, nd, true), lambda));
+  } else if (nd.sketched()) {
     const View Gt = truncate_j(G, nd.r);
     View om;
     // Omega_t and Psi_t both start by contracting t's last mode with the same
@@ -1244,12 +1349,38 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
     return v;
   };
   const TNode& root = P.nodes[P.root];
+  // Khatri-Rao prefix (TTNN, binary32 walk, whole first-level products): with
+  // one left root child Lc whose first child c1 spans Lc's leading modes with
+  // s_c1 = s_Lc, the Y chains of Omega_Lc, of Psi_Lc's c1 axis and of the
+  // root's Psi (its L axis, when the root's Y is on the R side) all start by
+  // contracting c1's modes with the same columns of kr(Y_mu, mu in c1).  That
+  // contraction runs as one long reduction over c1's merged index on each of
+  // D1's two column groups (G_Lc and the root's H), instead of mode by mode
+  // through large intermediates.
+  const TNode* krL = nullptr;
+  if (P.variant == TTNN_VARIANT_TTNN && r1 == 0 && !P.walk_f64 && P.Lch.size() == 1) {
+    const TNode& Lc = P.nodes[P.Lch[0]];
+    if (Lc.sketched() && !Lc.leaf && Lc.user != P.ychild && Lc.r <= P.rXL && Lc.s <= 32) {
+      const TNode& c1 = P.nodes[Lc.ch.front()];
+      int64_t n1 = 1;
+      for (int m = c1.lo; m < c1.hi; ++m) n1 *= box.ext[m];
+      if (!c1.identity && c1.s == Lc.s && c1.lo == P.Llo && c1.hi - c1.lo <= 4 && n1 >= 512 &&
+          n1 < (int64_t(1) << 31))
+        krL = &Lc;
+    }
+  }
   // L side (both variants): G over L modes from D1's X part
   if (P.rXL > 0) {
     View GL{D1, mode_axes(P.Llo, P.Lhi), P.wRpad};
     GL.ax.push_back(Ax{AX_J, -1, P.rXL, 0});
     if (r1 == 1) GL = bview(P.Llo, P.Lhi, Ax{AX_J, -1, 1, 0}, P.rXL, bw);
-    for (size_t k = 0; k < P.Lch.size(); ++k) {
+    if (krL) {
+      const TNode& c1 = P.nodes[krL->ch.front()];
+      View pre;
+      TTNN_TRY(kr_prefix(C, truncate_j(GL, krL->r), c1.user, c1.lo, c1.hi, c1.s, &pre));
+      TTNN_TRY(walk(C, acc, krL->user, truncate_j(GL, krL->rsub), lambda, &pre));
+    }
+    for (size_t k = 0; k < P.Lch.size() && !krL; ++k) {
       const TNode& c = P.nodes[P.Lch[k]];
       if (c.rsub == 0) continue;
       View cur = truncate_j(GL, c.rsub);
@@ -1299,7 +1430,13 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
         H = bview(P.Llo, P.Lhi, Ax{AX_SK, P.ychild, 1, 0}, P.wYR, bw + (int64_t)P.rXL * eb);
       }
       View cur = H;
-      for (int k = (int)P.Lch.size() - 1; k >= 0; --k) {
+      if (krL) {
+        const TNode& c1 = P.nodes[krL->ch.front()];
+        View e;
+        TTNN_TRY(kr_prefix(C, H, krL->user, c1.lo, c1.hi, krL->s, &e));
+        TTNN_TRY(y_chain_rest(C, e, krL->user, c1.hi, krL->hi, &cur));
+      }
+      for (int k = (int)P.Lch.size() - 1; k >= 0 && !krL; --k) {
         const TNode& c = P.nodes[P.Lch[k]];
         if (c.identity) continue;
         View nx;
@@ -1385,7 +1522,7 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   }
   if (!dry) {
     if (batch) batch->walks.absorb(prog);
-    else TTNN_TRY(prog.run(st));
+    else TTNN_TRY(prog.run(st, P.flags & TTNN_FLAG_DUMP_PROGRAM));
   }
   P.last_walk_ops = (int)prog.size();
   P.last_walk_levels = prog.levels();
@@ -1629,7 +1766,7 @@ ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores
       }
     }
   }
-  if (!dry) TTNN_TRY(prog.run(st));
+  if (!dry) TTNN_TRY(prog.run(st, P.flags & TTNN_FLAG_DUMP_PROGRAM));
   if (peak) *peak = ws.peak;
   if (!ws.ok()) {
     set_error("internal: workspace overflow (%lld > %lld)", (long long)ws.peak, (long long)ws.cap);
@@ -1684,7 +1821,7 @@ ttnn_status plan_sync(ttnn_plan_s& P) {
 
 ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
                         int64_t* peak, bool async) {
-  Ws ws(P.ws, P.ws_bytes, dry);
+  Ws ws(P.ws_rec, P.ws_rec_bytes, dry);
   Program prog;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
   const int seb = P.walk_f64 ? 8 : 4;
@@ -1812,7 +1949,7 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
     set_error("internal: workspace overflow in recovery");
     return TTNN_ENOMEM;
   }
-  if (!dry) TTNN_TRY(prog.run(st));
+  if (!dry) TTNN_TRY(prog.run(st, P.flags & TTNN_FLAG_DUMP_PROGRAM));
   if (!dry) prof_push(P, 2, ev0, prof_event(P, st));
   if (dry) return TTNN_OK;
   // read-back of kept ranks, sweeps and the device error word into pinned

@@ -66,6 +66,10 @@ struct ttnn_plan_s {
   void* yW = nullptr;           // walk-type copy of the pass Y block (full box)
   char* ws = nullptr;
   int64_t ws_bytes = 0;
+  // the recovery's own scratch: a recovery may run on another stream while
+  // the next update of another state of the plan uses `ws`
+  char* ws_rec = nullptr;
+  int64_t ws_rec_bytes = 0;
   int64_t dev_bytes = 0;        // device memory the plan holds (all its allocations)
   // workspace bytes a dense update needs, by box extents (+ whole-tensor flag)
   std::map<std::vector<int64_t>, int64_t> ws_need_cache;
@@ -112,6 +116,11 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
 // workspace bytes through *peak when dry.
 // Workspace bytes a dense update of `box` needs (dry run, cached per shape).
 ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need);
+// Workspace bytes of a CP update (any rank: ranks are taken kProjQ at a time).
+int64_t cp_update_need(const ttnn_plan_s& P);
+// Bytes of the library's static scratch block (ttnn_update_dense_static),
+// resident on a device once the library's module is loaded there.
+int64_t static_scratch_resident_bytes();
 // A real (non-dry) update first checks its workspace need against the plan's
 // workspace and returns TTNN_ENOMEM, launching nothing, when it does not fit.
 // Work of several dense updates recorded for joint launches: the box side

@@ -4,7 +4,6 @@
 #include <type_traits>
 
 #include <cstdio>
-#include <cstdlib>
 
 #include "program.cuh"
 
@@ -313,6 +312,123 @@ __device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
   }
 }
 
+// Split-K register-tiled contraction for long reductions into few outputs per
+// column (e.g. the Khatri-Rao contraction of all leading modes of a first-level
+// product at once):  out[p,b,q,j] (+)= alpha * sum_i W(i, b) in[p,i,q,j],
+// b < NB <= 32, with W(i, b) = w[i*wsI + b*wsB] or the Khatri-Rao product of
+// the factors c.kr (nkr > 0).  Columns n = (p, q, j) are tiled kKgNT per
+// block, the reduction index in chunks of op.chunk (block = (tile, split));
+// each thread accumulates 8 (b) x 4 (n) outputs from shared-memory tiles of
+// kKgKT rows, the next rows prefetched into registers.  With nsplit > 1 the
+// block writes its partial sums [split][p][b][q][j], reduced in a fixed order
+// (OP_REDUCE), else the outputs.
+constexpr int kKgKT = 16, kKgNT = 256, kKgMB = 32;
+
+// W(i, b) of a split-K contraction; i < 2^31 (the recorder checks).
+__device__ __forceinline__ float kg_weight(const Contract& c, int64_t i, int b) {
+  if (c.nkr == 0) return ((const float*)c.w)[i * c.wsI + (int64_t)b * c.wsB];
+  float v = 1.f;
+  uint32_t rem = (uint32_t)i;
+#pragma unroll
+  for (int f = 3; f >= 0; --f) {
+    if (f >= c.nkr) continue;
+    const uint32_t n = (uint32_t)c.krn[f];
+    const uint32_t q = rem / n;
+    const uint32_t d = rem - q * n;
+    rem = q;
+    v *= ((const float*)c.kr[f])[(int64_t)d * c.wsI + (int64_t)b * c.wsB];
+  }
+  return v;
+}
+
+__device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
+  const Contract& c = op.c;
+  float* Ws = (float*)smem;                       // [kKgKT][kKgMB]
+  float* Is = Ws + kKgKT * kKgMB;                 // [kKgKT][kKgNT]
+  const int t = threadIdx.x;
+  const int64_t ncols = c.P * c.Q * c.J;
+  const int64_t ntile = (ncols + kKgNT - 1) / kKgNT;
+  const int64_t tile = blk % ntile, split = blk / ntile;
+  const int64_t i0 = split * op.chunk;
+  const int64_t i1 = min(c.NI, i0 + op.chunk);
+  const int NB = (int)c.NB;
+  // load role: column n0 + t of the tile, all kKgKT rows of a step
+  const int64_t ln = tile * kKgNT + t;
+  const bool lval = ln < ncols;
+  int64_t lbase = 0;
+  if (lval) {
+    const int64_t j = ln % c.J, pq = ln / c.J;
+    const int64_t q = pq % c.Q, p = pq / c.Q;
+    lbase = p * c.isP + q * c.isQ + j * c.isJ;
+  }
+  const float* in = (const float*)c.in;
+  // compute role: outputs b in [8 bg, 8 bg + 8), columns [4 cg, 4 cg + 4)
+  const int cg = t % 64, bg = t / 64;
+  float acc[8][4];
+#pragma unroll
+  for (int x = 0; x < 8; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+  float ri[kKgKT], rw[2];
+  auto fetch = [&](int64_t k0) {
+    const float* src = in + lbase + k0 * c.isI;
+    const int nk = (int)min((int64_t)kKgKT, i1 - k0);
+#pragma unroll
+    for (int kk = 0; kk < kKgKT; ++kk) {
+      ri[kk] = (lval && kk < nk) ? src[0] : 0.f;
+      src += c.isI;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + h * 256, kk = e / kKgMB, b = e % kKgMB;
+      const int64_t i = k0 + kk;
+      rw[h] = (b < NB && i < i1) ? kg_weight(c, i, b) : 0.f;
+    }
+  };
+  if (i0 < i1) fetch(i0);
+  for (int64_t k0 = i0; k0 < i1; k0 += kKgKT) {
+#pragma unroll
+    for (int kk = 0; kk < kKgKT; ++kk) Is[kk * kKgNT + t] = ri[kk];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) Ws[t + h * 256] = rw[h];
+    __syncthreads();
+    if (k0 + kKgKT < i1) fetch(k0 + kKgKT);
+#pragma unroll
+    for (int kk = 0; kk < kKgKT; ++kk) {
+      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg + 4]);
+      const float4 xv = *reinterpret_cast<const float4*>(&Is[kk * kKgNT + 4 * cg]);
+      const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+      const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += wv[x] * xs[y];
+    }
+    __syncthreads();
+  }
+  const int64_t total = c.P * c.NB * c.Q * c.J;
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    const int64_t n = tile * kKgNT + 4 * cg + y;
+    if (n >= ncols) continue;
+    const int64_t j = n % c.J, pq = n / c.J;
+    const int64_t q = pq % c.Q, p = pq / c.Q;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int b = 8 * bg + x;
+      if (b >= NB) continue;
+      if (op.nsplit > 1) {
+        ((float*)op.partial)[split * total + ((p * c.NB + b) * c.Q + q) * c.J + j] = acc[x][y];
+      } else {
+        float* o = (float*)c.out + p * c.osP + (int64_t)b * c.osB + q * c.osQ + j * c.osJ;
+        const float v = (float)c.alpha * acc[x][y];
+        *o = c.accumulate ? *o + v : v;
+      }
+    }
+  }
+}
+
 template <typename I>
 __device__ __forceinline__ I scatter_div(const Scatter& s, int a, I n) {
   if (sizeof(I) == 4) {
@@ -485,6 +601,9 @@ __device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned 
     case OP_OUTER:
       dev_outer(op, blk);
       break;
+    case OP_KGEMM:
+      dev_kgemm(op, blk, dsm);
+      break;
     default:
       break;
   }
@@ -543,6 +662,18 @@ int64_t plan_contract(Op& op) {
   if (total == 0) {
     op.blocks = 0;
     return 0;
+  }
+  if (c.nkr > 0) {
+    // Khatri-Rao weights exist only in the split-K tiled form (binary32,
+    // NB <= kKgMB, weights independent of p, q, j: the recorder checks)
+    const int64_t ntile = ceil_div(c.P * c.Q * c.J, (int64_t)kKgNT);
+    const int64_t want = (int64_t)exec_sms() * 2;
+    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, ntile), c.NI / 64));
+    op.chunk = round_up(ceil_div(c.NI, ns), (int64_t)kKgKT);
+    op.nsplit = (int)ceil_div(c.NI, op.chunk);
+    op.kind = OP_KGEMM;
+    op.blocks = ntile * op.nsplit;
+    return op.nsplit > 1 ? total * op.nsplit : 0;
   }
   // long reductions with few outputs: split-K through shared-memory tiles
   if (c.w && c.wsQ == 0 && c.wsJ == 0 && c.wsP == 0 && op.tin == ET_F32 && op.tw == ET_F32 &&
@@ -616,7 +747,7 @@ void Program::add(Op op, const void* in1, const void* in2) {
                     : op.kind == OP_PROJ  ? (const void*)op.pj.out
                     : op.kind == OP_OUTER ? op.ou.out
                                           : op.c.out;
-  if ((op.kind == OP_CONTRACT && op.nsplit > 1) || op.kind == OP_KRED) {
+  if (((op.kind == OP_CONTRACT || op.kind == OP_KGEMM) && op.nsplit > 1) || op.kind == OP_KRED) {
     Op part = op;
     part.level = lvl;
     ops_.push_back(part);
@@ -674,16 +805,7 @@ static DevOp to_dev(const Op& o) {
   return d;
 }
 
-// TTNN_DUMP_PROGRAM=1 prints every executed op (level, kind, shape) to stderr.
-static bool dump_program() {
-  static const bool on = [] {
-    const char* e = getenv("TTNN_DUMP_PROGRAM");
-    return e && e[0] == '1';
-  }();
-  return on;
-}
-
-ttnn_status Program::run(cudaStream_t st) {
+ttnn_status Program::run(cudaStream_t st, bool dump) {
   const int L = levels();
   for (int lvl = 1; lvl <= L; ++lvl) {
     LevelBatch lb;
@@ -705,7 +827,25 @@ ttnn_status Program::run(cudaStream_t st) {
     };
     for (const Op& o : ops_) {
       if (o.level != lvl || o.blocks == 0) continue;
-      if (dump_program()) {
+      if (dump) {
+        // debugging: each op alone, timed (the stream is synchronised)
+        TTNN_TRY(flush());
+        cudaEvent_t a = nullptr, b = nullptr;
+        TTNN_TRY_CUDA(cudaEventCreate(&a));
+        TTNN_TRY_CUDA(cudaEventCreate(&b));
+        lb.ops[0] = to_dev(o);
+        lb.start[0] = 0;
+        lb.start[1] = o.blocks;
+        lb.nops = 1;
+        TTNN_TRY_CUDA(cudaEventRecord(a, st));
+        TTNN_TRY(flush());
+        TTNN_TRY_CUDA(cudaEventRecord(b, st));
+        TTNN_TRY_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        fprintf(stderr, "[ttnn] %8.1f us  ", ms * 1e3f);
         if (o.kind == OP_SCATTER)
           fprintf(stderr, "[ttnn] L%d scatter nd %d nsc %d blocks %lld\n", lvl, o.s.nd, o.s.nsc,
                   (long long)o.blocks);
@@ -716,6 +856,7 @@ ttnn_status Program::run(cudaStream_t st) {
                   lvl, (int)o.kind, (long long)o.c.P, (long long)o.c.NI, (long long)o.c.NB,
                   (long long)o.c.Q, (long long)o.c.J, (long long)o.c.isJ, (long long)o.c.wsJ,
                   (long long)o.c.wsQ, (long long)o.c.wsP, o.g, o.nsplit, (long long)o.blocks);
+        continue;
       }
       if (lb.nops == kMaxLevelOps) TTNN_TRY(flush());
       lb.ops[lb.nops] = to_dev(o);

@@ -13,7 +13,8 @@ namespace ttnn {
 enum OpKind {
   OP_CONTRACT = 0, OP_MP = 1, OP_SCATTER = 2, OP_REDUCE = 3, OP_EYE = 4, OP_KRED = 5,
   OP_PROJ = 6,    // projections of CP factors onto DRM factors (binary64)
-  OP_OUTER = 7    // sums of outer products of vector products into a sketch
+  OP_OUTER = 7,   // sums of outer products of vector products into a sketch
+  OP_KGEMM = 8    // split-K register-tiled contraction (long reduction, <= 32 outputs per column)
 };
 
 // OP_PROJ:  out[q * ldo + j] = w_q * sum_{k < n} F[k * ldF + j] * a[k * sak + (q0 + q) * saq]
@@ -81,7 +82,7 @@ struct DevOp {
   int idx32;   // every index of the op fits 31 bits: decode with 32-bit math
 };
 
-constexpr int kMaxLevelOps = 36;   // ops per batched launch (parameter space)
+constexpr int kMaxLevelOps = 34;   // ops per batched launch (parameter space)
 
 struct LevelBatch {
   LevelBatch() {}
@@ -96,8 +97,9 @@ class Program {
   void buffer(const void* p, int64_t bytes, int level = 0);
   // Records an op; its level follows the buffers it reads.
   void add(Op op, const void* in1, const void* in2 = nullptr);
-  // Launches every level in order on `st`.
-  ttnn_status run(cudaStream_t st);
+  // Launches every level in order on `st`; dump: print each op (level, kind,
+  // shape, blocks) to stderr first (a plan's TTNN_FLAG_DUMP_PROGRAM).
+  ttnn_status run(cudaStream_t st, bool dump = false);
   void clear() {
     ops_.clear();
     bufs_.clear();

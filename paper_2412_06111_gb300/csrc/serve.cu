@@ -270,14 +270,17 @@ extern "C" {
 
 ttnn_status ttnn_server_create(const ttnn_server_opts* opts, ttnn_server_t* out) {
   TTNN_CHECK_ARG(opts && out, "null argument");
-  TTNN_CHECK_ARG(opts->hbm_budget_bytes > 0, "hbm_budget_bytes must be positive");
+  TTNN_CHECK_ARG(opts->hbm_budget_bytes > static_scratch_resident_bytes(),
+                 "hbm_budget_bytes must exceed the library's %lld-byte static scratch block",
+                 (long long)static_scratch_resident_bytes());
   *out = nullptr;
   ttnn_server_s* S = new (std::nothrow) ttnn_server_s();
   if (!S) {
     set_error("host allocation failed");
     return TTNN_ENOMEM;
   }
-  S->budget = opts->hbm_budget_bytes;
+  // the library's static scratch block is resident beside the streams
+  S->budget = opts->hbm_budget_bytes - static_scratch_resident_bytes();
   S->max_batch = opts->max_batch > 0 ? opts->max_batch : 64;
   S->capacity = opts->queue_capacity > 0 ? (size_t)opts->queue_capacity : 65536;
   const int nw = opts->workers > 0 ? std::min(opts->workers, 64) : 4;

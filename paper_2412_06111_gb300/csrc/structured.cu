@@ -45,6 +45,17 @@ void add_vec(Outer& o, const double* v, int sq, int si, int ax, int64_t dv, int6
 
 }  // namespace
 
+int64_t cp_update_need(const ttnn_plan_s& P) {
+  // the allocations of one chunk of kProjQ ranks below, in the same order
+  Bump ws{nullptr, int64_t(1) << 62};
+  for (int mu = 0; mu < P.d; ++mu) {
+    ws.alloc((int64_t)kProjQ * P.rmax * 8);
+    ws.alloc((int64_t)kProjQ * P.smax * 8);
+  }
+  ws.alloc((int64_t)kProjQ * P.dims[0] * 8);
+  return ws.top;
+}
+
 ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weights,
                           const double* const* factors, double lambda, cudaStream_t st) {
   if (P.variant != 0) {
@@ -219,7 +230,7 @@ ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weight
         finish(op, nd.ps_off, shape);
       }
     }
-    TTNN_TRY(prog.run(st));
+    TTNN_TRY(prog.run(st, P.flags & TTNN_FLAG_DUMP_PROGRAM));
   }
   return TTNN_OK;
 }

@@ -46,14 +46,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false on timeout or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// Bounded wait: false after limit_ns or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit_ns = kTimeoutNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort) return false;
-    if (gtimer() - t0 > kTimeoutNs) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
 }
 // Bounded wait that ignores the abort flag (used to drain own work).
@@ -131,6 +132,10 @@ ttnn_status encode_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, 
                        int64_t inner, int64_t outer, uint32_t box_inner, uint32_t box_outer,
                        CUtensorMapSwizzle sw);
 int sm_count();
+// SMs a first-level pass spreads its persistent CTAs over: all of them, or,
+// with TTNN_FLAG_RESERVE_SMS, all but max(8, sketched nodes) (at most a
+// quarter), which stay free for a recovery running on another stream.
+int pass_sms(const ttnn_plan_s& P);
 // D[i][w] = sum_k P[k][i][w] for w < wpad (rows i < rows).
 __global__ void reduce_partials(const float* P, int K, int64_t stride_k, int64_t rows, int wpad,
                                 float* D);

@@ -51,8 +51,16 @@ def test_static_update_matches_update_dense_twice(case):
             api.ttnn_state_zero(run.state)
             api.ttnn_state_zero(other)
             api.ttnn_update_dense(other, data, off, ext, lam=lam)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            plan0 = api.ttnn_plan_device_bytes(run.plan)
             api.ttnn_update_dense_static(run.state, data, off, ext, lam=lam)
             torch.cuda.synchronize()
+            if call == 1:
+                # the second call (the block's address already known) allocates
+                # nothing: device memory and the plan's footprint are unchanged
+                assert torch.cuda.mem_get_info()[0] == free0
+                assert api.ttnn_plan_device_bytes(run.plan) == plan0
             got = run.state_host()
             buf = np.zeros_like(got, dtype=np.float64 if run.sizes[1] == 8 else np.float32)
             api.ttnn_state_save(other, buf)

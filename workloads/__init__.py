@@ -260,10 +260,44 @@ def streaming_updates(dims, n_updates, seed, box_modes=3, box_extent=32, cp_rank
 # ---------------------------------------------------------------------------
 # TTN rounding input
 # ---------------------------------------------------------------------------
+def _block_norm2(parent, ch, modes, cores, lo, rb):
+    """Squared Frobenius norm of the network formed by the [lo, lo + rb)
+    diagonal block of every core (input plumbing: Gram matrices contracted
+    leaves first)."""
+    order = []
+    stack = [parent.index(-1)]
+    while stack:
+        v = stack.pop()
+        order.append(v)
+        stack.extend(ch[v])
+    G = {}
+    for v in reversed(order):
+        C = cores[v]
+        if not ch[v]:
+            B = C[lo:lo + rb].reshape(rb, -1)
+            G[v] = B @ B.T
+            continue
+        sl = tuple(slice(lo, lo + rb) for _ in range(C.ndim))
+        B = C[sl]
+        head = 0 if parent[v] < 0 else 1
+        # contract every child axis with that child's Gram matrix
+        X = B
+        for k, c in enumerate(ch[v]):
+            X = np.moveaxis(np.tensordot(X, G[c], axes=([head + k], [0])), -1, head + k)
+        if head:
+            G[v] = np.tensordot(B, X, axes=(list(range(1, B.ndim)), list(range(1, B.ndim))))
+        else:
+            G[v] = np.array(np.sum(B * X))
+    return float(G[order[0]])
+
+
 def rounding_input(tree, dims, r_dom, r_noise, seed, dom_scale=100.0):
     """TTN with every edge of rank r_dom + r_noise: cores are block-diagonal
     direct sums of a dominant (rank r_dom) and a noise (rank r_noise) TTN,
-    entries N(0, 1/R); the dominant root block is scaled by dom_scale."""
+    entries N(0, 1/R) before scaling.  Each part's root block is then scaled
+    so that the noise part has unit Frobenius norm and the dominant part
+    dom_scale times that (with unscaled cores the noise part, of larger
+    ranks, would carry almost all of the norm)."""
     parent, leaf_modes, _ = tree
     ch, modes = children_of(parent, leaf_modes)
     rng = np.random.default_rng(seed)
@@ -286,9 +320,13 @@ def rounding_input(tree, dims, r_dom, r_noise, seed, dom_scale=100.0):
             for b, (lo, rb) in enumerate(((0, r_dom), (r_dom, r_noise))):
                 sl = tuple(slice(lo, lo + rb) for _ in shape)
                 C[sl] = blocks[b]
-            if is_root:
-                C[tuple(slice(0, r_dom) for _ in shape)] *= dom_scale
         cores[v] = C
+    root = parent.index(-1)
+    Cr = cores[root]
+    for lo, rb, target in ((0, r_dom, dom_scale), (r_dom, r_noise, 1.0)):
+        nrm = np.sqrt(_block_norm2(parent, ch, modes, cores, lo, rb))
+        sl = tuple(slice(lo, lo + rb) for _ in range(Cr.ndim))
+        Cr[sl] *= target / nrm
     return cores
 
 
