@@ -518,6 +518,49 @@ def run_rounding(api, W, torch, steps=5, warmup=3):
         api.ttnn_state_destroy(st)
         api.ttnn_plan_destroy(plan)
     out["noise_level"] = 0.01
+    # the paper's TTN-rounding workload (Sec. 8, second experiment) at its
+    # size: the example tree, modes 500, rank 70, orthogonal-CP transfer
+    # tensors with cubic decay, Haar leaves -> ranks 20, p = 10, binary64
+    tr6 = W.toy_tree()
+    n6 = len(tr6[0])
+    dims6 = [500] * 6
+    c6 = W.orthogonal_cp_ttn(tr6, dims6, 70, lambda i: 1.0 / i ** 3, 1006)
+    d6 = [torch.from_numpy(np.ascontiguousarray(c6[v])).cuda() for v in range(n6)]
+    ch6, _ = W.children_of(tr6[0], tr6[1])
+    tt6 = _ttn_inner(tr6[0], ch6, c6, c6)
+    plan = api.ttnn_plan_create(tr6, dims6, [20] * n6, [10] * n6, SEED + 6, sketch_dtype=api.F64,
+                                flags=api.FLAG_STRUCTURED_ONLY)
+    st = api.ttnn_state_create(plan)
+    outc = torch.zeros(api.ttnn_plan_sizes(plan)[2], dtype=torch.float64, device="cuda")
+
+    def step6():
+        api.ttnn_state_zero(st)
+        api.ttnn_update_ttn(st, d6, [70] * n6)
+        api.ttnn_recover_async(st, outc)
+
+    for _ in range(warmup):
+        step6()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step6()
+    e1.record()
+    torch.cuda.synchronize()
+    api.ttnn_plan_sync(plan)
+    host = outc.cpu().numpy()
+    nodes = [api.ttnn_plan_node(plan, v) for v in range(n6)]
+    got = {nd["user_index"]: host[nd["core_offset"]:nd["core_offset"] + nd["core_elems"]]
+           .reshape(nd["core_shape"]) for nd in nodes}
+    err6 = float(np.sqrt(max(tt6 - 2 * _ttn_inner(tr6[0], ch6, c6, got) +
+                             _ttn_inner(tr6[0], ch6, got, got), 0.0) / tt6))
+    out["paper_workload"] = {
+        "workload": "example tree, modes 500 (5^6 x 10^9 entries never formed), TTN rank 70, "
+                    "orthogonal-CP cores with sigma_i = i^-3, Haar leaves -> ranks 20, p = 10, FP64",
+        "ms_per_rounding": e0.elapsed_time(e1) / steps, "rel_error": err6,
+        "input_bytes": sum(c.numel() * 8 for c in d6)}
+    api.ttnn_state_destroy(st)
+    api.ttnn_plan_destroy(plan)
     return out
 
 

@@ -119,6 +119,21 @@ typedef struct {
                                        nodes) SMs (at most a quarter) free, so that a recovery
                                        of another state issued on another stream runs beside
                                        the next update's pass instead of after it */
+#define TTNN_FLAG_DENSE_DRM 128u    /* unstructured Gaussian DRMs [Sec. 4 eq. (sketch), the DRMs
+                                       of Thm 6.6]: node v draws its own X_v (n_{D\v} x r_v,
+                                       Philox kind 4) and Y_v (n_v x s_v, kind 5) keyed by its
+                                       lexicographic index, rounded to the plan's format,
+                                       instead of Khatri-Rao products of per-mode factors.
+                                       TTNN, binary64 / binary32 plans, at most 1 GiB of DRMs,
+                                       whole-tensor dense updates only (boxes, CP and
+                                       TTN-format updates: TTNN_EUNSUPPORTED) */
+#define TTNN_FLAG_TRUNCATE 256u    /* eps-truncated output [Sec. 4 recovery, eq.
+                                       (stabilized_nystrom)]: the directions the eps-pseudo-
+                                       inverse drops are cut from the cores, R_v,eps^+ being
+                                       applied as (V_1 Sigma_1^-1) U_1^T with U_1 moved into the
+                                       parent's Q_v: every core has its rank axes at the kept
+                                       ranks, written compactly (row-major) from its offset;
+                                       ttnn_plan_node reports those shapes after the recovery */
 #define TTNN_FLAG_WAIT_TEST 32u     /* testing the bounded-wait error path: the pipeline waits
                                        of the tensor-core passes give up at once, so a dense
                                        update on this plan is abandoned on the device and the
@@ -178,7 +193,9 @@ ttnn_status ttnn_philox_gaussian(uint64_t seed, int32_t kind, int32_t ident, int
  * draws the DRM factors on the device and sizes the workspace.
  * tree, dims (host [d]), ranks and oversample (host [n_nodes]) are read during
  * the call only.  opts may be NULL (TTNN, F32, eps_factor 10, u = 2^-52).
- * EINVAL: invalid tree/sizes (see conventions); EUNSUPPORTED: STTNN whose
+ * EINVAL: invalid tree/sizes (see conventions), a tensor of more than 2^46
+ * entries without TTNN_FLAG_STRUCTURED_ONLY (up to 2^62 with it: CP and
+ * TTN-format inputs never form the tensor); EUNSUPPORTED: STTNN whose
  * first root child is an identity leaf, or a TTNN_BF16X2 / TTNN_E4M3 plan
  * whose whole-tensor pass matrix (n_L x n_R) the tensor-core pass does not
  * take (n_L a multiple of 8; n_R a multiple of 8, or of 16 for E4M3; side

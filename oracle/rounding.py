@@ -166,3 +166,73 @@ def ttn_entries(tree, cores, idx):
         return np.einsum(spec, C, *vecs, optimize=True)
 
     return val(tree.root)
+
+
+# ---------------------------------------------------------------------------
+# TTN-SVD of a network (the hierarchical SVD of Sec. 8's comparisons, on a
+# tensor given in TTN format)
+# ---------------------------------------------------------------------------
+def _axes_except(nd_ndim, a):
+    return [i for i in range(nd_ndim) if i != a]
+
+
+def ttn_svd(tree, cores):
+    """The TTN-SVD approximant (every non-root node t projected onto the r_t
+    dominant left singular vectors of the unfolding T^(t), as
+    ``baselines.hsvd`` does on a dense tensor), computed without forming T:
+    1. orthogonalise the network leaves first (QR of each core against its
+       parent axis, the R factor absorbed by the parent), so that the subtree
+       of t spans T^(t)'s columns with an orthonormal basis U_t;
+    2. top-down Gram matrices G_t = M_t M_t^T of the rest of the network
+       (T^(t) = U_t M_t), so that the left singular vectors of T^(t) are
+       U_t W_t with W_t the dominant eigenvectors of G_t;
+    3. W_t W_t^T inserted on every edge (the orthogonal projector P_t acts on
+       that edge only), written as cores of ranks r_t.
+    Returns (cores, sigma) with sigma[t] the singular values of T^(t)."""
+    C = {v: np.array(c, dtype=np.float64) for v, c in cores.items()}
+    root = tree.root
+    # 1. orthogonalise: children before parents
+    for v in reversed(tree.lex):
+        if v == root:
+            continue
+        nd = tree.node(v)
+        X = C[v]
+        M = np.moveaxis(X, 0, -1).reshape(-1, X.shape[0])       # (rest, R_v)
+        Q, R = np.linalg.qr(M)
+        k = Q.shape[1]
+        C[v] = np.moveaxis(Q.reshape(list(np.moveaxis(X, 0, -1).shape[:-1]) + [k]), -1, 0)
+        par = tree.node(nd.parent)
+        a = par.children.index(v) + (0 if nd.parent == root else 1)
+        C[nd.parent] = np.moveaxis(np.tensordot(C[nd.parent], R, axes=([a], [1])), -1, a)
+    # 2. Gram matrices of the rest of the network, parents before children
+    G = {}
+    for v in tree.lex:
+        nd = tree.node(v)
+        if nd.is_leaf:
+            continue
+        X = C[v]
+        head = 0 if v == root else 1
+        Xg = X if v == root else np.tensordot(G[v], X, axes=([1], [0]))
+        for k, c in enumerate(nd.children):
+            a = head + k
+            G[c] = np.tensordot(X, Xg, axes=(_axes_except(X.ndim, a), _axes_except(X.ndim, a)))
+    # 3. projectors on the edges
+    W, sig = {}, {}
+    for v in tree.nonroot():
+        nd = tree.node(v)
+        ev, V = np.linalg.eigh((G[v] + G[v].T) / 2)
+        order = np.argsort(ev)[::-1]
+        sig[v] = np.sqrt(np.maximum(ev[order], 0.0))
+        W[v] = V[:, order[:min(nd.r, V.shape[1])]]
+    out = {}
+    for v in tree.lex:
+        nd = tree.node(v)
+        X = C[v]
+        head = 0 if v == root else 1
+        if v != root:
+            X = np.tensordot(W[v].T, X, axes=([1], [0]))
+        if not nd.is_leaf:
+            for k, c in enumerate(nd.children):
+                X = np.moveaxis(np.tensordot(X, W[c], axes=([head + k], [0])), -1, head + k)
+        out[v] = X
+    return out, sig

@@ -92,17 +92,33 @@ class Drm:
         self.Lch, self.Rch = ch[:a], ch[a:]
         self.Lmodes = list(range(tree.node(ch[0]).lo, tree.node(ch[a - 1]).hi))
         self.Rmodes = list(range(tree.node(ch[a]).lo, tree.node(ch[-1]).hi))
-        # "round": sketches of a TTN input (Sec. 7) never multiply a dense A
-        # on the tensor cores, so no KR block is rounded a second time
-        blk = (lambda f: kr(f)) if variant == "round" else (lambda f: pass_block(f, fmt))
-        self.BRX = blk([self.X[mu] for mu in self.Rmodes])
-        self.BLX = blk([self.X[mu] for mu in self.Lmodes])
         ygrp = self.Rch if yside == "R" else self.Lch
         self.ychild = ygrp[0] if len(ygrp) == 1 else None
-        self.Yside = None
-        if self.ychild is not None and not tree.node(self.ychild).identity:
-            c = tree.node(self.ychild)
-            self.Yside = blk([self.Y[mu] for mu in range(c.lo, c.hi)])
+        self._blocks = {}
+
+    def _block(self, key, factors):
+        # "round": sketches of a TTN input (Sec. 7) never multiply a dense A
+        # on the tensor cores, so no KR block is rounded a second time.  The
+        # blocks are formed on first use (a TTN input never needs them).
+        if key not in self._blocks:
+            self._blocks[key] = (kr(factors) if self.variant == "round"
+                                 else pass_block(factors, self.fmt))
+        return self._blocks[key]
+
+    @property
+    def BRX(self):
+        return self._block("BRX", [self.X[mu] for mu in self.Rmodes])
+
+    @property
+    def BLX(self):
+        return self._block("BLX", [self.X[mu] for mu in self.Lmodes])
+
+    @property
+    def Yside(self):
+        if self.ychild is None or self.tree.node(self.ychild).identity:
+            return None
+        c = self.tree.node(self.ychild)
+        return self._block("Yside", [self.Y[mu] for mu in range(c.lo, c.hi)])
 
     def in_left(self, v):
         return self.tree.node(v).lo < self.Rmodes[0]
@@ -209,7 +225,16 @@ def eps_pinv(R, eps_factor=10.0, u=U_DEFAULT):
     return Rp, int(keep.sum())
 
 
-def recover(tree, Om, Ps, Pr, eps_factor=10.0, u=U_DEFAULT):
+def eps_pinv_factors(R, eps_factor=10.0, u=U_DEFAULT):
+    """R_eps^+ = A U_1^T split into A = V_1 Sigma_1^-1 (r x k) and U_1 (r x k),
+    the k singular values > eps kept in decreasing order."""
+    Uu, sv, Vt = np.linalg.svd(R)
+    eps = eps_factor * u * (sv[0] if sv.size else 0.0)
+    keep = sv > eps
+    return Vt[keep].T / sv[keep][None, :], Uu[:, keep]
+
+
+def recover(tree, Om, Ps, Pr, eps_factor=10.0, u=U_DEFAULT, truncate=False):
     """Cores B_t from the sketches (Sec. 4 recovery phase, Algorithm 2).
 
     [Q_t, R_t] = qr(Omega_t);  leaf: B_t = Psi_t R_t,eps^+;
@@ -218,12 +243,19 @@ def recover(tree, Om, Ps, Pr, eps_factor=10.0, u=U_DEFAULT):
     root: B = (kron_c Q_c)^T Psi_root.  Identity nodes: Q = I, core = I.
     Cores use the axis order root (r_c1..r_cm), transfer (r_t, r_c1..r_cm),
     leaf (r_t, n_mu1..n_mus).  Returns (cores, info) keyed by user index;
-    info[v] = (numerical rank kept by the eps-pseudo-inverse).
+    info[v] = (numerical rank kept by the eps-pseudo-inverse).  truncate:
+    the rank axes carry the kept ranks (the same tensor, eq.
+    (stabilized_nystrom) with the dropped directions cut).
     """
     Q, Rp, info = {}, {}, {}
     for v in tree.sketched():
         Q[v], R = qr_pos(Om[v])
         Rp[v], info[v] = eps_pinv(R, eps_factor, u)
+        if truncate:
+            # eps-truncated output: R_eps^+ = (V_1 Sigma_1^-1) U_1^T with U_1
+            # moved into Q_v, so node v's rank axis carries the kept rank only
+            A, U1 = eps_pinv_factors(R, eps_factor, u)
+            Q[v], Rp[v] = Q[v] @ U1, A
 
     def Qc(c):
         nd = tree.node(c)
@@ -237,7 +269,7 @@ def recover(tree, Om, Ps, Pr, eps_factor=10.0, u=U_DEFAULT):
             continue
         if nd.is_leaf:
             B = Ps[v] @ Rp[v]                              # (n_t, r_t)
-            cores[v] = B.T.reshape([nd.r] + tree.dims[nd.lo:nd.hi])
+            cores[v] = B.T.reshape([B.shape[1]] + tree.dims[nd.lo:nd.hi])
         else:
             P = Ps[v]
             for k, c in enumerate(nd.children):
@@ -317,17 +349,20 @@ def ttnn_projectors(T, tree, drm):
 class DenseDrm:
     """Independent unstructured Gaussian DRMs X_{l,k} (n_{D\\t} x r_t) and
     Y_{l,k} (n_t x s_t) of eq. (sketch), as Thm 6.6 assumes (Philox kinds
-    DX / DY keyed by the node's lexicographic index)."""
+    DX / DY keyed by the node's lexicographic index), rounded to the run's
+    number format (the rounded matrix is the DRM)."""
 
-    def __init__(self, tree, seed):
-        self.tree, self.seed = tree, int(seed)
+    def __init__(self, tree, seed, fmt="f64"):
+        self.tree, self.seed, self.fmt = tree, int(seed), fmt
 
     def Yt(self, v):
         nd = self.tree.node(v)
         if nd.identity:
             return np.eye(nd.n)
-        return philox.gaussian_matrix(self.seed, philox.KIND_DY, nd.lex, nd.n, nd.s)
+        return quant.round_to(philox.gaussian_matrix(self.seed, philox.KIND_DY, nd.lex, nd.n, nd.s),
+                              self.fmt)
 
     def Xt(self, v):
         nd = self.tree.node(v)
-        return philox.gaussian_matrix(self.seed, philox.KIND_DX, nd.lex, self.tree.N // nd.n, nd.r)
+        return quant.round_to(philox.gaussian_matrix(self.seed, philox.KIND_DX, nd.lex,
+                                                     self.tree.N // nd.n, nd.r), self.fmt)

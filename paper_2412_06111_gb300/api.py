@@ -13,7 +13,7 @@ from ._sigs import TtnnNodeInfo, TtnnOpts, TtnnTree
 F64, F32, BF16, E4M3, BF16X2 = 0, 1, 2, 3, 4
 VARIANT_TTNN, VARIANT_STTNN = 0, 1
 FLAG_NO_SIDE_CACHE, FLAG_SIMT_PASS, FLAG_CLUSTER_REDUCE, FLAG_STRUCTURED_ONLY = 1, 2, 4, 8
-FLAG_DUMP_PROGRAM, FLAG_WAIT_TEST, FLAG_RESERVE_SMS = 16, 32, 64
+FLAG_DUMP_PROGRAM, FLAG_WAIT_TEST, FLAG_RESERVE_SMS, FLAG_DENSE_DRM, FLAG_TRUNCATE = 16, 32, 64, 128, 256
 KIND_X, KIND_Y, KIND_XT = 1, 2, 3
 
 

@@ -57,6 +57,7 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->sideR);
   cudaFree(P->sideL);
   cudaFree(P->yW);
+  cudaFree(P->dxy);
   cudaFree(P->ws);
   cudaFree(P->ws_rec);
   cudaFree(P->jobs_dev);
@@ -193,7 +194,23 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   for (int m = P.Rlo; m < P.Rhi; ++m) nR *= P.dims[m];
   const int sb = store_bytes(P.side_store);
   const bool dense = !(P.flags & TTNN_FLAG_STRUCTURED_ONLY);
-  if (dense && !(P.flags & TTNN_FLAG_NO_SIDE_CACHE)) {
+  if (P.flags & TTNN_FLAG_DENSE_DRM) {
+    // unstructured Gaussian X_t, Y_t per node (binary64 draws rounded to the
+    // plan's format, stored in the walk type)
+    if ((s = dense_drm_check(P)) != TTNN_OK) return fail(s);
+    const int64_t el = dense_drm_elems(P);
+    if ((s = palloc(&P.dxy, el * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
+    double* tmp = (double*)P.dxy;
+    if (!P.walk_f64 && (s = dev_alloc((void**)&tmp, el * 8)) != TTNN_OK) return fail(s);
+    s = dense_drm_generate(P, tmp, st);
+    if (s == TTNN_OK && !P.walk_f64) s = launch_convert_f64_to_f32(tmp, (float*)P.dxy, el, st);
+    if (!P.walk_f64) {
+      cudaStreamSynchronize(st);
+      cudaFree(tmp);
+    }
+    if (s != TTNN_OK) return fail(s);
+  }
+  if (dense && !(P.flags & (TTNN_FLAG_NO_SIDE_CACHE | TTNN_FLAG_DENSE_DRM))) {
     if (P.wR > 0) {
       if ((s = palloc(&P.sideR, (int64_t)P.wRpad * nR * sb)) != TTNN_OK) return fail(s);
       if ((s = make_side(P, fb, 0, P.sideR, nR, st))) return fail(s);
@@ -215,13 +232,16 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
   int64_t need_u = 0, need_r = 0;
   if (dense) {
     if ((s = dense_update_need(P, fb, &need_u))) return fail(s);
-    Box bb = fb;
-    bb.full = false;
-    int64_t need_b = 0;
-    if ((s = dense_update_need(P, bb, &need_b))) return fail(s);
-    need_u = std::max(need_u, need_b);
+    if (!(P.flags & TTNN_FLAG_DENSE_DRM)) {   // that form takes whole tensors only
+      Box bb = fb;
+      bb.full = false;
+      int64_t need_b = 0;
+      if ((s = dense_update_need(P, bb, &need_b))) return fail(s);
+      need_u = std::max(need_u, need_b);
+    }
   }
-  if (P.variant == TTNN_VARIANT_TTNN) need_u = std::max(need_u, cp_update_need(P));
+  if (P.variant == TTNN_VARIANT_TTNN && !(P.flags & TTNN_FLAG_DENSE_DRM))
+    need_u = std::max(need_u, cp_update_need(P));
   if ((s = run_recover(P, nullptr, nullptr, st, true, &need_r))) return fail(s);
   P.ws_bytes = need_u + 4096;
   if ((s = palloc((void**)&P.ws, P.ws_bytes)) != TTNN_OK) return fail(s);
@@ -301,6 +321,32 @@ ttnn_status ttnn_plan_node(ttnn_plan_t P, int32_t v, ttnn_node_info* o) {
   o->core_elems = nd.core_el;
   o->core_ndim = (int32_t)std::min<size_t>(nd.core_shape.size(), 10);
   for (int k = 0; k < o->core_ndim; ++k) o->core_shape[k] = nd.core_shape[k];
+  if (P->flags & TTNN_FLAG_TRUNCATE) {
+    // eps-truncated output: the shape of the last recovery's core (its rank
+    // axes at the kept ranks), once every kept rank it involves is known
+    auto kept = [&](int u) { return P->nodes[u].identity ? P->nodes[u].n : (int64_t)P->nodes[u].kept; };
+    std::vector<int64_t> sh(nd.core_shape.begin(), nd.core_shape.end());
+    bool known = true;
+    int a0 = 0;
+    if (v != P->root) {
+      if (!nd.identity) sh[0] = kept(v);
+      known = known && sh[0] >= 0;
+      a0 = 1;
+    }
+    if (!nd.leaf)
+      for (size_t k = 0; k < nd.ch.size(); ++k) {
+        sh[a0 + k] = kept(nd.ch[k]);
+        known = known && sh[a0 + k] >= 0;
+      }
+    if (known) {
+      int64_t el = 1;
+      for (int k = 0; k < o->core_ndim; ++k) {
+        o->core_shape[k] = sh[k];
+        el *= sh[k];
+      }
+      o->core_elems = el;
+    }
+  }
   o->kept_rank = nd.kept;
   o->jacobi_sweeps = nd.sweeps;
   return TTNN_OK;

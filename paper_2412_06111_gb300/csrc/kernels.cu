@@ -848,6 +848,38 @@ ttnn_status launch_axpy(void* y, const void* x, double alpha, int64_t n, int is_
   return check_launch("axpy_kernel");
 }
 
+// block (node k, chunk): the padded core's entries whose indices all lie
+// below the axes' kept extents, to their compact row-major positions.
+__global__ void compact_cores_kernel(const __grid_constant__ CompactBatch b) {
+  const CompactNode& nd = b.nd[blockIdx.y];
+  int32_t keep[10];
+  int64_t tot = 1;
+  for (int a = 0; a < nd.ndim; ++a) {
+    keep[a] = nd.job[a] >= 0 ? min(b.kept[nd.job[a]], nd.full[a]) : nd.full[a];
+    tot *= nd.full[a];
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e, dst = 0, stride = 1;
+    bool in = true;
+    for (int a = nd.ndim - 1; a >= 0; --a) {
+      const int64_t i = rem % nd.full[a];
+      rem /= nd.full[a];
+      if (i >= keep[a]) in = false;
+      dst += i * stride;
+      stride *= keep[a];
+    }
+    if (in) b.dst[nd.off + dst] = b.src[nd.off + e];
+  }
+}
+
+ttnn_status launch_compact_cores(const CompactBatch& b, int64_t max_elems, cudaStream_t st) {
+  if (b.n == 0) return TTNN_OK;
+  const int64_t bx = std::min<int64_t>(std::max<int64_t>(ceil_div(max_elems, 256), 1), 1024);
+  compact_cores_kernel<<<dim3((unsigned)bx, (unsigned)b.n, 1), 256, 0, st>>>(b);
+  return check_launch("compact_cores_kernel");
+}
+
 __global__ void eye_kernel(double* dst, int64_t n) {
   const int64_t m = n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;

@@ -139,7 +139,27 @@ struct QrJob {
   int s, r;
 };
 ttnn_status launch_qr_pinv(const QrJob* jobs_dev, int njobs, int rmax, int state_f64,
-                           double eps_factor, double u, int* kept_dev, cudaStream_t st);
+                           double eps_factor, double u, int* kept_dev, int trunc,
+                           cudaStream_t st);
+// Copies the assembled (rank-padded) cores into their eps-truncated shapes:
+// per node, the entries whose every index lies below its axis' kept rank,
+// row-major and compact, from src + off to dst + off.  Axis a of a node keeps
+// kept[job[a]] entries (job[a] >= 0) or all of full[a] (job[a] < 0).
+struct CompactNode {
+  int64_t off = 0;
+  int ndim = 0;
+  int32_t full[10] = {0};
+  int32_t job[10] = {0};
+};
+constexpr int kCompactNodes = 32;
+struct CompactBatch {
+  int n = 0;
+  const double* src = nullptr;
+  double* dst = nullptr;
+  const int* kept = nullptr;
+  CompactNode nd[kCompactNodes];
+};
+ttnn_status launch_compact_cores(const CompactBatch& b, int64_t max_elems, cudaStream_t st);
 constexpr int kMaxRecoverS = 128;
 constexpr int kMaxRecoverR = 64;
 

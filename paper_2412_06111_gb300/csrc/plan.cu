@@ -42,7 +42,7 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
   P.N = 1;
   for (int m = 0; m < d; ++m) {
     TTNN_CHECK_ARG(dims[m] >= 1, "mode size %d must be >= 1", m);
-    TTNN_CHECK_ARG(P.N <= (int64_t(1) << 46) / dims[m], "tensor too large");
+    TTNN_CHECK_ARG(P.N <= (int64_t(1) << 62) / dims[m], "tensor too large");
     P.N *= dims[m];
   }
   if (opts) {
@@ -52,6 +52,11 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
     P.u = opts->unit_roundoff;
     P.flags = opts->flags;
   }
+  // dense tensors are indexed with 64-bit products of their size; a plan
+  // for structured (CP / TTN-format) inputs never forms the tensor
+  TTNN_CHECK_ARG((P.flags & TTNN_FLAG_STRUCTURED_ONLY) || P.N <= (int64_t(1) << 46),
+                 "tensor too large for dense updates (more than 2^46 entries): use "
+                 "TTNN_FLAG_STRUCTURED_ONLY");
   TTNN_CHECK_ARG(P.variant == 0 || P.variant == 1, "bad variant");
   TTNN_CHECK_ARG(P.dtype >= 0 && P.dtype <= 4, "bad sketch dtype");
   TTNN_CHECK_ARG(P.eps_factor >= 0 && P.u >= 0, "eps_factor and unit_roundoff must be >= 0");
@@ -1125,6 +1130,22 @@ ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need) {
 ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                              const float* tile_scale, double lambda, cudaStream_t st, bool dry,
                              int64_t* peak, UpdateBatch* batch) {
+  if (P.flags & TTNN_FLAG_DENSE_DRM) {
+    if (batch) {
+      set_error("unstructured Gaussian DRMs: no batched (served) updates");
+      return TTNN_EUNSUPPORTED;
+    }
+    if (!dry) {
+      int64_t need = 0;
+      TTNN_TRY(dense_update_need(P, box, &need));
+      if (need > P.ws_bytes) {
+        set_error("dense update needs %lld workspace bytes, the plan holds %lld", (long long)need,
+                  (long long)P.ws_bytes);
+        return TTNN_ENOMEM;
+      }
+    }
+    return run_dense_drm_update(P, acc, data, box, lambda, st, dry, peak);
+  }
   if (!dry && P.dtype == TTNN_E4M3 && (!tile_scale || ((uintptr_t)tile_scale & 3))) {
     set_error("E4M3 updates need their tile scales (4-byte aligned)");
     return TTNN_EINVAL;
@@ -1568,6 +1589,10 @@ int j_axis(const View& v) { return find_ax(v, AX_J, -1); }
 ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores_in,
                            const int32_t* ranks_in, double lambda, cudaStream_t st, bool dry,
                            int64_t* peak) {
+  if (P.flags & TTNN_FLAG_DENSE_DRM) {
+    set_error("TTN-format updates need the Khatri-Rao DRMs");
+    return TTNN_EUNSUPPORTED;
+  }
   if (P.variant != TTNN_VARIANT_TTNN) {
     set_error("TTN-format updates take TTNN plans");
     return TTNN_EUNSUPPORTED;
@@ -1822,6 +1847,12 @@ ttnn_status plan_sync(ttnn_plan_s& P) {
 ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStream_t st, bool dry,
                         int64_t* peak, bool async) {
   Ws ws(P.ws_rec, P.ws_rec_bytes, dry);
+  // eps-truncated output: the cores are assembled rank-padded in the
+  // workspace, then copied into their kept shapes
+  const bool trunc = (P.flags & TTNN_FLAG_TRUNCATE) != 0;
+  double* padded = trunc ? (double*)ws.alloc(P.core_elems * 8) : nullptr;
+  double* const out_cores = cores;
+  if (trunc) cores = padded;
   Program prog;
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
   const int seb = P.walk_f64 ? 8 : 4;
@@ -1847,7 +1878,7 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
       P.jobs_host = jobs;
     }
     TTNN_TRY(launch_qr_pinv(P.jobs_dev, (int)jobs.size(), P.rmax, P.walk_f64, P.eps_factor, P.u,
-                            P.kept_dev, st));
+                            P.kept_dev, trunc ? 1 : 0, st));
   }
   ws.prog = &prog;   // Q and R_eps^+ above are produced before the program (level 0)
   // contraction of axis k of a contiguous tensor `dims` with W(i, b) =
@@ -1950,6 +1981,47 @@ ttnn_status run_recover(ttnn_plan_s& P, const void* acc, double* cores, cudaStre
     return TTNN_ENOMEM;
   }
   if (!dry) TTNN_TRY(prog.run(st, P.flags & TTNN_FLAG_DUMP_PROGRAM));
+  if (!dry && trunc) {
+    // every core into its kept shape (device-side kept ranks)
+    std::vector<int> job_of(P.nodes.size(), -1);
+    for (size_t j = 0; j < job_node.size(); ++j) job_of[job_node[j]] = (int)j;
+    CompactBatch b;
+    b.src = padded;
+    b.dst = out_cores;
+    b.kept = P.kept_dev;
+    int64_t maxel = 0;
+    for (int v : P.lex) {
+      const TNode& nd = P.nodes[v];
+      if (nd.core_shape.size() > 10) {
+        set_error("eps-truncated output: cores of at most 10 axes");
+        return TTNN_EUNSUPPORTED;
+      }
+      CompactNode& c = b.nd[b.n];
+      c.off = nd.core_off;
+      c.ndim = (int)nd.core_shape.size();
+      for (int a = 0; a < c.ndim; ++a) {
+        c.full[a] = (int32_t)nd.core_shape[a];
+        c.job[a] = -1;
+      }
+      int a0 = 0;
+      if (v != P.root) {
+        if (!nd.identity) c.job[0] = job_of[v];
+        a0 = 1;
+      }
+      if (!nd.leaf)
+        for (size_t k = 0; k < nd.ch.size(); ++k) {
+          const TNode& ch = P.nodes[nd.ch[k]];
+          if (!ch.identity) c.job[a0 + k] = job_of[ch.user];
+        }
+      maxel = std::max(maxel, nd.core_el);
+      if (++b.n == kCompactNodes) {
+        TTNN_TRY(launch_compact_cores(b, maxel, st));
+        b.n = 0;
+        maxel = 0;
+      }
+    }
+    TTNN_TRY(launch_compact_cores(b, maxel, st));
+  }
   if (!dry) prof_push(P, 2, ev0, prof_event(P, st));
   if (dry) return TTNN_OK;
   // read-back of kept ranks, sweeps and the device error word into pinned

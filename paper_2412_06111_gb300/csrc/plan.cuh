@@ -26,6 +26,7 @@ struct TNode {
   int64_t xt_off = -1;          // STTNN XT_v factor offset (elements) in the factor arrays
   int kept = -1;
   int sweeps = 0;
+  int64_t dx_off = -1, dy_off = -1;   // unstructured DRMs X_t, Y_t (TTNN_FLAG_DENSE_DRM)
   bool sketched() const { return parent >= 0 && !identity; }
 };
 
@@ -64,6 +65,7 @@ struct ttnn_plan_s {
   void* sideR = nullptr;        // cached full-size side blocks (pass storage)
   void* sideL = nullptr;
   void* yW = nullptr;           // walk-type copy of the pass Y block (full box)
+  void* dxy = nullptr;          // unstructured DRMs of every node, walk type (TTNN_FLAG_DENSE_DRM)
   char* ws = nullptr;
   int64_t ws_bytes = 0;
   // the recovery's own scratch: a recovery may run on another stream while
@@ -118,6 +120,14 @@ ttnn_status build_plan(ttnn_plan_s& P, const ttnn_tree* tree, int32_t d, const i
 ttnn_status dense_update_need(ttnn_plan_s& P, const Box& box, int64_t* need);
 // Workspace bytes of a CP update (any rank: ranks are taken kProjQ at a time).
 int64_t cp_update_need(const ttnn_plan_s& P);
+// Unstructured Gaussian DRMs (dense_drm.cu): the plan's restrictions, the
+// factor layout (sets dx_off / dy_off, returns the element count), their
+// generation in binary64 (rounded to the plan's format) and one update.
+ttnn_status dense_drm_check(const ttnn_plan_s& P);
+int64_t dense_drm_elems(ttnn_plan_s& P);
+ttnn_status dense_drm_generate(ttnn_plan_s& P, double* tmp64, cudaStream_t st);
+ttnn_status run_dense_drm_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
+                                 double lambda, cudaStream_t st, bool dry, int64_t* peak);
 // Bytes of the library's static scratch block (ttnn_update_dense_static),
 // resident on a device once the library's module is loaded there.
 int64_t static_scratch_resident_bytes();

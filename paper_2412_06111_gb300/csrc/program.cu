@@ -52,15 +52,30 @@ __device__ void dev_contract(const DevOp& op, int64_t blk) {
     const int64_t i0 = (int64_t)split * op.chunk;
     const int64_t i1 = min(c.NI, i0 + op.chunk);
     const Tin* ip = (const Tin*)c.in + (int64_t)p * c.isP + (int64_t)q * c.isQ + (int64_t)j * c.isJ;
+    // four independent partial sums: loads and multiply-adds of different
+    // terms overlap instead of waiting on one accumulator
+    Tacc a1 = 0, a2 = 0, a3 = 0;
+    int64_t i = i0 + lg;
     if (c.w) {
       const Tw* wp = (const Tw*)c.w + (int64_t)p * c.wsP + (int64_t)b * c.wsB + (int64_t)q * c.wsQ +
                      (int64_t)j * c.wsJ;
-#pragma unroll 4
-      for (int64_t i = i0 + lg; i < i1; i += g) acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
+      for (; i + 3 * g < i1; i += 4 * g) {
+        acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
+        a1 += (Tacc)ip[(i + g) * c.isI] * (Tacc)wp[(i + g) * c.wsI];
+        a2 += (Tacc)ip[(i + 2 * g) * c.isI] * (Tacc)wp[(i + 2 * g) * c.wsI];
+        a3 += (Tacc)ip[(i + 3 * g) * c.isI] * (Tacc)wp[(i + 3 * g) * c.wsI];
+      }
+      for (; i < i1; i += g) acc += (Tacc)ip[i * c.isI] * (Tacc)wp[i * c.wsI];
     } else {
-#pragma unroll 4
-      for (int64_t i = i0 + lg; i < i1; i += g) acc += (Tacc)ip[i * c.isI];
+      for (; i + 3 * g < i1; i += 4 * g) {
+        acc += (Tacc)ip[i * c.isI];
+        a1 += (Tacc)ip[(i + g) * c.isI];
+        a2 += (Tacc)ip[(i + 2 * g) * c.isI];
+        a3 += (Tacc)ip[(i + 3 * g) * c.isI];
+      }
+      for (; i < i1; i += g) acc += (Tacc)ip[i * c.isI];
     }
+    acc = (acc + a1) + (a2 + a3);
   }
   for (int off = g >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if (valid && lg == 0) {
@@ -322,7 +337,9 @@ __device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
 // kKgKT rows, the next rows prefetched into registers.  With nsplit > 1 the
 // block writes its partial sums [split][p][b][q][j], reduced in a fixed order
 // (OP_REDUCE), else the outputs.
-constexpr int kKgKT = 16, kKgNT = 256, kKgMB = 32;
+constexpr int kKgKT = 8, kKgNT = 128, kKgMB = 32;
+constexpr int kKgWPT = kKgKT * kKgMB / 256;   // weight-tile entries per thread
+static_assert(kKgKT * kKgMB % 256 == 0 && kKgWPT >= 1, "weight tile must split over 256 threads");
 
 // W(i, b) of a split-K contraction; i < 2^31 (the recorder checks).
 __device__ __forceinline__ float kg_weight(const Contract& c, int64_t i, int b) {
@@ -352,8 +369,9 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
   const int64_t i0 = split * op.chunk;
   const int64_t i1 = min(c.NI, i0 + op.chunk);
   const int NB = (int)c.NB;
-  // load role: column n0 + t of the tile, all kKgKT rows of a step
-  const int64_t ln = tile * kKgNT + t;
+  // load role: column t % kKgNT of the tile, rows t / kKgNT + 2 u of a step
+  const int lc = t % kKgNT, lr = t / kKgNT;
+  const int64_t ln = tile * kKgNT + lc;
   const bool lval = ln < ncols;
   int64_t lbase = 0;
   if (lval) {
@@ -362,51 +380,51 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     lbase = p * c.isP + q * c.isQ + j * c.isJ;
   }
   const float* in = (const float*)c.in;
-  // compute role: outputs b in [8 bg, 8 bg + 8), columns [4 cg, 4 cg + 4)
-  const int cg = t % 64, bg = t / 64;
-  float acc[8][4];
+  // compute role: outputs b in [4 bg, 4 bg + 4), columns [4 cg, 4 cg + 4)
+  const int cg = t % 32, bg = t / 32;
+  float acc[4][4];
 #pragma unroll
-  for (int x = 0; x < 8; ++x)
+  for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-  float ri[kKgKT], rw[2];
-  auto fetch = [&](int64_t k0) {
-    const float* src = in + lbase + k0 * c.isI;
-    const int nk = (int)min((int64_t)kKgKT, i1 - k0);
-#pragma unroll
-    for (int kk = 0; kk < kKgKT; ++kk) {
-      ri[kk] = (lval && kk < nk) ? src[0] : 0.f;
-      src += c.isI;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = t + h * 256, kk = e / kKgMB, b = e % kKgMB;
-      const int64_t i = k0 + kk;
-      rw[h] = (b < NB && i < i1) ? kg_weight(c, i, b) : 0.f;
-    }
-  };
-  if (i0 < i1) fetch(i0);
+  // the next step's rows are read into registers while this step computes
+  constexpr int kRows = kKgKT * kKgNT / 256;      // input rows each thread loads per step
+  float ri[kRows], rw[kKgWPT];
+#define KG_FETCH(k0_)                                                         \
+  {                                                                           \
+    const int nk_ = (int)min((int64_t)kKgKT, i1 - (k0_));                     \
+    _Pragma("unroll") for (int u = 0; u < kRows; ++u) {                      \
+      const int kk_ = lr + u * (256 / kKgNT);                                 \
+      ri[u] = (lval && kk_ < nk_) ? in[lbase + ((k0_) + kk_) * c.isI] : 0.f;  \
+    }                                                                         \
+    _Pragma("unroll") for (int h = 0; h < kKgWPT; ++h) {                     \
+      const int e_ = t + h * 256, kk_ = e_ / kKgMB, b_ = e_ % kKgMB;          \
+      rw[h] = (b_ < NB && kk_ < nk_) ? kg_weight(c, (k0_) + kk_, b_) : 0.f;   \
+    }                                                                         \
+  }
+  if (i0 < i1) KG_FETCH(i0);
   for (int64_t k0 = i0; k0 < i1; k0 += kKgKT) {
 #pragma unroll
-    for (int kk = 0; kk < kKgKT; ++kk) Is[kk * kKgNT + t] = ri[kk];
+    for (int u = 0; u < kRows; ++u) Is[(lr + u * (256 / kKgNT)) * kKgNT + lc] = ri[u];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) Ws[t + h * 256] = rw[h];
+    for (int h = 0; h < kKgWPT; ++h) Ws[t + h * 256] = rw[h];
     __syncthreads();
-    if (k0 + kKgKT < i1) fetch(k0 + kKgKT);
+    if (k0 + kKgKT < i1) KG_FETCH(k0 + kKgKT);
 #pragma unroll
     for (int kk = 0; kk < kKgKT; ++kk) {
-      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg]);
-      const float4 w1 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg + 4]);
+      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 4 * bg]);
       const float4 xv = *reinterpret_cast<const float4*>(&Is[kk * kKgNT + 4 * cg]);
-      const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-      const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-      for (int x = 0; x < 8; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] += wv[x] * xs[y];
+#define KG_ROW(row_, w_)          \
+  acc[row_][0] += (w_) * xv.x;    \
+  acc[row_][1] += (w_) * xv.y;    \
+  acc[row_][2] += (w_) * xv.z;    \
+  acc[row_][3] += (w_) * xv.w;
+      KG_ROW(0, w0.x) KG_ROW(1, w0.y) KG_ROW(2, w0.z) KG_ROW(3, w0.w)
+#undef KG_ROW
     }
     __syncthreads();
   }
+#undef KG_FETCH
   const int64_t total = c.P * c.NB * c.Q * c.J;
 #pragma unroll
   for (int y = 0; y < 4; ++y) {
@@ -415,8 +433,8 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     const int64_t j = n % c.J, pq = n / c.J;
     const int64_t q = pq % c.Q, p = pq / c.Q;
 #pragma unroll
-    for (int x = 0; x < 8; ++x) {
-      const int b = 8 * bg + x;
+    for (int x = 0; x < 4; ++x) {
+      const int b = 4 * bg + x;
       if (b >= NB) continue;
       if (op.nsplit > 1) {
         ((float*)op.partial)[split * total + ((p * c.NB + b) * c.Q + q) * c.J + j] = acc[x][y];
@@ -571,9 +589,7 @@ __device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned 
         switch (op.BG) {
           case 8: dev_mpw<8, I>(op, blk, dsm); break;
           case 16: dev_mpw<16, I>(op, blk, dsm); break;
-          case 32: dev_mpw<32, I>(op, blk, dsm); break;
-          case 48: dev_mpw<48, I>(op, blk, dsm); break;
-          default: dev_mpw<64, I>(op, blk, dsm); break;
+          default: dev_mpw<32, I>(op, blk, dsm); break;
         }
       } else if (op.tout == ET_F64) {
         dev_mp<double, I>(op, blk, dsm);
@@ -633,8 +649,10 @@ static bool mp_tiling(Op& op) {
   if (!(op.tin == op.tw && op.tw == op.tout)) return false;
   if (op.tout == ET_F64) return false;    // few FP64 units per SM: spread FP64 work thin instead
   if (c.P * c.Q * c.NB * c.J < 8192) return false;
-  if (c.NI <= kWsMaxNI) {
-    const int nbt = c.NB <= 8 ? 8 : c.NB <= 16 ? 16 : c.NB <= 32 ? 32 : c.NB <= 48 ? 48 : 64;
+  if (c.NI <= kWsMaxNI && c.NB <= 32) {
+    // at most 32 outputs per thread (3 resident blocks per SM; wider weights
+    // take the tiled form below)
+    const int nbt = c.NB <= 8 ? 8 : c.NB <= 16 ? 16 : 32;
     op.kind = OP_MP;
     op.BG = nbt;
     op.CG = 0;
@@ -681,15 +699,18 @@ int64_t plan_contract(Op& op) {
       c.NB * c.J <= 16 * kExecThreads && c.P * c.Q <= 64) {
     const int64_t items = c.P * c.Q;
     const int64_t want = (int64_t)exec_sms() * 4;
-    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, items), c.NI / 256));
+    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, items), c.NI / kKredTile));
     op.chunk = round_up(ceil_div(c.NI, ns), kKredTile);
     op.nsplit = (int)ceil_div(c.NI, op.chunk);
     op.kind = OP_KRED;
     op.blocks = items * op.nsplit;
     return total * op.nsplit;
   }
-  if (mp_tiling(op)) return 0;
+  // the tiled and weight-stationary mode products give each thread many
+  // outputs: for small ops that leaves most SMs idle while a few blocks run
+  // long; there one lane group per output spreads the work instead
   const int64_t want = (int64_t)exec_sms() * 1024;   // threads that keep the GPU busy
+  if (total >= want / 4 && mp_tiling(op)) return 0;
   int g = 1;
   while (g < 32 && total * g < want && c.NI >= 8 * g) g <<= 1;
   op.g = g;

@@ -80,9 +80,13 @@ __device__ void tri_inv_upper(const double* W, double* X, int r, const double* r
 
 // dynamic shared memory (column-major, leading dimension s for A and Q,
 // r for W, V and X): A (s x r), Q (s x r), W, V, X (r x r), small arrays.
+// trunc != 0 (eps-truncated output): when singular values of R are dropped,
+// q receives Q U_1 and rp receives V_1 Sigma_1^-1 (kept columns first, in
+// index order, zero columns after), so that the cores assembled from them
+// carry the kept ranks; R_eps^+ = (V_1 Sigma_1^-1) U_1^T is the same map.
 __global__ void __launch_bounds__(kQrMaxThreads) qr_pinv_kernel(const QrJob* jobs, int state_f64,
                                                              double eps_factor, double u,
-                                                             int* kept) {
+                                                             int* kept, int trunc) {
   extern __shared__ double sm[];
   const QrJob job = jobs[blockIdx.x];
   const int s = job.s, r = job.r;
@@ -392,12 +396,43 @@ __global__ void __launch_bounds__(kQrMaxThreads) qr_pinv_kernel(const QrJob* job
   double* inv2 = vn;
   for (int k = tid; k < r; k += (int)blockDim.x) inv2[k] = rd[k] > eps ? 1.0 / (rd[k] * rd[k]) : 0.0;
   __syncthreads();
-  // Rp[i][j] = sum_{kept k} V[i][k] W[j][k] / sigma_k^2  (row-major output)
-  for (int e = tid; e < r * r; e += (int)blockDim.x) {
-    const int i = e / r, j = e % r;
-    double acc = 0.0;
-    for (int k = 0; k < r; ++k) acc += V[k * r + i] * W[k * r + j] * inv2[k];
-    job.rp[e] = acc;
+  if (trunc) {
+    // kept columns in index order: slot[k] = position among the kept, -1 dropped
+    __shared__ int slot[kMaxRecoverR];
+    if (tid == 0) {
+      int c = 0;
+      for (int k = 0; k < r; ++k) slot[k] = rd[k] > eps ? c++ : -1;
+    }
+    __syncthreads();
+    // rp = V_1 Sigma_1^-1 (r x r, row-major, kept columns first)
+    for (int e = tid; e < r * r; e += (int)blockDim.x) {
+      const int i = e / r, c = e % r;
+      double v = 0.0;
+      for (int k = 0; k < r; ++k)
+        if (slot[k] == c) v = V[k * r + i] / rd[k];
+      job.rp[e] = v;
+    }
+    // q <- Q U_1 with U_1[:, c] = W[:, k] / sigma_k; A (no longer needed)
+    // holds the product until every thread has read Q
+    double* QU = A;
+    for (int e = tid; e < s * r; e += (int)blockDim.x) {
+      const int i = e / r, c = e % r;
+      double acc = 0.0;
+      for (int k = 0; k < r; ++k)
+        if (slot[k] == c)
+          for (int l = 0; l < r; ++l) acc += job.q[i * r + l] * (W[k * r + l] / rd[k]);
+      QU[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < s * r; e += (int)blockDim.x) job.q[e] = QU[e];
+  } else {
+    // Rp[i][j] = sum_{kept k} V[i][k] W[j][k] / sigma_k^2  (row-major output)
+    for (int e = tid; e < r * r; e += (int)blockDim.x) {
+      const int i = e / r, j = e % r;
+      double acc = 0.0;
+      for (int k = 0; k < r; ++k) acc += V[k * r + i] * W[k * r + j] * inv2[k];
+      job.rp[e] = acc;
+    }
   }
   if (tid == 0) {
     int cnt = 0;
@@ -408,14 +443,16 @@ __global__ void __launch_bounds__(kQrMaxThreads) qr_pinv_kernel(const QrJob* job
 }
 
 ttnn_status launch_qr_pinv(const QrJob* jobs_dev, int njobs, int rmax, int state_f64,
-                           double eps_factor, double u, int* kept_dev, cudaStream_t st) {
+                           double eps_factor, double u, int* kept_dev, int trunc,
+                           cudaStream_t st) {
   if (njobs == 0) return TTNN_OK;
   const size_t smem = (size_t)(2 * kMaxRecoverS * kMaxRecoverR + 3 * kMaxRecoverR * kMaxRecoverR +
                                2 * (kMaxRecoverR + 1)) * sizeof(double);
   TTNN_TRY_CUDA(cudaFuncSetAttribute(qr_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
   const int warps = std::min(kQrMaxWarps, std::max(8, (rmax + 1) / 2));
-  qr_pinv_kernel<<<njobs, warps * 32, smem, st>>>(jobs_dev, state_f64, eps_factor, u, kept_dev);
+  qr_pinv_kernel<<<njobs, warps * 32, smem, st>>>(jobs_dev, state_f64, eps_factor, u, kept_dev,
+                                                  trunc);
   return check_launch("qr_pinv_kernel");
 }
 

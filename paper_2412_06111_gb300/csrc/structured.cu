@@ -62,6 +62,10 @@ ttnn_status run_cp_update(ttnn_plan_s& P, void* acc, int Q, const double* weight
     set_error("CP updates take TTNN plans (STTNN sketches a dense tensor in one pass)");
     return TTNN_EUNSUPPORTED;
   }
+  if (P.flags & TTNN_FLAG_DENSE_DRM) {
+    set_error("CP updates need the Khatri-Rao DRMs");
+    return TTNN_EUNSUPPORTED;
+  }
   if (P.d > kOuterVecs) {
     set_error("CP updates support order <= %d", kOuterVecs);
     return TTNN_EUNSUPPORTED;

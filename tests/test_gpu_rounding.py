@@ -81,3 +81,48 @@ def test_rounding_order8_rank200_to_30_matches_oracle(dtype):
                     OR.ttn_inner(t, cores, cores))
     assert abs(noise - 0.01) <= 1e-3
     assert abs(e_gpu - e_orc) <= 1e-3 * e_orc
+
+
+# ---------------------------------------------------------------------------
+# the paper's TTN-rounding workload (Sec. 8, second experiment) at its size
+# ---------------------------------------------------------------------------
+DECAYS = {"quadratic": lambda i: 1.0 / i ** 2, "cubic": lambda i: 1.0 / i ** 3,
+          "exponential": lambda i: 2.0 ** (-i)}
+
+
+@pytest.mark.timeout(900)
+@pytest.mark.parametrize("decay", sorted(DECAYS))
+def test_paper_rounding_workload_6d_modes500_rank70(decay):
+    """The paper's example tree, modes 500, TTN rank 70 with orthogonal-CP
+    transfer tensors (sigma_i decaying) and Haar leaves, recompressed to ranks
+    20 with p = 10 in binary64: sketches and recovered entries against the
+    oracle, and the approximation error beside the oracle's TTN-SVD."""
+    tr = W.toy_tree()
+    n = len(tr[0])
+    dims = [500] * 6
+    R, r, p = 70, 20, 10
+    cores = W.orthogonal_cp_ttn(tr, dims, R, DECAYS[decay], 1006)
+    t = Tree(tr[0], tr[1], dims, [r] * n, [p] * n, tr[2])
+    run = Run(tr, dims, [r] * n, [p] * n, SEED + 1, dtype=api.F64, flags=api.FLAG_STRUCTURED_ONLY)
+    try:
+        dev = [torch.from_numpy(np.ascontiguousarray(cores[v])).cuda() for v in range(n)]
+        api.ttnn_update_ttn(run.state, dev, [R] * n)
+        gOm, gPs, gPr = run.sketches()
+        got = run.recover()
+    finally:
+        run.close()
+    Om, Ps, Pr = OR.sketch_ttn_input(cores, t, O.Drm(t, SEED + 1, "f64", "round"))
+    worst = max(max(rel(gOm[v], Om[v]), rel(gPs[v], Ps[v])) for v in t.sketched())
+    worst = max(worst, rel(gPr, Pr))
+    assert worst <= 1e-12, worst
+    want = O.recover(t, Om, Ps, Pr)[0]
+    rng = np.random.default_rng(7)
+    idx = np.stack([rng.integers(0, 500, size=20000) for _ in range(6)], axis=1)
+    assert rel(OR.ttn_entries(t, got, idx), OR.ttn_entries(t, want, idx)) <= 1e-10
+    e_gpu, e_orc = _err(t, cores, got), _err(t, cores, want)
+    assert abs(e_gpu - e_orc) <= 1e-6 * e_orc
+    svd, _ = OR.ttn_svd(t, cores)
+    e_svd = _err(t, cores, svd)
+    # quasi-optimality of the TTN-SVD: it is within sqrt(#edges) of the best
+    # rank-r TTN, which no approximation of these ranks beats
+    assert e_gpu >= e_svd / np.sqrt(n - 1) * (1 - 1e-9)

@@ -95,7 +95,8 @@ def _state(plan, st):
 
 
 def test_mixed_streams_equal_alone_bitwise():
-    srv = api.ttnn_server_create(64 << 30, max_batch=8)
+    # one worker: requests that arrive while it works queue up and are batched
+    srv = api.ttnn_server_create(64 << 30, max_batch=8, workers=1)
     rng = np.random.default_rng(0)
     alone, sids, work = [], [], []
     try:

@@ -129,3 +129,32 @@ def test_eps_pseudo_inverse_threshold():
     R2 = np.triu(W.gaussian((5, 5), 7)) + 5 * np.eye(5)
     Rp2, k2 = O.eps_pinv(R2)
     assert k2 == 5 and np.allclose(Rp2 @ R2, np.eye(5), atol=1e-13)
+
+
+@pytest.mark.parametrize("variant", ["ttnn", "sttnn"])
+def test_truncated_output_is_the_same_tensor_with_kept_ranks(variant):
+    """eps-truncated cores: rank axes at the kept ranks, same reconstruction
+    as the untruncated cores; exact recovery still holds."""
+    tr = W.toy_tree()
+    dims = [5, 4, 5, 4, 5, 4]
+    T, _ = W.exact_ttn(tr, dims, [2] * 10, 3)
+    t = _tree(tr, dims, 4, 3)
+    drm = O.Drm(t, 9, "f64", variant)
+    sk = (O.sketch_ttnn if variant == "ttnn" else OS.sketch_sttnn)(T, t, drm)
+    full, info = O.recover(t, *sk)
+    cut, info2 = O.recover(t, *sk, truncate=True)
+    assert info == info2 and min(info.values()) < 4
+    for v in t.nonroot():
+        nd = t.node(v)
+        if nd.identity:
+            continue
+        assert cut[v].shape[0] == info[v]
+        if not nd.is_leaf:
+            for k, c in enumerate(nd.children):
+                if not t.node(c).identity:
+                    assert cut[v].shape[1 + k] == info[c]
+    for k, c in enumerate(t.node(t.root).children):
+        if not t.node(c).identity:
+            assert cut[t.root].shape[k] == info[c]
+    assert _rel(O.reconstruct(t, cut), O.reconstruct(t, full)) < 1e-12
+    assert _rel(O.reconstruct(t, cut), T) < 1e-10

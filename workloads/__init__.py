@@ -16,7 +16,14 @@ Sec. 8; these mirror their shapes):
 * cp_term / box_update: rank-2 CP terms with N(0,1) factors and dense
   sub-blocks of N(0, 0.01) noise (streamed order-6 case).
 * rounding_input: TTN cores of rank R_dom + R_noise as a block-diagonal direct
-  sum, N(0, 1/R) entries, the dominant block scaled by 100 (order-8 rounding).
+  sum, N(0, 1/R) entries, the dominant part 100 times the noise part in norm
+  (order-8 rounding).
+* orthogonal_cp_ttn: the paper's TTN-rounding inputs (Sec. 8, second
+  experiment): every transfer tensor a superdiagonal tensor of a decaying
+  sequence sigma_i multiplied by Haar orthogonal matrices along each axis,
+  Haar orthogonal leaf matrices.
+* hilbert: the paper's Hilbert tensor 1 / (1 + i_1 + ... + i_d) (Sec. 8,
+  first experiment).
 """
 import numpy as np
 
@@ -328,6 +335,49 @@ def rounding_input(tree, dims, r_dom, r_noise, seed, dom_scale=100.0):
         sl = tuple(slice(lo, lo + rb) for _ in range(Cr.ndim))
         Cr[sl] *= target / nrm
     return cores
+
+
+def haar_orthogonal(n, k, rng):
+    """n x k with orthonormal columns, Haar distributed: Q of the QR of a
+    Gaussian n x k matrix with the signs of diag(R) folded in (Mezzadri)."""
+    Z = rng.standard_normal((n, k))
+    Q, R = np.linalg.qr(Z)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def orthogonal_cp_ttn(tree, dims, rank, decay, seed):
+    """TTN of edge rank `rank`: each transfer tensor (and the root) is the
+    superdiagonal tensor with entries sigma_i = decay(i), i = 1..rank,
+    multiplied along every axis by a Haar orthogonal rank x rank matrix; each
+    leaf core is the transpose of a Haar orthogonal n_leaf x rank matrix."""
+    parent, leaf_modes, _ = tree
+    ch, modes = children_of(parent, leaf_modes)
+    rng = np.random.default_rng(seed)
+    sig = np.array([decay(i) for i in range(1, rank + 1)], dtype=np.float64)
+    cores = {}
+    for v in range(len(parent)):
+        if not ch[v]:
+            n = int(np.prod([dims[m] for m in modes[v]]))
+            cores[v] = haar_orthogonal(n, rank, rng).T.reshape([rank] + [dims[m] for m in modes[v]])
+            continue
+        k = len(ch[v]) + (0 if parent[v] < 0 else 1)
+        C = np.zeros([rank] * k)
+        C[tuple(np.arange(rank) for _ in range(k))] = sig
+        for a in range(k):
+            U = haar_orthogonal(rank, rank, rng)
+            C = np.moveaxis(np.tensordot(C, U, axes=([a], [1])), -1, a)
+        cores[v] = C
+    return cores
+
+
+def hilbert(d, n, dtype=np.float64):
+    """H[i_1..i_d] = 1 / (1 + i_1 + ... + i_d), 0-based indices (Sec. 8)."""
+    s = np.zeros([n] * d)
+    for mu in range(d):
+        sh = [1] * d
+        sh[mu] = n
+        s = s + np.arange(n, dtype=np.float64).reshape(sh)
+    return (1.0 / (1.0 + s)).astype(dtype)
 
 
 # ---------------------------------------------------------------------------
