@@ -564,6 +564,88 @@ def run_rounding(api, W, torch, steps=5, warmup=3):
     return out
 
 
+def _sampled_error(api, plan, tree, cores_dev, dims, exact, samples=20000, seed=77):
+    """Relative error of the recovered TTN on `samples` seeded entries against
+    exact(idx) (host evaluation of the cores: leaf slices, then each transfer
+    tensor against its children's vectors)."""
+    parent, leaf_modes, _ = tree
+    nn = len(parent)
+    nodes = [api.ttnn_plan_node(plan, v) for v in range(nn)]
+    host = cores_dev.cpu().numpy()
+    rng = np.random.default_rng(seed)
+    d = len(dims)
+    idx = np.stack([rng.integers(0, dims[m], size=samples) for m in range(d)], axis=1)
+    ch = {v: sorted([c for c in range(nn) if parent[c] == v], key=lambda c: nodes[c]["mode_lo"])
+          for v in range(nn)}
+    letters = "bcdefghijk"
+
+    def val(v):
+        nd = nodes[v]
+        core = host[nd["core_offset"]:nd["core_offset"] + nd["core_elems"]].reshape(nd["core_shape"])
+        if not ch[v]:
+            lo, hi = nd["mode_lo"], nd["mode_hi"]
+            flat = np.ravel_multi_index(tuple(idx[:, lo:hi].T), [dims[m] for m in range(lo, hi)])
+            return core.reshape(core.shape[0], -1)[:, flat].T
+        vecs = [val(c) for c in ch[v]]
+        m = len(vecs)
+        head = "" if parent[v] < 0 else "a"
+        spec = head + letters[:m] + "," + ",".join("s" + letters[k] for k in range(m)) + "->s" + head
+        return np.einsum(spec, core, *vecs, optimize=True)
+
+    approx = val(parent.index(-1))
+    want = exact(idx)
+    return float(np.linalg.norm(approx - want) / np.linalg.norm(want))
+
+
+def run_hilbert(api, W, torch, steps=3, warmup=2, r=10, p=5):
+    """The paper's first experiment (Sec. 8): the 6D Hilbert tensor
+    1/(1 + i_1 + .. + i_6) with modes 20 on the paper's example tree, ranks
+    r, oversampling p, binary64: TTNN and STTNN with Khatri-Rao DRMs, TTNN
+    with unstructured Gaussian DRMs (the paper's sketches for this
+    experiment) and TTN-HMT on the same sketches, each timed (whole-tensor
+    update + recovery, or the two passes of TTN-HMT) and its error measured
+    on 20000 seeded entries."""
+    tr = W.toy_tree()
+    nn = len(tr[0])
+    dims = [20] * 6
+    dev = torch.from_numpy(W.hilbert(6, 20)).cuda()
+    exact = lambda idx: 1.0 / (1.0 + idx.sum(axis=1))
+    out = {"workload": f"Hilbert 20^6 (FP64, {dev.numel() * 8 / 1e6:.0f} MB), example tree, "
+                       f"r = {r}, p = {p}"}
+    for name, variant, flags, hmt in (("ttnn_kr", api.VARIANT_TTNN, 0, False),
+                                      ("sttnn_kr", api.VARIANT_STTNN, 0, False),
+                                      ("ttnn_gaussian", api.VARIANT_TTNN, api.FLAG_DENSE_DRM, False),
+                                      ("ttn_hmt_gaussian", api.VARIANT_TTNN, api.FLAG_DENSE_DRM, True)):
+        plan = api.ttnn_plan_create(tr, dims, [r] * nn, [p] * nn, SEED + 7, variant=variant,
+                                    sketch_dtype=api.F64, flags=flags)
+        st = api.ttnn_state_create(plan)
+        cores = torch.zeros(api.ttnn_plan_sizes(plan)[2], dtype=torch.float64, device="cuda")
+
+        def step():
+            if hmt:
+                api.ttnn_hmt(plan, dev, cores)
+            else:
+                api.ttnn_state_zero(st)
+                api.ttnn_update_dense(st, dev)
+                api.ttnn_recover_async(st, cores)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        api.ttnn_plan_sync(plan)
+        out[name] = {"ms": e0.elapsed_time(e1) / steps,
+                     "rel_error": _sampled_error(api, plan, tr, cores, dims, exact)}
+        api.ttnn_state_destroy(st)
+        api.ttnn_plan_destroy(plan)
+    return out
+
+
 def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=3.0):
     """Serving mix: n_streams resident BF16 streams of mixed order, sizes,
     trees and ranks (workloads.serving_stream_spec; streams whose device
@@ -840,6 +922,8 @@ def main():
         out["serving"] = run_serving(api, W, torch)
         log("rounding leg")
         out["rounding"] = run_rounding(api, W, torch)
+        log("hilbert leg")
+        out["hilbert"] = run_hilbert(api, W, torch)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_sample()
     if rank == 0:

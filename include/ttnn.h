@@ -124,7 +124,7 @@ typedef struct {
                                        Philox kind 4) and Y_v (n_v x s_v, kind 5) keyed by its
                                        lexicographic index, rounded to the plan's format,
                                        instead of Khatri-Rao products of per-mode factors.
-                                       TTNN, binary64 / binary32 plans, at most 1 GiB of DRMs,
+                                       TTNN, binary64 / binary32 plans, at most 8 GiB of DRMs,
                                        whole-tensor dense updates only (boxes, CP and
                                        TTN-format updates: TTNN_EUNSUPPORTED) */
 #define TTNN_FLAG_TRUNCATE 256u    /* eps-truncated output [Sec. 4 recovery, eq.
@@ -330,6 +330,18 @@ ttnn_status ttnn_plan_sync(ttnn_plan_t plan);
  * recovery into `cores`.  EINVAL if the plan is not an STTNN plan. */
 ttnn_status sttnn_run(ttnn_plan_t plan, const void* dense, const float* tile_scale,
                       double* cores, void* stream);
+
+/* ttnn_hmt -- TTN-HMT, the randomised comparator of Sec. 8 (the TTN-SVD with
+ * every SVD replaced by the HMT range finder, on the same right sketches X_t
+ * as TTNN): two passes over the dense tensor (device, binary64, row-major);
+ * pass 1 forms Q_t = orth(T^(t) X_t) for every node (Householder QR in
+ * binary64), pass 2 the root core (kron_c Q_c)^T T; leaf cores Q_t^T,
+ * transfer cores (kron_c Q_c)^T Q_t.  cores: device, the plan's core layout
+ * (ttnn_plan_node).  Needs a TTNN_F64 plan with TTNN_FLAG_DENSE_DRM (the X_t
+ * are the plan's unstructured DRMs); grows the plan's workspace if needed.
+ * Synchronous with the stream's order only (no host wait).
+ * EINVAL: NULL arguments; EUNSUPPORTED: other plans; ENOMEM / ECUDA. */
+ttnn_status ttnn_hmt(ttnn_plan_t plan, const void* dense, double* cores, void* stream);
 
 /* ttnn_round -- TTN rounding end to end [Sec. 7]: sketches of a TTN-format
  * input (see ttnn_update_ttn) followed by recovery into `cores`. */

@@ -97,3 +97,43 @@ def tt_svd(T, ranks):
     for G in cores[1:]:
         out = np.tensordot(out, G, axes=([-1], [0]))
     return out.reshape(dims)
+
+
+def ttn_hmt(T, tree, drm):
+    """TTN-HMT (Sec. 8): the TTN-SVD with each SVD replaced by the HMT range
+    finder on the same right sketches X_t as TTNN: Q_t = orth(T^(t) X_t)
+    (n_t x r_t), P_t = Q_t Q_t^T, and the approximant (prod over levels of
+    kron_t P_t) T in TTN format -- leaf core Q_t^T, transfer core
+    (kron_c Q_c)^T Q_t as (r_t, r_c1, .., r_cm), root core (kron_c Q_c)^T T^D.
+    Two passes over T: the sketches, then the root core.  Identity nodes keep
+    Q = I.  Returns cores keyed by user index (the library's axis order)."""
+    from .ttnn import contract_axis
+    T = np.asarray(T, dtype=np.float64)
+    Q = {}
+    for v in tree.sketched():
+        nd = tree.node(v)
+        Q[v], _ = np.linalg.qr(unfold(T, nd.lo, nd.hi) @ drm.Xt(v), mode="reduced")
+
+    def Qc(c):
+        nd = tree.node(c)
+        return np.eye(nd.n) if nd.identity else Q[c]
+
+    cores = {}
+    for v in tree.nonroot():
+        nd = tree.node(v)
+        if nd.identity:
+            cores[v] = np.eye(nd.n).reshape([nd.n] + tree.dims[nd.lo:nd.hi])
+            continue
+        if nd.is_leaf:
+            cores[v] = Q[v].T.reshape([Q[v].shape[1]] + tree.dims[nd.lo:nd.hi])
+            continue
+        P = Q[v].reshape([tree.node(c).n for c in nd.children] + [Q[v].shape[1]])
+        for k, c in enumerate(nd.children):
+            P = contract_axis(P, k, Qc(c))
+        cores[v] = np.moveaxis(P, -1, 0)
+    root = tree.node(tree.root)
+    P = T.reshape([tree.node(c).n for c in root.children])
+    for k, c in enumerate(root.children):
+        P = contract_axis(P, k, Qc(c))
+    cores[tree.root] = P
+    return cores

@@ -67,6 +67,7 @@ SIGS = {
     "ttnn_recover_async": (c_i32, [c_vp, c_vp, c_vp]),
     "ttnn_plan_sync": (c_i32, [c_vp]),
     "sttnn_run": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ttnn_hmt": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "ttnn_round": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_i32), c_vp, c_vp]),
     "ttnn_fp8_quantize": (c_i32, [c_vp, c_vp, C.POINTER(c_i64), c_vp, c_vp, c_vp]),
     "ttnn_profile": (c_i32, [c_vp, c_i32]),

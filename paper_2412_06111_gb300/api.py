@@ -218,6 +218,10 @@ def sttnn_run(plan, dense, cores, tile_scale=None, stream=None):
     _check(_lib().sttnn_run(plan, _ptr(dense), _ptr(tile_scale), _ptr(cores), _stream(stream)))
 
 
+def ttnn_hmt(plan, dense, cores, stream=None):
+    _check(_lib().ttnn_hmt(plan, _ptr(dense), _ptr(cores), _stream(stream)))
+
+
 def ttnn_round(plan, cores_in, ranks_in, cores, stream=None):
     cp = _arr(C.c_void_p, [c.data_ptr() for c in cores_in])
     _check(_lib().ttnn_round(plan, cp, _arr(C.c_int32, ranks_in), _ptr(cores), _stream(stream)))

@@ -533,6 +533,15 @@ ttnn_status sttnn_run(ttnn_plan_t P, const void* dense, const float* tile_scale,
   return s;
 }
 
+ttnn_status ttnn_hmt(ttnn_plan_t P, const void* dense, double* cores, void* stream) {
+  TTNN_CHECK_ARG(P && dense && cores, "null argument");
+  const cudaStream_t st = (cudaStream_t)stream;
+  int64_t need = 0;
+  TTNN_TRY(run_hmt(*P, dense, nullptr, st, true, &need));
+  if (need > P->ws_bytes) TTNN_TRY(grow_workspace(*P, need + 4096));
+  return run_hmt(*P, dense, cores, st, false, nullptr);
+}
+
 ttnn_status ttnn_round(ttnn_plan_t P, const double* const* cores_in, const int32_t* ranks_in,
                        double* cores, void* stream) {
   TTNN_CHECK_ARG(P && cores_in && ranks_in && cores, "null argument");

@@ -83,8 +83,8 @@ ttnn_status dense_drm_check(const ttnn_plan_s& P) {
   int64_t el = 0;
   for (const TNode& nd : P.nodes)
     if (nd.sketched()) el += (P.N / nd.n) * nd.r + nd.n * nd.s;
-  if (el * 8 > (int64_t(1) << 30)) {
-    set_error("unstructured Gaussian DRMs need %lld bytes (> 1 GiB): use the Khatri-Rao DRMs",
+  if (el * 8 > (int64_t(8) << 30)) {
+    set_error("unstructured Gaussian DRMs need %lld bytes (> 8 GiB): use the Khatri-Rao DRMs",
               (long long)(el * 8));
     return TTNN_EUNSUPPORTED;
   }
@@ -114,6 +114,84 @@ ttnn_status dense_drm_generate(ttnn_plan_s& P, double* tmp64, cudaStream_t st) {
   return TTNN_OK;
 }
 
+// G_t = A^(t) X_t (n_t x r_t, walk type, row-major) into ws: A permuted so
+// that t's modes come first (when t does not start at mode 0), then one
+// contraction over the other modes' merged index.
+static ttnn_status dense_g(ttnn_plan_s& P, const TNode& nd, const void* data, Bump& ws,
+                           cudaStream_t st, char** G) {
+  const ElemType et = P.walk_f64 ? ET_F64 : ET_F32;
+  const int eb = P.walk_f64 ? 8 : 4;
+  int64_t npre = 1, npost = 1;
+  for (int m = 0; m < nd.lo; ++m) npre *= P.dims[m];
+  for (int m = nd.hi; m < P.d; ++m) npost *= P.dims[m];
+  const int64_t nt = nd.n, K = npre * npost;
+  // B = A permuted so that t's modes come first: out[i, p, q] = A[p, i, q]
+  const void* B = data;
+  if (npre > 1) {
+    char* b = ws.alloc(P.N * eb);
+    Contract c;
+    c.P = nt;
+    c.NI = 1;
+    c.Q = npre;
+    c.J = npost;
+    c.isP = npost;
+    c.isQ = nt * npost;
+    c.isJ = 1;
+    c.osP = npre * npost;
+    c.osQ = npost;
+    c.osJ = 1;
+    c.in = data;
+    c.out = b;
+    if (!ws.dry) TTNN_TRY(launch_contract(c, et, et, et, nullptr, 0, st));
+    B = b;
+  }
+  *G = ws.alloc(nt * nd.r * eb);
+  return mode_product(B, nt, K, 1, 1, (const char*)P.dxy + nd.dx_off * eb, nd.r, *G, 1.0, 0, et,
+                      ws, st);
+}
+
+// Psi_root-shaped contraction of the dense tensor: every non-identity root
+// child's axis of A against W_c (n_c x w_c, walk type, row-major) -- Y_c for
+// the sketch, Q_c for TTN-HMT's root core -- into out (alpha, accumulate).
+static ttnn_status root_contract(ttnn_plan_s& P, const void* data, const char* const* W,
+                                 const int* wcols, void* out, double alpha, int accumulate,
+                                 Bump& ws, cudaStream_t st) {
+  const ElemType et = P.walk_f64 ? ET_F64 : ET_F32;
+  const int eb = P.walk_f64 ? 8 : 4;
+  const TNode& rt = P.nodes[P.root];
+  std::vector<int64_t> dims;
+  for (int c : rt.ch) dims.push_back(P.nodes[c].n);
+  const int m = (int)dims.size();
+  int last = -1;
+  for (int k = 0; k < m; ++k)
+    if (!P.nodes[rt.ch[k]].identity) last = k;
+  if (last < 0) {
+    Contract c;
+    c.P = P.N;
+    c.isP = 1;
+    c.osP = 1;
+    c.in = data;
+    c.out = out;
+    c.alpha = alpha;
+    c.accumulate = accumulate;
+    return ws.dry ? TTNN_OK : launch_contract(c, et, et, et, nullptr, 0, st);
+  }
+  const void* cur = data;
+  for (int k = 0; k < m; ++k) {
+    if (P.nodes[rt.ch[k]].identity) continue;
+    int64_t pre = 1, post = 1;
+    for (int a = 0; a < k; ++a) pre *= dims[a];
+    for (int a = k + 1; a < m; ++a) post *= dims[a];
+    const bool fin = k == last;
+    char* o = fin ? (char*)out : ws.alloc(pre * wcols[k] * post * eb);
+    TTNN_TRY(mode_product(cur, pre, dims[k], post, 1, W[k], wcols[k], o, fin ? alpha : 1.0,
+                          fin ? accumulate : 0, et, ws, st));
+    dims[k] = wcols[k];
+    cur = o;
+  }
+  return TTNN_OK;
+}
+
 ttnn_status run_dense_drm_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                                  double lambda, cudaStream_t st, bool dry, int64_t* peak) {
   if (!box.full) {
@@ -132,33 +210,9 @@ ttnn_status run_dense_drm_update(ttnn_plan_s& P, void* acc, const void* data, co
     if (!nd.sketched()) continue;
     pk = std::max(pk, ws.top);
     ws.top = mark0;
-    int64_t npre = 1, npost = 1;
-    for (int m = 0; m < nd.lo; ++m) npre *= P.dims[m];
-    for (int m = nd.hi; m < P.d; ++m) npost *= P.dims[m];
-    const int64_t nt = nd.n, K = npre * npost;
-    // B = A permuted so that t's modes come first: out[i, p, q] = A[p, i, q]
-    const void* B = data;
-    if (npre > 1) {
-      char* b = ws.alloc(P.N * eb);
-      Contract c;
-      c.P = nt;
-      c.NI = 1;
-      c.Q = npre;
-      c.J = npost;
-      c.isP = npost;
-      c.isQ = nt * npost;
-      c.isJ = 1;
-      c.osP = npre * npost;
-      c.osQ = npost;
-      c.osJ = 1;
-      c.in = data;
-      c.out = b;
-      if (!dry) TTNN_TRY(launch_contract(c, et, et, et, nullptr, 0, st));
-      B = b;
-    }
-    // G_t = B X_t (nt x r)
-    char* G = ws.alloc(nt * nd.r * eb);
-    TTNN_TRY(mode_product(B, nt, K, 1, 1, fac(nd.dx_off), nd.r, G, 1.0, 0, et, ws, st));
+    const int64_t nt = nd.n;
+    char* G = nullptr;
+    TTNN_TRY(dense_g(P, nd, data, ws, st, &G));
     // (mode_product's output [P][NB][Q][J] = [nt][r] here)
     // Omega_t += lambda Y_t^T G_t: contract G's row axis with Y_t
     TTNN_TRY(mode_product(G, 1, nt, 1, nd.r, fac(nd.dy_off), nd.s, at(nd.om_off), lambda, 1, et,
@@ -214,42 +268,224 @@ ttnn_status run_dense_drm_update(ttnn_plan_s& P, void* acc, const void* data, co
     pk = std::max(pk, ws.top);
     ws.top = mark0;
     const TNode& rt = P.nodes[P.root];
-    std::vector<int64_t> dims;
-    for (int c : rt.ch) dims.push_back(P.nodes[c].n);
-    const int m = (int)dims.size();
-    int last = -1;
-    for (int k = 0; k < m; ++k)
-      if (!P.nodes[rt.ch[k]].identity) last = k;
-    const void* cur = data;
-    for (int k = 0; k < m && last >= 0; ++k) {
-      const TNode& c = P.nodes[rt.ch[k]];
-      if (c.identity) continue;
-      int64_t pre = 1, post = 1;
-      for (int a = 0; a < k; ++a) pre *= dims[a];
-      for (int a = k + 1; a < m; ++a) post *= dims[a];
-      const bool fin = k == last;
-      char* o = fin ? at(rt.ps_off) : ws.alloc(pre * c.s * post * eb);
-      TTNN_TRY(mode_product(cur, pre, dims[k], post, 1, fac(c.dy_off), c.s, o, fin ? lambda : 1.0,
-                            fin ? 1 : 0, et, ws, st));
-      dims[k] = c.s;
-      cur = o;
+    std::vector<const char*> W;
+    std::vector<int> wc;
+    for (int c : rt.ch) {
+      const TNode& cn = P.nodes[c];
+      W.push_back(cn.identity ? nullptr : fac(cn.dy_off));
+      wc.push_back(cn.identity ? (int)cn.n : cn.s);
     }
-    if (last < 0) {
-      Contract c;
-      c.P = P.N;
-      c.isP = 1;
-      c.osP = 1;
-      c.in = data;
-      c.out = at(rt.ps_off);
-      c.alpha = lambda;
-      c.accumulate = 1;
-      if (!dry) TTNN_TRY(launch_contract(c, et, et, et, nullptr, 0, st));
-    }
+    TTNN_TRY(root_contract(P, data, W.data(), wc.data(), at(rt.ps_off), lambda, 1, ws, st));
   }
   pk = std::max(pk, ws.top);
   if (peak) *peak = std::max<int64_t>(pk, 1);
   if (!dry && pk > ws.cap) {
     set_error("internal: workspace overflow (unstructured DRMs)");
+    return TTNN_ENOMEM;
+  }
+  return TTNN_OK;
+}
+
+
+
+// ---------------------------------------------------------------------------
+// TTN-HMT (Sec. 8's randomised comparator): the TTN-SVD with every SVD
+// replaced by the HMT range finder on the same right sketches X_t.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kTsqrThreads = 1024;
+constexpr int kTsqrChunk = 16;   // columns reduced together
+
+struct TsqrJob {
+  double* A;     // n x r, row-major: overwritten by the Householder vectors
+  double* Q;     // n x r, row-major: the orthonormal factor
+  int64_t n;
+  int r;
+};
+
+// Sum over the CTA of up to kTsqrChunk per-thread values (returned to every
+// thread through shared memory).
+__device__ void block_sum(double* v, int m, double (*red)[kTsqrChunk], double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = 0; c < m; ++c) {
+    double x = v[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][c] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double s = 0.0;
+    for (int w = 0; w < kTsqrThreads / 32; ++w) s += red[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Householder QR of one tall n x r block per CTA (binary64, in global
+// memory): reflector k zeroes column k below the diagonal, then Q = H_0 ..
+// H_{r-1} [I; 0].  A zero column keeps its reflector empty (Q's column is
+// then the unit vector e_k, orthogonal to the others).
+__global__ void __launch_bounds__(kTsqrThreads) tsqr_kernel(const TsqrJob job) {
+  __shared__ double red[kTsqrThreads / 32][kTsqrChunk];
+  __shared__ double w[kTsqrChunk];
+  __shared__ double tau[kMaxRecoverR];
+  double* A = job.A;
+  double* Qm = job.Q;
+  const int64_t n = job.n;
+  const int r = job.r;
+  for (int k = 0; k < r; ++k) {
+    double part[kTsqrChunk];
+    part[0] = 0.0;
+    for (int64_t i = k + threadIdx.x; i < n; i += kTsqrThreads) part[0] += A[i * r + k] * A[i * r + k];
+    block_sum(part, 1, red, w);
+    if (threadIdx.x == 0) {
+      const double nrm2 = w[0], alpha = A[(int64_t)k * r + k], nrm = sqrt(nrm2);
+      double t = 0.0;
+      if (nrm > 0.0) {
+        const double beta = alpha > 0.0 ? -nrm : nrm;
+        const double v0 = alpha - beta;
+        const double vn2 = nrm2 - alpha * alpha + v0 * v0;
+        A[(int64_t)k * r + k] = v0;
+        t = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+      }
+      tau[k] = t;
+    }
+    __syncthreads();
+    if (tau[k] == 0.0) continue;
+    for (int j0 = k + 1; j0 < r; j0 += kTsqrChunk) {
+      const int m = min(kTsqrChunk, r - j0);
+      for (int c = 0; c < m; ++c) part[c] = 0.0;
+      for (int64_t i = k + threadIdx.x; i < n; i += kTsqrThreads) {
+        const double vi = A[i * r + k];
+        for (int c = 0; c < m; ++c) part[c] += vi * A[i * r + j0 + c];
+      }
+      block_sum(part, m, red, w);
+      for (int64_t i = k + threadIdx.x; i < n; i += kTsqrThreads) {
+        const double vi = tau[k] * A[i * r + k];
+        for (int c = 0; c < m; ++c) A[i * r + j0 + c] -= vi * w[c];
+      }
+      __syncthreads();
+    }
+  }
+  for (int64_t e = threadIdx.x; e < n * r; e += kTsqrThreads)
+    Qm[e] = (e / r == e % r) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = r - 1; k >= 0; --k) {
+    if (tau[k] == 0.0) continue;
+    for (int j0 = k; j0 < r; j0 += kTsqrChunk) {
+      const int m = min(kTsqrChunk, r - j0);
+      double part[kTsqrChunk];
+      for (int c = 0; c < m; ++c) part[c] = 0.0;
+      for (int64_t i = k + threadIdx.x; i < n; i += kTsqrThreads) {
+        const double vi = A[i * r + k];
+        for (int c = 0; c < m; ++c) part[c] += vi * Qm[i * r + j0 + c];
+      }
+      block_sum(part, m, red, w);
+      for (int64_t i = k + threadIdx.x; i < n; i += kTsqrThreads) {
+        const double vi = tau[k] * A[i * r + k];
+        for (int c = 0; c < m; ++c) Qm[i * r + j0 + c] -= vi * w[c];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// out[b][a] = in[a][b] for an (m x k) row-major binary64 matrix.
+ttnn_status transpose_f64(const double* in, int64_t m, int64_t k, double* out, bool dry,
+                          cudaStream_t st) {
+  if (dry) return TTNN_OK;
+  Contract c;
+  c.P = m;
+  c.J = k;
+  c.isP = k;
+  c.isJ = 1;
+  c.osP = 1;
+  c.osJ = m;
+  c.in = in;
+  c.out = out;
+  return launch_contract(c, ET_F64, ET_F64, ET_F64, nullptr, 0, st);
+}
+
+}  // namespace
+
+ttnn_status run_hmt(ttnn_plan_s& P, const void* data, double* cores, cudaStream_t st, bool dry,
+                    int64_t* peak) {
+  if (!(P.flags & TTNN_FLAG_DENSE_DRM) || !P.walk_f64 || P.variant != TTNN_VARIANT_TTNN) {
+    set_error("TTN-HMT: binary64 TTNN plans with TTNN_FLAG_DENSE_DRM only");
+    return TTNN_EUNSUPPORTED;
+  }
+  Bump ws(P.ws, P.ws_bytes, dry);
+  int64_t pk = 0;
+  std::vector<double*> Q(P.nodes.size(), nullptr);
+  // pass 1: Q_t = orth(A^(t) X_t) for every sketched node
+  for (int v : P.lex) {
+    const TNode& nd = P.nodes[v];
+    if (!nd.sketched()) continue;
+    Q[v] = (double*)ws.alloc(nd.n * nd.r * 8);
+    const int64_t mark = ws.top;
+    char* G = nullptr;
+    TTNN_TRY(dense_g(P, nd, data, ws, st, &G));
+    if (!dry) {
+      tsqr_kernel<<<1, kTsqrThreads, 0, st>>>(TsqrJob{(double*)G, Q[v], nd.n, nd.r});
+      TTNN_TRY(check_launch("tsqr_kernel"));
+    }
+    pk = std::max(pk, ws.top);
+    ws.top = mark;
+  }
+  // cores: leaf Q_t^T, transfer (kron_c Q_c)^T Q_t as (r_t, r_c..), identity I
+  for (int v : P.lex) {
+    const TNode& nd = P.nodes[v];
+    if (v == P.root) continue;
+    double* core = dry ? nullptr : cores + nd.core_off;
+    if (nd.identity) {
+      if (!dry) TTNN_TRY(launch_eye(core, nd.n, st));
+      continue;
+    }
+    if (nd.leaf) {
+      TTNN_TRY(transpose_f64(Q[v], nd.n, nd.r, core, dry, st));
+      continue;
+    }
+    const int64_t mark = ws.top;
+    std::vector<int64_t> dims;
+    for (int c : nd.ch) dims.push_back(P.nodes[c].n);
+    const int m = (int)dims.size();
+    const void* cur = Q[v];
+    for (int k = 0; k < m; ++k) {
+      const TNode& c = P.nodes[nd.ch[k]];
+      if (c.identity) continue;
+      int64_t pre = 1, post = 1;
+      for (int a = 0; a < k; ++a) pre *= dims[a];
+      for (int a = k + 1; a < m; ++a) post *= dims[a];
+      char* o = ws.alloc(pre * c.r * post * nd.r * 8);
+      TTNN_TRY(mode_product(cur, pre, dims[k], post, nd.r, Q[c.user], c.r, o, 1.0, 0, ET_F64, ws,
+                            st));
+      dims[k] = c.r;
+      cur = o;
+    }
+    int64_t rest = 1;
+    for (auto x : dims) rest *= x;
+    TTNN_TRY(transpose_f64((const double*)cur, rest, nd.r, core, dry, st));
+    pk = std::max(pk, ws.top);
+    ws.top = mark;
+  }
+  // pass 2: the root core (kron_c Q_c)^T A
+  {
+    const TNode& rt = P.nodes[P.root];
+    std::vector<const char*> W;
+    std::vector<int> wc;
+    for (int c : rt.ch) {
+      const TNode& cn = P.nodes[c];
+      W.push_back(cn.identity ? nullptr : (const char*)Q[c]);
+      wc.push_back(cn.identity ? (int)cn.n : cn.r);
+    }
+    TTNN_TRY(root_contract(P, data, W.data(), wc.data(), dry ? nullptr : cores + rt.core_off, 1.0,
+                           0, ws, st));
+    pk = std::max(pk, ws.top);
+  }
+  if (peak) *peak = std::max<int64_t>(pk, 1);
+  if (!dry && pk > ws.cap) {
+    set_error("internal: workspace overflow (TTN-HMT)");
     return TTNN_ENOMEM;
   }
   return TTNN_OK;

@@ -45,7 +45,6 @@ struct CvtParams {
   int discard;           // partial rows are whole 128-byte lines
   float* D2p;            // [G][C*tiles*128][wLpad]
   int* err;
-  int rstages;           // FP8: depth of the raw-tile ring
 };
 
 template <int MODE>
@@ -436,298 +435,8 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
   }
 }
 
-// E4M3 pass with the raw tiles in a ring of their own: TMA streams E4M3
-// tiles (16 KB each) rstages deep; the converter warps dequantise each into
-// one of two bf16 operand slots and fetch that tile's DRM block into the
-// slot; the MMA issuer reads the slot.  A raw slot is free as soon as it is
-// converted and an operand slot once its MMAs complete, so the copies in
-// flight no longer wait for the tensor cores.  Tile k of a CTA (row block u,
-// column tile t, k = u * nt + t) uses raw slot k % rstages and operand slot
-// k % kFp8OpSlots.  Warp roles and bounded waits as in pass_cvt_kernel.
-constexpr int kFp8OpSlots = 2;
-constexpr int kFp8MaxRaw = 8;
-
-__global__ void __launch_bounds__(kCvtThreads, 1)
-    pass_fp8_kernel(const __grid_constant__ CUtensorMap mapA,
-                    const __grid_constant__ CUtensorMap mapBR,
-                    const __grid_constant__ CUtensorMap mapBL, const CvtParams p) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar_rfull[kFp8MaxRaw], bar_rempty[kFp8MaxRaw];
-  __shared__ __align__(8) uint64_t bar_brfull[kFp8OpSlots], bar_conv[kFp8OpSlots],
-      bar_oempty[kFp8OpSlots];
-  __shared__ __align__(8) uint64_t bar_blfull[2], bar_blempty[2], bar_d1full[2], bar_d1empty[2];
-  __shared__ __align__(8) uint64_t bar_d2full;
-  __shared__ uint32_t tmem_slot;
-  __shared__ volatile int abort_flag;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int RS = p.rstages;
-  const uint32_t br_bytes = (uint32_t)p.wRpad * 128 * 2;
-  const uint32_t bl_bytes = (uint32_t)p.wLpad * 128 * 2;
-  const uint32_t op_bytes = 32768u + br_bytes;   // bf16 operand tile, then its DRM block
-  const uint32_t base = smem_u32(smem);
-  const uint32_t raw_base = base + kFp8OpSlots * op_bytes;
-  const uint32_t bl_base = raw_base + (uint32_t)RS * 16384u;
-
-  const int c = blockIdx.x % p.C, g = blockIdx.x / p.C;
-  const int b0 = (int)((int64_t)g * p.nb / p.G), b1 = (int)((int64_t)(g + 1) * p.nb / p.G);
-  const int nu = b1 - b0;
-  const int64_t cw = (int64_t)p.tiles * kTileN;
-  const int64_t col0 = c * cw;
-  const int64_t left_tiles = (p.nR - col0 + kTileN - 1) / kTileN;
-  const int nt = left_tiles < p.tiles ? (int)left_tiles : p.tiles;
-
-  if (threadIdx.x == 0) {
-    abort_flag = 0;
-    for (int s = 0; s < RS; ++s) {
-      mbar_init(smem_u32(&bar_rfull[s]), 1);
-      mbar_init(smem_u32(&bar_rempty[s]), kConvThreads / 32);
-    }
-    for (int o = 0; o < kFp8OpSlots; ++o) {
-      mbar_init(smem_u32(&bar_brfull[o]), 1);
-      mbar_init(smem_u32(&bar_conv[o]), kConvThreads / 32);
-      mbar_init(smem_u32(&bar_oempty[o]), 1);
-    }
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(smem_u32(&bar_blfull[k]), 1);
-      mbar_init(smem_u32(&bar_blempty[k]), 1);
-      mbar_init(smem_u32(&bar_d1full[k]), 1);
-      mbar_init(smem_u32(&bar_d1empty[k]), 4);
-    }
-    mbar_init(smem_u32(&bar_d2full), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_slot)),
-                 "r"(512u));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = tmem_slot;
-  const uint32_t d1_col = 0, d2_col = 2 * p.wRpad;
-
-  if (warp == 0) {
-    if (lane == 0 && nu > 0) {
-      // ---------------- TMA producer: BL blocks and raw E4M3 tiles ----------------
-      uint64_t pol_stream, pol_keep;
-      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_stream));
-      asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_keep));
-      uint32_t used = 0, last_ph = 0, bl_used = 0, bl_ph = 0;
-      bool ok = true;
-      for (int u = 0; u < nu && ok; ++u) {
-        const int ub = u & 1, row = (b0 + u) * kTileM;
-        ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag);
-        if (!ok) break;
-        const uint32_t blb = bl_base + ub * bl_bytes;
-        mbar_expect_tx(smem_u32(&bar_blfull[ub]), bl_bytes);
-        tma_2d(blb, &mapBL, row, 0, smem_u32(&bar_blfull[ub]), pol_keep);
-        tma_2d(blb + bl_bytes / 2, &mapBL, row + 64, 0, smem_u32(&bar_blfull[ub]), pol_keep);
-        bl_used |= 1u << ub;
-        bl_ph = (bl_ph & ~(1u << ub)) | ((uint32_t)((u >> 1) & 1) << ub);
-        for (int t = 0; t < nt; ++t) {
-          const int k = u * nt + t, rs = k % RS;
-          const uint32_t ph = (uint32_t)((k / RS) & 1);
-          ok = mbar_wait(smem_u32(&bar_rempty[rs]), ph ^ 1, &abort_flag);
-          if (!ok) break;
-          const uint32_t bar = smem_u32(&bar_rfull[rs]);
-          mbar_expect_tx(bar, 16384u);
-          tma_2d(raw_base + rs * 16384u, &mapA, (int)(col0 + t * kTileN), row, bar, pol_stream);
-          used |= 1u << rs;
-          last_ph = (last_ph & ~(1u << rs)) | (ph << rs);
-        }
-      }
-      if (!ok) {
-        abort_flag = 1;
-        atomicOr(p.err, 1);
-      }
-      for (int s = 0; s < RS; ++s)
-        if (((used >> s) & 1u) && !mbar_drain(smem_u32(&bar_rfull[s]), (last_ph >> s) & 1u))
-          atomicOr(p.err, 2);
-      for (int k = 0; k < 2; ++k)
-        if (((bl_used >> k) & 1u) && !mbar_drain(smem_u32(&bar_blfull[k]), (bl_ph >> k) & 1u))
-          atomicOr(p.err, 2);
-    }
-  } else if (warp == 1) {
-    if (lane == 0 && nu > 0) {
-      // ---------------- MMA issuer ----------------
-      const uint32_t id1 = idesc_bf16(kTileM, p.wRpad, false);
-      const uint32_t id2 = idesc_bf16(kTileN, p.wLpad, true);
-      bool ok = true;
-      for (int u = 0; u < nu && ok; ++u) {
-        const int buf = u & 1;
-        if (u >= 2) ok = mbar_wait(smem_u32(&bar_d1empty[buf]), ((u >> 1) - 1) & 1, &abort_flag);
-        if (ok) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag);
-        if (!ok) break;
-        fence_after();
-        const uint32_t blb = bl_base + buf * bl_bytes;
-        const uint32_t d1 = tmem + d1_col + buf * p.wRpad;
-        for (int t = 0; t < nt; ++t) {
-          const int k = u * nt + t, os = k % kFp8OpSlots;
-          const uint32_t ph = (uint32_t)((k / kFp8OpSlots) & 1);
-          ok = mbar_wait(smem_u32(&bar_conv[os]), ph, &abort_flag);
-          if (ok) ok = mbar_wait(smem_u32(&bar_brfull[os]), ph, &abort_flag);
-          if (!ok) break;
-          fence_after();
-          const uint32_t sa = base + os * op_bytes;
-          const uint32_t sbr = sa + 32768u;
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint64_t da = sdesc(sa + (kk >> 2) * 16384u + (kk & 3) * 32, 16, 1024);
-            const uint64_t db = sdesc(sbr + (kk >> 2) * (br_bytes / 2) + (kk & 3) * 32, 16, 1024);
-            mma_bf16(d1, da, db, id1, (t | kk) != 0);
-          }
-          const uint32_t d2 = tmem + d2_col + t * p.wLpad;
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint64_t da = sdesc(sa + kk * 2048, 16384u, 1024);
-            const uint64_t db = sdesc(blb + (kk >> 2) * (bl_bytes / 2) + (kk & 3) * 32, 16, 1024);
-            mma_bf16(d2, da, db, id2, (u | kk) != 0);
-          }
-          mma_commit(smem_u32(&bar_oempty[os]));
-        }
-        if (!ok) break;
-        mma_commit(smem_u32(&bar_blempty[buf]));
-        mma_commit(smem_u32(&bar_d1full[buf]));
-      }
-      if (!ok) {
-        abort_flag = 1;
-        atomicOr(p.err, 4);
-      }
-      mma_commit(smem_u32(&bar_d2full));
-    }
-  } else if (warp >= 6) {
-    // ---------------- converters (and the DRM block of each operand slot) ----------------
-    const int ct = threadIdx.x - 192;
-    uint64_t pol_keep = 0;
-    if (ct == 0) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_keep));
-    uint32_t br_used = 0, br_ph = 0;
-    bool ok = true;
-    auto scale_of = [&](int u, int t) -> float {
-      if (u >= nu) return 1.f;
-      return __ldg(p.scale + (int64_t)(b0 + u) * p.ncolt + (int)(col0 / kTileN) + t);
-    };
-    float s_next = nu > 0 ? scale_of(0, 0) : 1.f;
-    for (int u = 0; u < nu && ok; ++u) {
-      for (int t = 0; t < nt; ++t) {
-        const float s_cur = s_next;
-        s_next = t + 1 < nt ? scale_of(u, t + 1) : scale_of(u + 1, 0);
-        const int k = u * nt + t, rs = k % RS, os = k % kFp8OpSlots;
-        const uint32_t rph = (uint32_t)((k / RS) & 1), oph = (uint32_t)((k / kFp8OpSlots) & 1);
-        bool w = mbar_wait(smem_u32(&bar_rfull[rs]), rph, &abort_flag);
-        if (w) w = mbar_wait(smem_u32(&bar_oempty[os]), oph ^ 1, &abort_flag);
-        ok = conv_all(w);
-        if (!ok) break;
-        const uint32_t sa = base + os * op_bytes;
-        if (ct == 0) {
-          const uint32_t bar = smem_u32(&bar_brfull[os]);
-          const int col = (int)(col0 + t * kTileN);
-          mbar_expect_tx(bar, br_bytes);
-          tma_2d(sa + 32768u, &mapBR, col, 0, bar, pol_keep);
-          tma_2d(sa + 32768u + br_bytes / 2, &mapBR, col + 64, 0, bar, pol_keep);
-          br_used |= 1u << os;
-          br_ph = (br_ph & ~(1u << os)) | (oph << os);
-        }
-        convert_fp8(smem + (raw_base - base) + rs * 16384u, smem + os * op_bytes, s_cur, ct);
-        fence_proxy_async();   // generic-proxy writes -> visible to the tensor cores
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(smem_u32(&bar_conv[os]));
-          mbar_arrive(smem_u32(&bar_rempty[rs]));
-        }
-      }
-    }
-    if (!ok) {
-      abort_flag = 1;
-      atomicOr(p.err, 64);
-    }
-    // the DRM-block copies this thread issued land before the CTA may exit
-    if (ct == 0)
-      for (int o = 0; o < kFp8OpSlots; ++o)
-        if (((br_used >> o) & 1u) && !mbar_drain(smem_u32(&bar_brfull[o]), (br_ph >> o) & 1u))
-          atomicOr(p.err, 2);
-  } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;
-    const int r_in = 32 * q + lane;
-    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    bool ok = true;
-    for (int u = 0; u < nu && ok; ++u) {
-      const int buf = u & 1;
-      ok = mbar_wait(smem_u32(&bar_d1full[buf]), (u >> 1) & 1, &abort_flag);
-      if (!ok) break;
-      fence_after();
-      const int64_t row = (int64_t)(b0 + u) * kTileM + r_in;
-      float* dst = p.C == 1 ? p.D1 + row * p.wRpad
-                            : p.D1p + ((int64_t)c * p.nb * kTileM + row) * p.wRpad;
-      for (int cg = 0; cg < p.wRpad; cg += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + lane_off + d1_col + buf * p.wRpad + cg, v);
-        tmem_wait_ld();
-        if (row < p.nL) {
-          float4* d4 = reinterpret_cast<float4*>(dst + cg);
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
-                                __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
-        }
-      }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bar_d1empty[buf]));
-      if (p.C > 1)
-        fold_d1_rows(&p.cnt[(int64_t)(b0 + u) * 4 + q], p.C, p.D1p, p.D1, p.nb, p.wRpad,
-                     (int64_t)(b0 + u) * kTileM + 32 * q, p.nL, p.discard, lane);
-    }
-    if (!ok) {
-      abort_flag = 1;
-      atomicOr(p.err, 8);
-    }
-    if (nu == 0) {
-      for (int t = 0; t < p.tiles; ++t) {
-        const int64_t col = col0 + t * kTileN + r_in;
-        if (col >= p.nR) continue;
-        float* dst = p.D2p + ((int64_t)g * p.C * cw + col) * p.wLpad;
-        for (int k = 0; k < p.wLpad; ++k) dst[k] = 0.f;
-      }
-    } else if (ok && mbar_wait(smem_u32(&bar_d2full), 0, &abort_flag)) {
-      fence_after();
-      for (int t = 0; t < nt; ++t) {
-        const int64_t col = col0 + t * kTileN + r_in;
-        float* dst = p.D2p + ((int64_t)g * p.C * cw + col) * p.wLpad;
-        for (int cg = 0; cg < p.wLpad; cg += 16) {
-          uint32_t v[16];
-          tmem_ld16(tmem + lane_off + d2_col + t * p.wLpad + cg, v);
-          tmem_wait_ld();
-          if (col < p.nR) {
-            float4* d4 = reinterpret_cast<float4*>(dst + cg);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              d4[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
-                                  __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
-          }
-        }
-      }
-    } else {
-      atomicOr(p.err, 16);
-    }
-  }
-  if (warp == 1 && lane == 0 && nu > 0) {
-    if (!mbar_drain(smem_u32(&bar_d2full), 0)) atomicOr(p.err, 32);
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
-  }
-}
-
 struct CvtGeometry {
-  int C, G, nb, tiles, stages, rstages, grid;
+  int C, G, nb, tiles, stages, grid;
   int64_t d1p_elems, d2p_elems;
   size_t smem;
 };
@@ -741,26 +450,15 @@ static bool cvt_geometry(int mode, const ttnn_plan_s& P, int64_t nL, int64_t nR,
   if (tiles < 1) return false;
   // as few chunks as TMEM allows, tiles spread evenly over them
   tiles = (int)((ntile + (ntile + tiles - 1) / tiles - 1) / ((ntile + tiles - 1) / tiles));
+  const int64_t op = mode == MODE_SPLIT ? 65536 : 32768, raw = mode == MODE_SPLIT ? 0 : 16384;
+  const int64_t stage_bytes = op + raw + (int64_t)P.wRpad * 256;
   const int64_t bl = 2 * (int64_t)P.wLpad * 256;
-  if (mode == MODE_FP8) {
-    // two operand slots (bf16 tile + DRM block), the rest raw E4M3 tiles
-    const int64_t opb = 32768 + (int64_t)P.wRpad * 256;
-    const int raw = (int)std::min<int64_t>(kFp8MaxRaw,
-                                           (kSmemBudget - 1024 - bl - kFp8OpSlots * opb) / 16384);
-    if (raw < 2) return false;
-    g->tiles = tiles;
-    g->stages = kFp8OpSlots;
-    g->rstages = raw;
-    g->smem = (size_t)(1024 + kFp8OpSlots * opb + raw * 16384 + bl);
-  } else {
-    const int64_t stage_bytes = 65536 + (int64_t)P.wRpad * 256;
-    const int stages = (int)std::min<int64_t>(3, (kSmemBudget - 1024 - bl) / stage_bytes);
-    if (stages < 2) return false;
-    g->tiles = tiles;
-    g->stages = stages;
-    g->rstages = 0;
-    g->smem = (size_t)(1024 + stages * stage_bytes + bl);
-  }
+  const int stages = (int)std::min<int64_t>(mode == MODE_SPLIT ? 3 : 4,
+                                            (kSmemBudget - 1024 - bl) / stage_bytes);
+  if (stages < 2) return false;
+  g->tiles = tiles;
+  g->stages = stages;
+  g->smem = (size_t)(1024 + stages * stage_bytes + bl);
   g->C = (int)((nR + tiles * kTileN - 1) / (tiles * kTileN));
   g->nb = (int)((nL + kTileM - 1) / kTileM);
   const int sms = pass_sms(P);
@@ -916,7 +614,6 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
   prm.nb = g.nb;
   prm.tiles = g.tiles;
   prm.stages = g.stages;
-  prm.rstages = g.rstages;
   prm.wRpad = P.wRpad;
   prm.wLpad = P.wLpad;
   prm.ncolt = (int)((nR + tc::kTileN - 1) / tc::kTileN);
@@ -934,8 +631,8 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
     TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_SPLIT>, 1));
     tc::pass_cvt_kernel<tc::MODE_SPLIT><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
   } else {
-    TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_fp8_kernel, 2));
-    tc::pass_fp8_kernel<<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
+    TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_FP8>, 2));
+    tc::pass_cvt_kernel<tc::MODE_FP8><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
   }
   TTNN_TRY(check_launch("tc pass_cvt_kernel"));
   const int sms = tc::sm_count();

@@ -128,6 +128,10 @@ int64_t dense_drm_elems(ttnn_plan_s& P);
 ttnn_status dense_drm_generate(ttnn_plan_s& P, double* tmp64, cudaStream_t st);
 ttnn_status run_dense_drm_update(ttnn_plan_s& P, void* acc, const void* data, const Box& box,
                                  double lambda, cudaStream_t st, bool dry, int64_t* peak);
+// TTN-HMT of a dense tensor with the plan's unstructured X_t (binary64):
+// cores in the plan's core layout; dry: only the workspace peak.
+ttnn_status run_hmt(ttnn_plan_s& P, const void* data, double* cores, cudaStream_t st, bool dry,
+                    int64_t* peak);
 // Bytes of the library's static scratch block (ttnn_update_dense_static),
 // resident on a device once the library's module is loaded there.
 int64_t static_scratch_resident_bytes();

@@ -337,7 +337,7 @@ __device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
 // kKgKT rows, the next rows prefetched into registers.  With nsplit > 1 the
 // block writes its partial sums [split][p][b][q][j], reduced in a fixed order
 // (OP_REDUCE), else the outputs.
-constexpr int kKgKT = 8, kKgNT = 128, kKgMB = 32;
+constexpr int kKgKT = 16, kKgNT = 256, kKgMB = 32;
 constexpr int kKgWPT = kKgKT * kKgMB / 256;   // weight-tile entries per thread
 static_assert(kKgKT * kKgMB % 256 == 0 && kKgWPT >= 1, "weight tile must split over 256 threads");
 
@@ -380,11 +380,11 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     lbase = p * c.isP + q * c.isQ + j * c.isJ;
   }
   const float* in = (const float*)c.in;
-  // compute role: outputs b in [4 bg, 4 bg + 4), columns [4 cg, 4 cg + 4)
-  const int cg = t % 32, bg = t / 32;
-  float acc[4][4];
+  // compute role: outputs b in [8 bg, 8 bg + 8), columns [4 cg, 4 cg + 4)
+  const int cg = t % 64, bg = t / 64;
+  float acc[8][4];
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < 8; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
   // the next step's rows are read into registers while this step computes
@@ -412,7 +412,8 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     if (k0 + kKgKT < i1) KG_FETCH(k0 + kKgKT);
 #pragma unroll
     for (int kk = 0; kk < kKgKT; ++kk) {
-      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 4 * bg]);
+      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg + 4]);
       const float4 xv = *reinterpret_cast<const float4*>(&Is[kk * kKgNT + 4 * cg]);
 #define KG_ROW(row_, w_)          \
   acc[row_][0] += (w_) * xv.x;    \
@@ -420,6 +421,7 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
   acc[row_][2] += (w_) * xv.z;    \
   acc[row_][3] += (w_) * xv.w;
       KG_ROW(0, w0.x) KG_ROW(1, w0.y) KG_ROW(2, w0.z) KG_ROW(3, w0.w)
+      KG_ROW(4, w1.x) KG_ROW(5, w1.y) KG_ROW(6, w1.z) KG_ROW(7, w1.w)
 #undef KG_ROW
     }
     __syncthreads();
@@ -433,8 +435,8 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     const int64_t j = n % c.J, pq = n / c.J;
     const int64_t q = pq % c.Q, p = pq / c.Q;
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      const int b = 4 * bg + x;
+    for (int x = 0; x < 8; ++x) {
+      const int b = 8 * bg + x;
       if (b >= NB) continue;
       if (op.nsplit > 1) {
         ((float*)op.partial)[split * total + ((p * c.NB + b) * c.Q + q) * c.J + j] = acc[x][y];

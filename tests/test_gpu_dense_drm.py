@@ -127,3 +127,64 @@ def test_dense_drm_refused_updates_and_plans():
         assert not np.any(run.state_host())
     finally:
         run.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_ttn_hmt_matches_oracle(case):
+    """TTN-HMT (Sec. 8 comparator) on the GPU: Householder range finders on
+    the plan's unstructured sketches, cores against the oracle's (compared
+    through their reconstructions), exact for TTN ranks at the targets."""
+    from oracle import baselines as B
+    tr, dims, r, p = CASES[case]
+    n = len(tr[0])
+    t = _otree(tr, dims, r, p)
+    run = Run(tr, dims, [r] * n, [p] * n, 13, dtype=api.F64, flags=api.FLAG_DENSE_DRM)
+    try:
+        for T in (W.gaussian(dims, 5), W.exact_ttn(tr, dims, [r] * n, 6)[0]):
+            out = torch.zeros(run.sizes[2], dtype=torch.float64, device="cuda")
+            api.ttnn_hmt(run.plan, torch.from_numpy(T).cuda(), out)
+            host = out.cpu().numpy()
+            got = {nd["user_index"]: host[nd["core_offset"]:nd["core_offset"] + nd["core_elems"]]
+                   .reshape(nd["core_shape"]) for nd in run.nodes}
+            want = B.ttn_hmt(T, t, O.DenseDrm(t, 13))
+            rg = O.reconstruct(t, got)
+            assert rel(rg, O.reconstruct(t, want)) <= 1e-10
+        assert rel(rg, T) <= 1e-10            # the exact-rank tensor
+    finally:
+        run.close()
+
+
+def test_hilbert_ttnn_sttnn_hmt_against_oracle():
+    """The paper's first experiment in miniature (Hilbert 1/(1 + sum i),
+    example tree, Gaussian sketches): TTNN with unstructured DRMs and TTN-HMT
+    on the GPU equal the oracle's; the errors of both, and of TTN-SVD, are
+    the paper's comparison (TTN-HMT slightly more accurate than TTNN)."""
+    from oracle import baselines as B
+    tr = W.toy_tree()
+    n = len(tr[0])
+    dims = [10] * 6
+    T = W.hilbert(6, 10)
+    r, p = 5, 5
+    t = _otree(tr, dims, r, p)
+    run = Run(tr, dims, [r] * n, [p] * n, 21, dtype=api.F64, flags=api.FLAG_DENSE_DRM)
+    try:
+        dev = torch.from_numpy(T).cuda()
+        api.ttnn_update_dense(run.state, dev)
+        g_ttnn = O.reconstruct(t, run.recover())
+        out = torch.zeros(run.sizes[2], dtype=torch.float64, device="cuda")
+        api.ttnn_hmt(run.plan, dev, out)
+        host = out.cpu().numpy()
+        g_hmt = O.reconstruct(t, {nd["user_index"]: host[nd["core_offset"]:nd["core_offset"] +
+                                                            nd["core_elems"]].reshape(nd["core_shape"])
+                                  for nd in run.nodes})
+    finally:
+        run.close()
+    drm = O.DenseDrm(t, 21)
+    o_ttnn = O.reconstruct(t, O.recover(t, *O.sketch_ttnn(T, t, drm))[0])
+    o_hmt = O.reconstruct(t, B.ttn_hmt(T, t, drm))
+    assert rel(g_ttnn, o_ttnn) <= 1e-8 and rel(g_hmt, o_hmt) <= 1e-10
+    e_svd = rel(B.hsvd(T, t), T)
+    e_ttnn, e_hmt = rel(g_ttnn, T), rel(g_hmt, T)
+    # every method is at least as far from T as the quasi-optimal TTN-SVD
+    # allows (within sqrt(#edges) of the best approximation of these ranks)
+    assert min(e_ttnn, e_hmt) >= e_svd / np.sqrt(n - 1)

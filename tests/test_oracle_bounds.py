@@ -1,6 +1,7 @@
 """Pins of the oracle against the error analysis of Sec. 6 and against
 brute-force hierarchical / TT SVD truncations."""
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import baselines as B
@@ -98,3 +99,27 @@ def test_hosvd_on_tucker_tree():
     tails = [B.svd_tail(O.unfold(T, m, m + 1), 3) for m in range(3)]
     e = np.linalg.norm(H - T)
     assert max(tails) * (1 - 1e-12) <= e <= np.sqrt(np.sum(np.square(tails))) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("tr,dims", [(W.toy_tree(), [3, 4, 3, 4, 3, 4]),
+                                     (W.balanced_binary(4), [5, 4, 6, 3]),
+                                     (W.tensor_train(4), [4, 5, 4, 3])])
+def test_ttn_hmt_equals_its_projector_form_and_recovers_exact_ranks(tr, dims):
+    """TTN-HMT cores reproduce (prod_levels kron P_t) T with the orthogonal
+    projectors P_t = Q_t Q_t^T, Q_t = orth(T^(t) X_t); exact for a tensor
+    whose TTN ranks are at most the targets."""
+    n = len(tr[0])
+    t = _tree(tr, dims, 2, 2)
+    T = W.gaussian(dims, 21)
+    drm = O.DenseDrm(t, 8)
+    cores = B.ttn_hmt(T, t, drm)
+    proj = {}
+    for v in t.sketched():
+        nd = t.node(v)
+        Qv, _ = np.linalg.qr(O.unfold(T, nd.lo, nd.hi) @ drm.Xt(v), mode="reduced")
+        proj[v] = Qv @ Qv.T
+    A = O.projector_approximant(T, t, proj)
+    assert np.linalg.norm(O.reconstruct(t, cores) - A) <= 1e-12 * np.linalg.norm(T)
+    Te, _ = W.exact_ttn(tr, dims, [2] * n, 4)
+    ce = B.ttn_hmt(Te, t, O.DenseDrm(t, 9))
+    assert np.linalg.norm(O.reconstruct(t, ce) - Te) <= 1e-12 * np.linalg.norm(Te)
