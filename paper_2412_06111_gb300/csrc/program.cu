@@ -327,19 +327,26 @@ __device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
   }
 }
 
-// Split-K register-tiled contraction for long reductions into few outputs per
-// column (e.g. the Khatri-Rao contraction of all leading modes of a first-level
-// product at once):  out[p,b,q,j] (+)= alpha * sum_i W(i, b) in[p,i,q,j],
-// b < NB <= 32, with W(i, b) = w[i*wsI + b*wsB] or the Khatri-Rao product of
-// the factors c.kr (nkr > 0).  Columns n = (p, q, j) are tiled kKgNT per
-// block, the reduction index in chunks of op.chunk (block = (tile, split));
-// each thread accumulates 8 (b) x 4 (n) outputs from shared-memory tiles of
-// kKgKT rows, the next rows prefetched into registers.  With nsplit > 1 the
-// block writes its partial sums [split][p][b][q][j], reduced in a fixed order
-// (OP_REDUCE), else the outputs.
+// Split-K register-tiled contraction for long reductions (e.g. the
+// Khatri-Rao contraction of all leading modes of a first-level product at
+// once, or a TTN core against a sketch block):
+//   out[p,b,q,j] (+)= alpha * sum_i W(i, b) in[p,i,q,j],
+// with W(i, b) = w[i*wsI + b*wsB] or the Khatri-Rao product of the factors
+// c.kr (nkr > 0).  Columns n = (p, q, j) are tiled kKgNT per block, the
+// outputs b in groups of kKgMB (op.BG groups) and the reduction index in
+// chunks of op.chunk: block = (tile, b group, split).  Each thread
+// accumulates 8 (b) x 4 (n) outputs from shared-memory tiles of kKgKT rows,
+// the next rows prefetched into registers.  Tiles are read column-wise
+// (consecutive threads, consecutive columns: contiguous j) or, with op.CG = 1
+// (J = Q = 1 and a contiguous reduction index), row-wise (16 consecutive i of
+// a column per 16 threads).  With nsplit > 1 the block writes its partial
+// sums [split][p][b][q][j], reduced in a fixed order (OP_REDUCE), else the
+// outputs.
 constexpr int kKgKT = 16, kKgNT = 256, kKgMB = 32;
+constexpr int kKgLd = kKgNT + 4;               // padded tile row (row-wise stores: 2-way banks)
 constexpr int kKgWPT = kKgKT * kKgMB / 256;   // weight-tile entries per thread
 static_assert(kKgKT * kKgMB % 256 == 0 && kKgWPT >= 1, "weight tile must split over 256 threads");
+static_assert(kKgKT == 16 && kKgNT == 256, "row-wise tile loads assume 16 x 256 tiles");
 
 // W(i, b) of a split-K contraction; i < 2^31 (the recorder checks).
 __device__ __forceinline__ float kg_weight(const Contract& c, int64_t i, int b) {
@@ -358,28 +365,42 @@ __device__ __forceinline__ float kg_weight(const Contract& c, int64_t i, int b) 
   return v;
 }
 
+template <typename I>
 __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
   const Contract& c = op.c;
   float* Ws = (float*)smem;                       // [kKgKT][kKgMB]
-  float* Is = Ws + kKgKT * kKgMB;                 // [kKgKT][kKgNT]
+  float* Is = Ws + kKgKT * kKgMB;                 // [kKgKT][kKgLd]
   const int t = threadIdx.x;
   const int64_t ncols = c.P * c.Q * c.J;
   const int64_t ntile = (ncols + kKgNT - 1) / kKgNT;
-  const int64_t tile = blk % ntile, split = blk / ntile;
+  const int nbg = op.BG > 0 ? op.BG : 1;
+  const int64_t tile = blk % ntile, rest = blk / ntile;
+  const int b0 = (int)(rest % nbg) * kKgMB;
+  const int64_t split = rest / nbg;
   const int64_t i0 = split * op.chunk;
   const int64_t i1 = min(c.NI, i0 + op.chunk);
   const int NB = (int)c.NB;
-  // load role: column t % kKgNT of the tile, rows t / kKgNT + 2 u of a step
-  const int lc = t % kKgNT, lr = t / kKgNT;
-  const int64_t ln = tile * kKgNT + lc;
-  const bool lval = ln < ncols;
-  int64_t lbase = 0;
-  if (lval) {
-    const int64_t j = ln % c.J, pq = ln / c.J;
-    const int64_t q = pq % c.Q, p = pq / c.Q;
-    lbase = p * c.isP + q * c.isQ + j * c.isJ;
-  }
+  const int NBg = min(kKgMB, NB - b0);
+  const bool rows = op.CG == 1;
+  // load role, column-wise: column t of the tile, all kKgKT rows of a step;
+  // row-wise: row t % 16 of columns t / 16 + 16 u
+  const int lc = rows ? t / kKgKT : t, lr = rows ? t % kKgKT : 0;
   const float* in = (const float*)c.in;
+  int64_t lbase = 0;
+  bool lval = false;
+  if (rows) {
+    lbase = (tile * kKgNT + lc) * c.isP;
+  } else {
+    const I ln = (I)(tile * kKgNT + lc);
+    lval = (int64_t)ln < ncols;
+    if (lval) {
+      const I j = ln % (I)c.J, pq = ln / (I)c.J;
+      const I q = pq % (I)c.Q, p = pq / (I)c.Q;
+      lbase = (int64_t)p * c.isP + (int64_t)q * c.isQ + (int64_t)j * c.isJ;
+    }
+  }
+  const int64_t rstep = (int64_t)(kKgNT / kKgKT) * c.isP;   // row-wise: 16 columns on
+  const int64_t rcols = ncols - tile * kKgNT;                // row-wise: valid columns
   // compute role: outputs b in [8 bg, 8 bg + 8), columns [4 cg, 4 cg + 4)
   const int cg = t % 64, bg = t / 64;
   float acc[8][4];
@@ -388,24 +409,33 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
 #pragma unroll
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
   // the next step's rows are read into registers while this step computes
-  constexpr int kRows = kKgKT * kKgNT / 256;      // input rows each thread loads per step
+  constexpr int kRows = kKgKT * kKgNT / 256;      // tile entries each thread loads per step
   float ri[kRows], rw[kKgWPT];
-#define KG_FETCH(k0_)                                                         \
-  {                                                                           \
-    const int nk_ = (int)min((int64_t)kKgKT, i1 - (k0_));                     \
-    _Pragma("unroll") for (int u = 0; u < kRows; ++u) {                      \
-      const int kk_ = lr + u * (256 / kKgNT);                                 \
-      ri[u] = (lval && kk_ < nk_) ? in[lbase + ((k0_) + kk_) * c.isI] : 0.f;  \
-    }                                                                         \
-    _Pragma("unroll") for (int h = 0; h < kKgWPT; ++h) {                     \
-      const int e_ = t + h * 256, kk_ = e_ / kKgMB, b_ = e_ % kKgMB;          \
-      rw[h] = (b_ < NB && kk_ < nk_) ? kg_weight(c, (k0_) + kk_, b_) : 0.f;   \
-    }                                                                         \
+#define KG_FETCH(k0_)                                                              \
+  {                                                                                \
+    const int nk_ = (int)min((int64_t)kKgKT, i1 - (k0_));                          \
+    if (rows) {                                                                    \
+      _Pragma("unroll") for (int u = 0; u < kRows; ++u)                            \
+        ri[u] = (lr < nk_ && lc + u * (kKgNT / kKgKT) < rcols)                     \
+                    ? in[lbase + u * rstep + (k0_) + lr] : 0.f;                    \
+    } else {                                                                       \
+      _Pragma("unroll") for (int u = 0; u < kRows; ++u)                            \
+        ri[u] = (lval && u < nk_) ? in[lbase + ((k0_) + u) * c.isI] : 0.f;         \
+    }                                                                              \
+    _Pragma("unroll") for (int h = 0; h < kKgWPT; ++h) {                          \
+      const int e_ = t + h * 256, kk_ = e_ / kKgMB, b_ = e_ % kKgMB;               \
+      rw[h] = (b_ < NBg && kk_ < nk_) ? kg_weight(c, (k0_) + kk_, b0 + b_) : 0.f;  \
+    }                                                                              \
   }
   if (i0 < i1) KG_FETCH(i0);
   for (int64_t k0 = i0; k0 < i1; k0 += kKgKT) {
+    if (rows) {
 #pragma unroll
-    for (int u = 0; u < kRows; ++u) Is[(lr + u * (256 / kKgNT)) * kKgNT + lc] = ri[u];
+      for (int u = 0; u < kRows; ++u) Is[lr * kKgLd + lc + u * (kKgNT / kKgKT)] = ri[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) Is[u * kKgLd + lc] = ri[u];
+    }
 #pragma unroll
     for (int h = 0; h < kKgWPT; ++h) Ws[t + h * 256] = rw[h];
     __syncthreads();
@@ -414,7 +444,7 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     for (int kk = 0; kk < kKgKT; ++kk) {
       const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg]);
       const float4 w1 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg + 4]);
-      const float4 xv = *reinterpret_cast<const float4*>(&Is[kk * kKgNT + 4 * cg]);
+      const float4 xv = *reinterpret_cast<const float4*>(&Is[kk * kKgLd + 4 * cg]);
 #define KG_ROW(row_, w_)          \
   acc[row_][0] += (w_) * xv.x;    \
   acc[row_][1] += (w_) * xv.y;    \
@@ -427,23 +457,26 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
     __syncthreads();
   }
 #undef KG_FETCH
-  const int64_t total = c.P * c.NB * c.Q * c.J;
 #pragma unroll
   for (int y = 0; y < 4; ++y) {
-    const int64_t n = tile * kKgNT + 4 * cg + y;
-    if (n >= ncols) continue;
-    const int64_t j = n % c.J, pq = n / c.J;
-    const int64_t q = pq % c.Q, p = pq / c.Q;
+    const I n = (I)(tile * kKgNT) + (I)(4 * cg + y);
+    if ((int64_t)n >= ncols) continue;
+    const I j = n % (I)c.J, pq = n / (I)c.J;
+    const I q = pq % (I)c.Q, p = pq / (I)c.Q;
+    // partial [split][p][b][q][j] or the output, at b = b0 + 8 bg
+    const int64_t pbase = ((int64_t)split * c.P + p) * c.NB * c.Q * c.J + (int64_t)q * c.J + j;
+    const int64_t pstep = c.Q * c.J;
+    float* o = (float*)c.out + (int64_t)p * c.osP + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
-      const int b = 8 * bg + x;
-      if (b >= NB) continue;
+      const int b = b0 + 8 * bg + x;
+      if (8 * bg + x >= NBg) continue;
       if (op.nsplit > 1) {
-        ((float*)op.partial)[split * total + ((p * c.NB + b) * c.Q + q) * c.J + j] = acc[x][y];
+        ((float*)op.partial)[pbase + (int64_t)b * pstep] = acc[x][y];
       } else {
-        float* o = (float*)c.out + p * c.osP + (int64_t)b * c.osB + q * c.osQ + j * c.osJ;
+        float* ob = o + (int64_t)b * c.osB;
         const float v = (float)c.alpha * acc[x][y];
-        *o = c.accumulate ? *o + v : v;
+        *ob = c.accumulate ? *ob + v : v;
       }
     }
   }
@@ -620,7 +653,7 @@ __device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned 
       dev_outer(op, blk);
       break;
     case OP_KGEMM:
-      dev_kgemm(op, blk, dsm);
+      dev_kgemm<I>(op, blk, dsm);
       break;
     default:
       break;
@@ -683,17 +716,29 @@ int64_t plan_contract(Op& op) {
     op.blocks = 0;
     return 0;
   }
-  if (c.nkr > 0) {
-    // Khatri-Rao weights exist only in the split-K tiled form (binary32,
-    // NB <= kKgMB, weights independent of p, q, j: the recorder checks)
+  // split-K tiled form: b groups of kKgMB, long reductions split until the
+  // blocks fill the GPU twice over (at least 64 reduction rows each)
+  auto kgemm = [&]() -> int64_t {
     const int64_t ntile = ceil_div(c.P * c.Q * c.J, (int64_t)kKgNT);
+    const int64_t nbg = ceil_div(c.NB, (int64_t)kKgMB);
     const int64_t want = (int64_t)exec_sms() * 2;
-    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, ntile), c.NI / 64));
+    // short reductions stay whole (the partial sums and their reduction
+    // would cost more than the extra blocks gain)
+    int64_t ns = c.NI < 1024 ? 1
+                 : std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, ntile * nbg), c.NI / 64));
     op.chunk = round_up(ceil_div(c.NI, ns), (int64_t)kKgKT);
     op.nsplit = (int)ceil_div(c.NI, op.chunk);
     op.kind = OP_KGEMM;
-    op.blocks = ntile * op.nsplit;
+    op.BG = (int)nbg;
+    // row-wise tile loads: one column per (p), contiguous reduction index
+    op.CG = (c.J == 1 && c.Q == 1 && c.isI == 1 && c.P > 1) ? 1 : 0;
+    op.blocks = ntile * nbg * op.nsplit;
     return op.nsplit > 1 ? total * op.nsplit : 0;
+  };
+  if (c.nkr > 0) {
+    // Khatri-Rao weights exist only in the split-K tiled form (binary32,
+    // NB <= kKgMB, weights independent of p, q, j: the recorder checks)
+    return kgemm();
   }
   // long reductions with few outputs: split-K through shared-memory tiles
   if (c.w && c.wsQ == 0 && c.wsJ == 0 && c.wsP == 0 && op.tin == ET_F32 && op.tw == ET_F32 &&
@@ -712,6 +757,12 @@ int64_t plan_contract(Op& op) {
   // outputs: for small ops that leaves most SMs idle while a few blocks run
   // long; there one lane group per output spreads the work instead
   const int64_t want = (int64_t)exec_sms() * 1024;   // threads that keep the GPU busy
+  // binary32 mode products with reductions longer than the weight-stationary
+  // form holds (e.g. a rank-200 TTN core against a sketch block) take the
+  // split-K tiled form
+  if (total >= want / 4 && c.w && c.wsQ == 0 && c.wsJ == 0 && c.wsP == 0 && c.NI > kWsMaxNI &&
+      c.NI < (int64_t(1) << 31) && op.tin == ET_F32 && op.tw == ET_F32 && op.tout == ET_F32)
+    return kgemm();
   if (total >= want / 4 && mp_tiling(op)) return 0;
   int g = 1;
   while (g < 32 && total * g < want && c.NI >= 8 * g) g <<= 1;
