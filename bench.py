@@ -218,7 +218,13 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     # the passes leave a few SMs free for the recovery that overlaps them
     plan = api.ttnn_plan_create(tr, dims, [RANK] * n, [OVERSAMPLE] * n, SEED, variant=variant,
                                 sketch_dtype=dtype, flags=api.FLAG_RESERVE_SMS)
-    main = torch.cuda.current_stream()
+    # the update path (pass, walk) on a high-priority stream: when its blocks
+    # and the overlapping recovery's wait for the same SMs, the update's go
+    # first (the recovery has a whole step of slack)
+    base = torch.cuda.current_stream()
+    main = torch.cuda.Stream(priority=-1)
+    main.wait_stream(base)
+    torch.cuda.set_stream(main)
     side = torch.cuda.Stream()
     upd_done = torch.cuda.Event()
     rec_done = [torch.cuda.Event(), torch.cuda.Event()]
@@ -299,6 +305,8 @@ def run_form(api, W, dtype, variant, steps, warmup, ws, torch, data, quantize=Fa
     for st in states:
         api.ttnn_state_destroy(st)
     api.ttnn_plan_destroy(plan)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(base)
     lat.sort()
     return {"ms_per_step": ms, "launches": launches, "tc_passes": passes[0], "simt_passes": passes[1],
             "pass_ms": prof[0][0] / max(prof[0][1], 1), "walk_ms": prof[1][0] / max(prof[1][1], 1),

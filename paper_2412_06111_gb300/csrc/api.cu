@@ -57,6 +57,7 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->sideR);
   cudaFree(P->sideL);
   cudaFree(P->yW);
+  cudaFree(P->xWo);
   cudaFree(P->dxy);
   cudaFree(P->ws);
   cudaFree(P->ws_rec);
@@ -220,9 +221,15 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
       if ((s = make_side(P, fb, 1, P.sideL, nL, st))) return fail(s);
     }
     const TNode& yc = P.nodes[P.ychild];
-    if (!yc.identity) {
+    // (a Y child whose Omega goes through D2 needs its block only for
+    // rank-one boxes: generated then)
+    if (!yc.identity && !omega_via_d2(P, nL, nR)) {
       if ((s = palloc(&P.yW, (int64_t)yc.s * yc.n * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
       if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
+    }
+    if (omega_via_d2(P, nL, nR)) {
+      if ((s = palloc(&P.xWo, (int64_t)P.rXL * nR * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
+      if ((s = make_side_xo(P, fb, P.xWo, nR, st))) return fail(s);
     }
   }
   // workspaces: updates -- the larger of a whole-tensor update (cached DRM

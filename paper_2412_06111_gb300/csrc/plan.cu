@@ -432,6 +432,14 @@ struct Ctx {
   // rank-one box with the Y child on the matrix-vector side: Y^T m, the Y
   // child's Omega before its broadcast column factor (walk type, s entries)
   const char* yom = nullptr;
+  // Y child over the L modes, whole 2-D box: Omega_y = Y^T (M X) = (M^T Y)^T X
+  // as a reduction over the R index: d2y = M^T Y (the Y columns of D2, row
+  // stride d2y_ld, nRo rows) and xo = the stored X block of the L side over
+  // the R modes (walk type, [rXL][nRo])
+  const char* d2y = nullptr;
+  int64_t d2y_ld = 0;
+  const char* xo = nullptr;
+  int64_t nRo = 0;
 };
 
 static int find_ax(const View& v, int kind, int id) {
@@ -959,6 +967,7 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda,
       Ax nax{AX_SK, v, nd.s, 0};
       TTNN_TRY(contract_view(C, Gt, k, facY(C, nd.hi - 1), P.smax, 1, -1, &nax, &z));
     }
+    std::vector<int64_t> om_os = {(int64_t)nd.r, 1};   // Omega [s][r] in the state
     if (v == P.ychild && C.yom && Gt.ax.back().bc > 0) {
       // rank-one box: G = m (x) x, so Omega = (Y^T m) (x) x, and Y^T m is
       // the Y part of the pass's matrix-vector product
@@ -966,6 +975,20 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda,
       om.ax = {Ax{AX_SK, v, nd.s, 0}, Gt.ax.back()};
       om.ld = 1;
       om.sc = Gt.sc;
+    } else if (v == P.ychild && C.d2y) {
+      // reduction over the (shorter) R index: Omega[b][j] = sum_i D2[i][b] X[j][i]
+      // (axes j, b: written transposed); whole 2-D boxes carry no scales
+      if (!Gt.sc.empty()) {
+        set_error("internal: scaled Y-child Omega through D2");
+        return TTNN_EUNSUPPORTED;
+      }
+      View h;
+      h.ptr = (char*)C.d2y;
+      h.ax = {Ax{AX_MODE, P.Rlo, C.nRo, 0}, Ax{AX_SK, v, nd.s, 0}};
+      h.ld = C.d2y_ld;
+      Ax nax{AX_J, -1, nd.r, 0};
+      TTNN_TRY(contract_view(C, h, 0, C.xo, 1, C.nRo, -1, &nax, &om));
+      om_os = {1, (int64_t)nd.r};
     } else if (v == P.ychild) {
       // Y of the pass-side root child is the stored (rounded) block
       View mg = Gt;
@@ -979,7 +1002,7 @@ static ttnn_status walk(Ctx& C, void* acc, int v, const View& G, double lambda,
     } else {
       TTNN_TRY(y_chain(C, Gt, v, nd.lo, nd.hi, nd.s, &om));
     }
-    TTNN_TRY(scatter_into(C, om, state_at(C, acc, nd.om_off), {(int64_t)nd.r, 1}, lambda));
+    TTNN_TRY(scatter_into(C, om, state_at(C, acc, nd.om_off), om_os, lambda));
     if (nd.leaf) {
       std::vector<int64_t> os(Gt.ax.size(), 1);
       for (int a = 0; a + 1 < (int)Gt.ax.size(); ++a) {
@@ -1106,6 +1129,27 @@ ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, 
   return launch_side(s, out, st);
 }
 
+// Walk-type copy of the pass X block of the L side (rows over the R modes of
+// the box, the rXL columns of B_R): the X factor of Omega for an L-side Y
+// child taken through D2.
+ttnn_status make_side_xo(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st) {
+  SideSpec s;
+  side_spec_common(P, box, P.Rlo, P.Rhi, s);
+  s.x_cols = P.rXL;
+  s.y_cols = 0;
+  s.y_kind = 0;
+  s.total_cols = P.rXL;
+  s.store = P.walk_f64 ? 0 : 1;
+  s.ld = ld;
+  return launch_side(s, out, st);
+}
+
+bool omega_via_d2(const ttnn_plan_s& P, int64_t nL, int64_t nR) {
+  const TNode& yc = P.nodes[P.ychild];
+  return P.yside == 1 && !P.walk_f64 && !yc.identity && P.wYL > 0 && P.rXL > 0 &&
+         yc.r <= P.rXL && nR * 2 <= nL && !(P.flags & TTNN_FLAG_DENSE_DRM);
+}
+
 ttnn_status UpdateBatch::launch(cudaStream_t st) {
   if (!gathers.empty()) TTNN_TRY(launch_side_gather_batch(gathers.data(), (int)gathers.size(), st));
   for (auto& p : passes) TTNN_TRY(p(st));
@@ -1229,7 +1273,10 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   // rank-one box whose Y child lies on the matrix-vector side: the walk takes
   // the Y child's Omega from that product and needs no Y block
   const bool y_from_gemv = (r1 == 1 && P.yside == 1) || (r1 == 2 && P.yside == 0);
-  if (!P.nodes[P.ychild].identity && !y_from_gemv) {
+  // whole 2-D boxes with an L-side Y child take its Omega through D2 and
+  // need no Y block copy
+  const bool y_via_d2 = r1 == 0 && omega_via_d2(P, nL, nR);
+  if (!P.nodes[P.ychild].identity && !y_from_gemv && !y_via_d2) {
     const TNode& yc = P.nodes[P.ychild];
     int64_t ny = 1;
     for (int m = yc.lo; m < yc.hi; ++m) ny *= box.ext[m];
@@ -1259,6 +1306,18 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   const char* Mw = r1 && r1_copy ? ws.alloc(r1_rows * eb) : (const char*)data;
   const char* bw = r1 && P.side_store == 2 ? ws.alloc((int64_t)r1_bpad * eb) : (const char*)r1_brow;
   if (y_from_gemv) C.yom = r1 == 1 ? D2 + (int64_t)P.rXR * eb : D1 + (int64_t)P.rXL * eb;
+  if (y_via_d2) {
+    C.d2y = D2 + (int64_t)P.rXR * eb;
+    C.d2y_ld = P.wLpad;
+    C.nRo = nR;
+    if (box.full && P.xWo) {
+      C.xo = (const char*)P.xWo;
+    } else {
+      char* b = ws.alloc((int64_t)P.rXL * nR * eb);
+      if (!dry) TTNN_TRY(make_side_xo(P, box, b, nR, st));
+      C.xo = b;
+    }
+  }
   cudaEvent_t ev0 = dry ? nullptr : prof_event(P, st);
   // the pass's own temporaries are released right after it and are not
   // program buffers: keep them out of the dependency registry

@@ -65,6 +65,7 @@ struct ttnn_plan_s {
   void* sideR = nullptr;        // cached full-size side blocks (pass storage)
   void* sideL = nullptr;
   void* yW = nullptr;           // walk-type copy of the pass Y block (full box)
+  void* xWo = nullptr;          // walk-type copy of the L side's X block over the R modes (full box)
   void* dxy = nullptr;          // unstructured DRMs of every node, walk type (TTNN_FLAG_DENSE_DRM)
   char* ws = nullptr;
   int64_t ws_bytes = 0;
@@ -167,6 +168,10 @@ ttnn_status launch_quantize_fp8(const float* src, int64_t rows, int64_t cols, ui
 // to *defer instead of launched (blocks that need computing are launched).
 ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
                       cudaStream_t st, std::vector<GatherJob>* defer = nullptr);
+ttnn_status make_side_xo(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st);
+// Omega of an L-side Y child is taken through D2 (a reduction over the R
+// index) for whole 2-D boxes of nL x nR
+bool omega_via_d2(const ttnn_plan_s& P, int64_t nL, int64_t nR);
 ttnn_status make_side_yw(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st,
                          std::vector<GatherJob>* defer = nullptr);
 // records an event on `st` if profiling is on (returns nullptr otherwise)
