@@ -16,6 +16,7 @@ measured the same way and reported beside it.
 on a bounded sample of the same workload on the host cores.
 """
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -654,13 +655,57 @@ def run_hilbert(api, W, torch, steps=3, warmup=2, r=10, p=5):
     return out
 
 
-def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=3.0):
+SERVE_QUEUE = 1024     # requests outstanding in the server (back-pressure beyond)
+SERVE_STREAM_QUEUE = 4   # ... and per stream
+EBUSY = 6
+
+
+def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=60.0):
     """Serving mix: n_streams resident BF16 streams of mixed order, sizes,
     trees and ranks (workloads.serving_stream_spec; streams whose device
     footprint exceeds 512 MiB are redrawn), fed a Poisson stream of N(0,1)
-    slices (one mode fixed at a uniform index) at `rate`/s for `seconds`."""
+    slices (one mode fixed at a uniform index) at `rate`/s for `seconds`.
+    The server holds at most SERVE_QUEUE outstanding requests, and
+    SERVE_STREAM_QUEUE per stream: a submit beyond either is refused (EBUSY)
+    and the client waits for that stream's oldest outstanding ticket (or the
+    busiest stream's) before retrying, which bounds the latency at full load."""
     rng = np.random.default_rng(1004)
-    srv = api.ttnn_server_create(160 << 30, max_batch=64, workers=8)
+    srv = api.ttnn_server_create(160 << 30, max_batch=64, queue_capacity=SERVE_QUEUE, workers=8,
+                                 stream_queue_capacity=SERVE_STREAM_QUEUE)
+    outstanding = collections.defaultdict(collections.deque)   # stream -> tickets in order
+    stats = {"throttled": 0, "throttle_s": 0.0, "failed": 0, "errors": {}}
+
+    def finish(t):
+        st = api.ttnn_server_wait(srv, t, 120_000_000)
+        if st != 0:
+            stats["failed"] += 1
+            key = f"{st}: {api.last_error_message()}"
+            stats["errors"][key] = stats["errors"].get(key, 0) + 1
+
+    def submit(sid, dm, mu, idx):
+        off = [0] * len(dm)
+        ext = list(dm)
+        off[mu], ext[mu] = idx, 1
+        while True:
+            try:
+                outstanding[sid].append(api.ttnn_server_submit(srv, sid, buf, off, ext))
+                return
+            except api.TtnnError as e:
+                if e.status != EBUSY:
+                    raise
+                q = outstanding[sid] if outstanding[sid] else max(outstanding.values(), key=len)
+                if not q:
+                    raise
+                stats["throttled"] += 1
+                tw = time.perf_counter()
+                finish(q.popleft())
+                stats["throttle_s"] += time.perf_counter() - tw
+
+    def drain():
+        for q in outstanding.values():
+            while q:
+                finish(q.popleft())
+
     sids, dims_of = [], []
     t_open = time.perf_counter()
     tries = 0
@@ -693,46 +738,31 @@ def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=3.0):
     for t in tickets:
         api.ttnn_server_wait(srv, t, 60_000_000)
     api.ttnn_server_stats(srv, reset=True)
-    tickets = []
     late = 0
     t0 = time.perf_counter()
-    for (ta, s, mu, idx) in arrivals:
+    for (ta, s_, mu, idx) in arrivals:
         while True:
             now = time.perf_counter() - t0
             if now >= ta:
                 break
         if now - ta > 1e-3:
             late += 1
-        dm = dims_of[s]
-        off = [0] * len(dm)
-        ext = list(dm)
-        off[mu], ext[mu] = idx, 1
-        tickets.append(api.ttnn_server_submit(srv, sids[s], buf, off, ext))
-    failed, errors = 0, {}
-    for t in tickets:
-        st = api.ttnn_server_wait(srv, t, 120_000_000)
-        if st != 0:
-            failed += 1
-            key = f"{st}: {api.last_error_message()}"
-            errors[key] = errors.get(key, 0) + 1
+        submit(sids[s_], dims_of[s_], mu, idx)
+    drain()
     wall = time.perf_counter() - t0
     rep = api.ttnn_server_stats(srv)
     dev_bytes = rep["device_bytes"]
-    # capacity: the same kind of slices submitted back to back (queues full),
-    # completion rate until the last one is done
+    offered = dict(throttled=stats["throttled"], throttle_s=stats["throttle_s"])
+    # capacity: the same kind of slices submitted back to back (the queue
+    # stays full; the client is held back by EBUSY), completion rate until
+    # the last one is done
     api.ttnn_server_stats(srv, reset=True)
-    burst = [(s, mu, idx) for (_, s, mu, idx) in arrivals[:20000]]
-    tickets = []
+    stats["throttled"], stats["throttle_s"] = 0, 0.0
+    burst = [(s_, mu, idx) for (_, s_, mu, idx) in arrivals[:100000]]
     t1 = time.perf_counter()
-    for (s, mu, idx) in burst:
-        dm = dims_of[s]
-        off = [0] * len(dm)
-        ext = list(dm)
-        off[mu], ext[mu] = idx, 1
-        tickets.append(api.ttnn_server_submit(srv, sids[s], buf, off, ext))
-    for t in tickets:
-        if api.ttnn_server_wait(srv, t, 120_000_000) != 0:
-            failed += 1
+    for (s_, mu, idx) in burst:
+        submit(sids[s_], dims_of[s_], mu, idx)
+    drain()
     cap_s = time.perf_counter() - t1
     cap = api.ttnn_server_stats(srv)
     api.ttnn_server_destroy(srv)
@@ -740,15 +770,25 @@ def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=3.0):
                         f"p=r/2, BF16), Poisson slices at {rate:.0f}/s for {seconds:.0f} s",
             "offered_per_s": len(arrivals) / seconds, "target_per_s": 20000,
             "drain_s": wall - seconds, "completed": rep["completed_updates"],
-            "completed_per_s": rep["completed_updates"] / wall, "failed": failed + rep["failed"],
+            "completed_per_s": rep["completed_updates"] / wall,
+            "failed": stats["failed"] + rep["failed"],
             "update_gbs": rep["update_bytes"] / wall / 1e9,
             "latency_us": {"p50": rep["p50_us"], "p99": rep["p99_us"], "max": rep["max_us"]},
-            "batches": rep["batches"], "late_submits": late, "open_s": open_s,
-            "worker_host_s": rep["worker_host_s"], "wall_s": wall, "errors": errors,
+            "batches": rep["batches"],
+            "updates_per_batch": rep["completed_updates"] / max(rep["batches"], 1),
+            "late_submits": late, "open_s": open_s, "queue_capacity": SERVE_QUEUE,
+            "stream_queue_capacity": SERVE_STREAM_QUEUE,
+            "throttled_submits": offered["throttled"], "throttle_wait_s": offered["throttle_s"],
+            "worker_host_s": rep["worker_host_s"], "wall_s": wall, "errors": stats["errors"],
             "device_gb": dev_bytes / 1e9,
-            "capacity": {"note": "the first slices of the same arrival list submitted back to back",
+            "capacity": {"note": "the first slices of the same arrival list submitted back to "
+                                 "back; submits beyond the queue capacity wait (EBUSY) for the "
+                                 "oldest outstanding ticket",
                          "updates": cap["completed_updates"], "per_s": cap["completed_updates"] / cap_s,
-                         "batches": cap["batches"], "p99_us": cap["p99_us"]}}
+                         "batches": cap["batches"],
+                         "updates_per_batch": cap["completed_updates"] / max(cap["batches"], 1),
+                         "p50_us": cap["p50_us"], "p99_us": cap["p99_us"], "max_us": cap["max_us"],
+                         "throttled_submits": stats["throttled"]}}
 
 
 def cpu_oracle_sample(max_seconds=25.0):
@@ -796,6 +836,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the Poisson serving run (60 s: the stated serving config)")
     ap.add_argument("--no-serving", action="store_true",
                     help="leave out the streamed-update and serving-mix legs (extra keys)")
     ap.add_argument("--nmode", type=int, default=NMODE, help="mode size (64 = the stated workload)")
@@ -927,7 +969,7 @@ def main():
         log("streaming leg")
         out["streaming"] = run_streaming(api, W, torch)
         log("serving leg")
-        out["serving"] = run_serving(api, W, torch)
+        out["serving"] = run_serving(api, W, torch, seconds=args.serve_seconds)
         log("rounding leg")
         out["rounding"] = run_rounding(api, W, torch)
         log("hilbert leg")

@@ -397,8 +397,12 @@ typedef struct {
                                 the library's 32 MiB static scratch block (resident once
                                 its module is loaded) is counted against it: must exceed it */
   int32_t max_batch;         /* requests per batch; <= 0: 64 */
-  int32_t queue_capacity;    /* pending requests; <= 0: 65536 */
+  int32_t queue_capacity;    /* requests outstanding (queued or on the device) before
+                                submits are refused with EBUSY; <= 0: 65536 */
   int32_t workers;           /* worker threads, each with its own CUDA stream; <= 0: 4 */
+  int32_t stream_queue_capacity; /* requests outstanding per stream before its submits are
+                                    refused with EBUSY (keeps one busy stream from filling
+                                    the queue); <= 0: unbounded */
 } ttnn_server_opts;
 
 typedef struct {
@@ -429,7 +433,9 @@ ttnn_status ttnn_server_open(ttnn_server_t server, const ttnn_tree* tree, int32_
 ttnn_status ttnn_server_close(ttnn_server_t server, int32_t stream_id, int64_t timeout_us);
 /* Queues ttnn_update_dense(stream, data, offset, extent, tile_scale, lambda).
  * data / tile_scale (device) must stay valid until the ticket is done.
- * Argument errors as ttnn_update_dense (checked here); EBUSY: queue full. */
+ * Argument errors as ttnn_update_dense (checked here); EBUSY: queue_capacity
+ * requests outstanding, or stream_queue_capacity of this stream (back-pressure:
+ * wait for one of the stream's tickets, then submit again). */
 ttnn_status ttnn_server_submit(ttnn_server_t server, int32_t stream_id, const void* data,
                                const int64_t* offset, const int64_t* extent,
                                const float* tile_scale, double lambda, uint64_t* ticket);

@@ -28,7 +28,7 @@ class TtnnNodeInfo(C.Structure):
 
 class TtnnServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", c_i64), ("max_batch", c_i32), ("queue_capacity", c_i32),
-                ("workers", c_i32)]
+                ("workers", c_i32), ("stream_queue_capacity", c_i32)]
 
 
 class TtnnServerReport(C.Structure):

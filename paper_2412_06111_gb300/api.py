@@ -262,10 +262,11 @@ def ttnn_plan_pass_counts(plan):
 # ---------------------------------------------------------------------------
 # serving
 # ---------------------------------------------------------------------------
-def ttnn_server_create(hbm_budget_bytes, max_batch=0, queue_capacity=0, workers=0):
+def ttnn_server_create(hbm_budget_bytes, max_batch=0, queue_capacity=0, workers=0,
+                       stream_queue_capacity=0):
     out = C.c_void_p()
     opts = _sigs.TtnnServerOpts(int(hbm_budget_bytes), int(max_batch), int(queue_capacity),
-                                int(workers))
+                                int(workers), int(stream_queue_capacity))
     _check(_lib().ttnn_server_create(C.byref(opts), C.byref(out)))
     return out
 

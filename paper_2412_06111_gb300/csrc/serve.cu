@@ -80,6 +80,7 @@ struct ttnn_server_s {
   int64_t budget = 0, used = 0;
   int max_batch = 64;
   size_t capacity = 65536;
+  int stream_capacity = 0;   // outstanding requests per stream (0: unbounded)
   size_t queued = 0;
   std::mutex mu;
   std::condition_variable cv_done;
@@ -283,6 +284,7 @@ ttnn_status ttnn_server_create(const ttnn_server_opts* opts, ttnn_server_t* out)
   S->budget = opts->hbm_budget_bytes - static_scratch_resident_bytes();
   S->max_batch = opts->max_batch > 0 ? opts->max_batch : 64;
   S->capacity = opts->queue_capacity > 0 ? (size_t)opts->queue_capacity : 65536;
+  S->stream_capacity = opts->stream_queue_capacity > 0 ? opts->stream_queue_capacity : 0;
   const int nw = opts->workers > 0 ? std::min(opts->workers, 64) : 4;
   S->workers = std::vector<Worker>(nw);
   cudaError_t e = cudaGetDevice(&S->device);
@@ -399,8 +401,14 @@ static ttnn_status enqueue(ttnn_server_s* S, Request&& r, uint64_t* ticket) {
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->slots.find(r.stream);
     TTNN_CHECK_ARG(it != S->slots.end(), "no open stream %d", r.stream);
-    if (S->queued >= S->capacity) {
-      set_error("request queue full (%zu)", S->capacity);
+    // back-pressure: requests outstanding (queued or on the device) are
+    // bounded, so a request's wait is bounded by the work ahead of it
+    if (S->inflight.size() >= S->capacity) {
+      set_error("request queue full (%zu outstanding)", S->capacity);
+      return TTNN_EBUSY;
+    }
+    if (S->stream_capacity > 0 && it->second.pending >= S->stream_capacity) {
+      set_error("stream %d has %d requests outstanding", r.stream, it->second.pending);
       return TTNN_EBUSY;
     }
     r.ticket = S->next_ticket++;

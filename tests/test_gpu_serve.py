@@ -149,6 +149,50 @@ def test_mixed_streams_equal_alone_bitwise():
             a.close()
 
 
+@pytest.mark.parametrize("cap,scap", [(3, 0), (0, 2)])
+def test_back_pressure_bounds_outstanding_requests(cap, scap):
+    # queue_capacity bounds the requests outstanding (queued or on the
+    # device), stream_queue_capacity those of one stream: submits beyond
+    # either are refused with EBUSY, the client waits
+    # for its oldest ticket and submits again; no update is lost or applied
+    # twice (the state equals the same updates applied alone)
+    tr, dims, r, p, dt = STREAMS[4]
+    n = len(tr[0])
+    srv = api.ttnn_server_create(64 << 30, max_batch=4, queue_capacity=cap, workers=1,
+                                 stream_queue_capacity=scap)
+    alone = Run(tr, dims, [r] * n, [p] * n, 300, dtype=dt)
+    rng = np.random.default_rng(3)
+    try:
+        sid = api.ttnn_server_open(srv, tr, dims, [r] * n, [p] * n, 300, sketch_dtype=dt)
+        work = [(off, ext, torch.from_numpy(np.ascontiguousarray(x)).to("cuda", TDT[dt]), lam)
+                for off, ext, x, lam in _slice_updates(dims, 40, rng)]
+        outstanding, refused = [], 0
+        for off, ext, x, lam in work:
+            while True:
+                try:
+                    outstanding.append(api.ttnn_server_submit(srv, sid, x, off, ext, lam=lam))
+                    break
+                except api.TtnnError as e:
+                    assert e.status == 6                   # EBUSY
+                    assert len(outstanding) >= 1
+                    refused += 1
+                    assert api.ttnn_server_wait(srv, outstanding.pop(0)) == 0
+            assert api.ttnn_server_stats(srv)["queued"] <= max(cap, scap)
+        for t in outstanding:
+            assert api.ttnn_server_wait(srv, t) == 0
+        assert refused > 0
+        for off, ext, x, lam in work:
+            api.ttnn_update_dense(alone.state, x, off, ext, lam=lam)
+        torch.cuda.synchronize()
+        got = _state(alone.plan, api.ttnn_server_stream_state(srv, sid))
+        want = _state(alone.plan, alone.state)
+        assert np.array_equal(got, want)
+        assert api.ttnn_server_stats(srv)["completed_updates"] == len(work)
+    finally:
+        api.ttnn_server_destroy(srv)
+        alone.close()
+
+
 def test_admission_by_device_memory_and_close():
     tr, dims, r, p, dt = STREAMS[0]
     n = len(tr[0])
