@@ -488,6 +488,9 @@ def run_rounding(api, W, torch, steps=5, warmup=3):
     dev = [torch.from_numpy(np.ascontiguousarray(cores[v])).cuda() for v in range(nn)]
     in_bytes = sum(c.numel() * 8 for c in dev)
     walk_bytes = 2 * sum(c.numel() for c in dev) * 4      # two sweeps over binary32 copies
+    # dominant GEMM flops of the sweeps: every core against its sketch
+    # blocks, up (r + s columns) and down (r columns)
+    flops = sum(2.0 * c.numel() * (r + (r + p) + r) for c in dev)
     ch, _ = W.children_of(tr[0], tr[1])
     tt = _ttn_inner(tr[0], ch, cores, cores)
     out = {"workload": f"TTN order {d}, modes {n}, balanced binary tree, edge ranks {rdom + rnoise} "
@@ -522,8 +525,13 @@ def run_rounding(api, W, torch, steps=5, warmup=3):
                .reshape(nd["core_shape"]) for nd in nodes}
         err = float(np.sqrt(max(tt - 2 * _ttn_inner(tr[0], ch, cores, got) +
                                 _ttn_inner(tr[0], ch, got, got), 0.0) / tt))
+        tf = flops / (ms * 1e-3) / 1e12
         out[name] = {"ms_per_rounding": ms, "input_gbs": in_bytes / (ms * 1e-3) / 1e9,
-                     "walk_gbs": walk_bytes / (ms * 1e-3) / 1e9, "rel_error": err}
+                     "walk_gbs": walk_bytes / (ms * 1e-3) / 1e9, "rel_error": err,
+                     "roofline": {"bound": "alu", "achieved": tf, "peak": FFMA_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": tf / FFMA_TFLOPS,
+                                  "flops": flops, "note": "binary32 FFMA peak from unit counts "
+                                  "and clocks; whole rounding (sweeps, QR, assembly) timed"}}
         api.ttnn_state_destroy(st)
         api.ttnn_plan_destroy(plan)
     out["noise_level"] = 0.01
@@ -655,6 +663,8 @@ def run_hilbert(api, W, torch, steps=3, warmup=2, r=10, p=5):
     return out
 
 
+# binary32 FMA peak of a GB300: 152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz
+FFMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SERVE_QUEUE = 1024     # requests outstanding in the server (back-pressure beyond)
 SERVE_STREAM_QUEUE = 4   # ... and per stream
 EBUSY = 6
@@ -846,6 +856,8 @@ def main():
                          "forms, e2e or serving legs; e.g. for profiling)")
     ap.add_argument("--form", default="bf16", choices=["bf16", "sttnn", "fp32", "bf16x2", "fp8"],
                     help="the form --headline-only times")
+    ap.add_argument("--leg", default=None, choices=["streaming", "serving", "rounding", "hilbert"],
+                    help="run only this extra leg and print its JSON (e.g. for profiling)")
     args = ap.parse_args()
     NMODE = args.nmode
     warmup = max(3, args.warmup)
@@ -879,6 +891,16 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     hbm, bf16_tf, peak_src = _peaks()
+    if args.leg:
+        if rank == 0:
+            legs = {"streaming": lambda: run_streaming(api, W, torch),
+                    "serving": lambda: run_serving(api, W, torch, seconds=args.serve_seconds),
+                    "rounding": lambda: run_rounding(api, W, torch),
+                    "hilbert": lambda: run_hilbert(api, W, torch)}
+            with Clocks(dev) as clk:
+                res = legs[args.leg]()
+            print(json.dumps({"leg": args.leg, args.leg: res, "clocks": clk.summary()}))
+        return
     N = NMODE ** D
     a32 = W.inv_sum_slab_torch(D, NMODE, ws, rank, "cuda", torch.float32)
     if args.headline_only:
