@@ -709,9 +709,6 @@ __device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned 
     case OP_OUTER:
       dev_outer(op, blk);
       break;
-    case OP_KGEMM:
-      dev_kgemm<I>(op, blk, dsm);
-      break;
     default:
       break;
   }
@@ -730,6 +727,24 @@ __global__ void __launch_bounds__(kExecThreads) level_kernel(const __grid_consta
   const int64_t blk = b - lb.start[lo];
   if (op.idx32) dispatch<uint32_t>(op, blk, dsm);
   else dispatch<int64_t>(op, blk, dsm);
+}
+
+// The split-K GEMM ops of a level in a kernel of their own: its code stays
+// small enough for the instruction caches (the generic level kernel's many op
+// kinds do not, and its ops stall on instruction fetch).
+__global__ void __launch_bounds__(kExecThreads, 2) kgemm_level_kernel(const __grid_constant__ LevelBatch lb) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = lb.nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (lb.start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const DevOp& op = lb.ops[lo];
+  const int64_t blk = b - lb.start[lo];
+  // one instantiation (64-bit column decoding: a few divisions per thread)
+  dev_kgemm<int64_t>(op, blk, dsm);
 }
 
 // ---------------------------------------------------------------------------
@@ -938,63 +953,77 @@ static DevOp to_dev(const Op& o) {
 
 ttnn_status Program::run(cudaStream_t st, bool dump) {
   const int L = levels();
-  for (int lvl = 1; lvl <= L; ++lvl) {
-    LevelBatch lb;
-    lb.nops = 0;
-    lb.start[0] = 0;
-    auto flush = [&]() -> ttnn_status {
-      if (lb.nops == 0) return TTNN_OK;
-      const int64_t blocks = lb.start[lb.nops];
-      if (blocks > 0) {
-        if (blocks >= (int64_t(1) << 31)) {
-          set_error("program level too large");
-          return TTNN_EUNSUPPORTED;
-        }
-        level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(lb);
+  // per level: the split-K GEMM ops in one launch of their kernel (first: the
+  // longest blocks start early), every other op in one level_kernel launch
+  LevelBatch lb[2];
+  auto flush = [&](int k) -> ttnn_status {
+    LevelBatch& b = lb[k];
+    if (b.nops == 0) return TTNN_OK;
+    const int64_t blocks = b.start[b.nops];
+    if (blocks > 0) {
+      if (blocks >= (int64_t(1) << 31)) {
+        set_error("program level too large");
+        return TTNN_EUNSUPPORTED;
+      }
+      if (k == 0) {
+        kgemm_level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(b);
+        TTNN_TRY(check_launch("kgemm_level_kernel"));
+      } else {
+        level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(b);
         TTNN_TRY(check_launch("level_kernel"));
       }
-      lb.nops = 0;
-      return TTNN_OK;
-    };
-    for (const Op& o : ops_) {
-      if (o.level != lvl || o.blocks == 0) continue;
-      if (dump) {
-        // debugging: each op alone, timed (the stream is synchronised)
-        TTNN_TRY(flush());
-        cudaEvent_t a = nullptr, b = nullptr;
-        TTNN_TRY_CUDA(cudaEventCreate(&a));
-        TTNN_TRY_CUDA(cudaEventCreate(&b));
-        lb.ops[0] = to_dev(o);
-        lb.start[0] = 0;
-        lb.start[1] = o.blocks;
-        lb.nops = 1;
-        TTNN_TRY_CUDA(cudaEventRecord(a, st));
-        TTNN_TRY(flush());
-        TTNN_TRY_CUDA(cudaEventRecord(b, st));
-        TTNN_TRY_CUDA(cudaEventSynchronize(b));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        fprintf(stderr, "[ttnn] %8.1f us  ", ms * 1e3f);
-        if (o.kind == OP_SCATTER)
-          fprintf(stderr, "[ttnn] L%d scatter nd %d nsc %d blocks %lld\n", lvl, o.s.nd, o.s.nsc,
-                  (long long)o.blocks);
-        else
-          fprintf(stderr,
-                  "[ttnn] L%d kind %d P %lld NI %lld NB %lld Q %lld J %lld isJ %lld wsJ %lld wsQ %lld "
-                  "wsP %lld g %d nsplit %d blocks %lld\n",
-                  lvl, (int)o.kind, (long long)o.c.P, (long long)o.c.NI, (long long)o.c.NB,
-                  (long long)o.c.Q, (long long)o.c.J, (long long)o.c.isJ, (long long)o.c.wsJ,
-                  (long long)o.c.wsQ, (long long)o.c.wsP, o.g, o.nsplit, (long long)o.blocks);
-        continue;
-      }
-      if (lb.nops == kMaxLevelOps) TTNN_TRY(flush());
-      lb.ops[lb.nops] = to_dev(o);
-      lb.start[lb.nops + 1] = lb.start[lb.nops] + o.blocks;
-      ++lb.nops;
     }
-    TTNN_TRY(flush());
+    b.nops = 0;
+    return TTNN_OK;
+  };
+  for (int lvl = 1; lvl <= L; ++lvl) {
+    for (int k = 0; k < 2; ++k) {
+      lb[k].nops = 0;
+      lb[k].start[0] = 0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      for (const Op& o : ops_) {
+        if (o.level != lvl || o.blocks == 0) continue;
+        const int k = o.kind == OP_KGEMM ? 0 : 1;
+        if (k != pass) continue;
+        LevelBatch& b = lb[k];
+        if (dump) {
+          // debugging: each op alone, timed (the stream is synchronised)
+          cudaEvent_t a = nullptr, e = nullptr;
+          TTNN_TRY_CUDA(cudaEventCreate(&a));
+          TTNN_TRY_CUDA(cudaEventCreate(&e));
+          b.ops[0] = to_dev(o);
+          b.start[0] = 0;
+          b.start[1] = o.blocks;
+          b.nops = 1;
+          TTNN_TRY_CUDA(cudaEventRecord(a, st));
+          TTNN_TRY(flush(k));
+          TTNN_TRY_CUDA(cudaEventRecord(e, st));
+          TTNN_TRY_CUDA(cudaEventSynchronize(e));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, e);
+          cudaEventDestroy(a);
+          cudaEventDestroy(e);
+          fprintf(stderr, "[ttnn] %8.1f us  ", ms * 1e3f);
+          if (o.kind == OP_SCATTER)
+            fprintf(stderr, "[ttnn] L%d scatter nd %d nsc %d blocks %lld\n", lvl, o.s.nd, o.s.nsc,
+                    (long long)o.blocks);
+          else
+            fprintf(stderr,
+                    "[ttnn] L%d kind %d P %lld NI %lld NB %lld Q %lld J %lld isJ %lld wsJ %lld "
+                    "wsQ %lld wsP %lld g %d nsplit %d blocks %lld\n",
+                    lvl, (int)o.kind, (long long)o.c.P, (long long)o.c.NI, (long long)o.c.NB,
+                    (long long)o.c.Q, (long long)o.c.J, (long long)o.c.isJ, (long long)o.c.wsJ,
+                    (long long)o.c.wsQ, (long long)o.c.wsP, o.g, o.nsplit, (long long)o.blocks);
+          continue;
+        }
+        if (b.nops == kMaxLevelOps) TTNN_TRY(flush(k));
+        b.ops[b.nops] = to_dev(o);
+        b.start[b.nops + 1] = b.start[b.nops] + o.blocks;
+        ++b.nops;
+      }
+      TTNN_TRY(flush(pass));
+    }
   }
   return TTNN_OK;
 }
