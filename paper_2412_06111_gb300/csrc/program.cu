@@ -714,7 +714,7 @@ __device__ __forceinline__ void dispatch(const DevOp& op, int64_t blk, unsigned 
   }
 }
 
-__global__ void __launch_bounds__(kExecThreads) level_kernel(const __grid_constant__ LevelBatch lb) {
+__global__ void __launch_bounds__(kExecThreads, 3) level_kernel(const __grid_constant__ LevelBatch lb) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int64_t b = blockIdx.x;
   int lo = 0, hi = lb.nops - 1;
