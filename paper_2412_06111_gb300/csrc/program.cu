@@ -327,32 +327,26 @@ __device__ void dev_kred(const DevOp& op, int64_t blk, unsigned char* smem) {
   }
 }
 
-// Split-K tiled contraction for long reductions (e.g. the Khatri-Rao
-// contraction of all leading modes of a first-level product at once, or a
-// TTN core against a sketch block):
+// Split-K register-tiled contraction for long reductions (e.g. the
+// Khatri-Rao contraction of all leading modes of a first-level product at
+// once, or a TTN core against a sketch block):
 //   out[p,b,q,j] (+)= alpha * sum_i W(i, b) in[p,i,q,j],
 // with W(i, b) = w[i*wsI + b*wsB] or the Khatri-Rao product of the factors
 // c.kr (nkr > 0).  Columns n = (p, q, j) are tiled kKgNT per block, the
 // outputs b in groups of kKgMB (op.BG groups) and the reduction index in
-// chunks of op.chunk: block = (tile, b group, split).  Tiles of kKgKT rows
-// are read into registers one step ahead (column-wise: consecutive threads,
-// consecutive columns, contiguous j; or, with op.CG = 1 -- J = Q = 1 and a
-// contiguous reduction index -- row-wise: 16 consecutive i of a column per
-// 16 threads) and stored in shared memory as a TF32 hi/lo split,
-// x = hi + lo + O(2^-22 |x|) (hi, lo rounded to nearest); warp w multiplies
-// b rows 0..31 by columns 32w..32w+31 on the tensor cores with three
-// m16n8k8 TF32 products per tile, hi*hi + hi*lo + lo*hi, accumulated in
-// binary32 (each product within ~2^-21 of the binary32 one; the dropped
-// lo*lo term is below that).  With nsplit > 1 the block writes its partial
+// chunks of op.chunk: block = (tile, b group, split).  Each thread
+// accumulates 8 (b) x 4 (n) outputs from shared-memory tiles of kKgKT rows,
+// the next rows prefetched into registers.  Tiles are read column-wise
+// (consecutive threads, consecutive columns: contiguous j) or, with op.CG = 1
+// (J = Q = 1 and a contiguous reduction index), row-wise (16 consecutive i of
+// a column per 16 threads).  With nsplit > 1 the block writes its partial
 // sums [split][p][b][q][j], reduced in a fixed order (OP_REDUCE), else the
 // outputs.
 constexpr int kKgKT = 16, kKgNT = 256, kKgMB = 32;
-constexpr int kKgWLd = kKgMB + 8;   // weight tile row: conflict-free fragment loads
-constexpr int kKgILd = kKgNT + 8;   // input tile row: conflict-free fragment loads
+constexpr int kKgLd = kKgNT + 4;               // padded tile row (row-wise stores: 2-way banks)
 constexpr int kKgWPT = kKgKT * kKgMB / 256;   // weight-tile entries per thread
 static_assert(kKgKT * kKgMB % 256 == 0 && kKgWPT >= 1, "weight tile must split over 256 threads");
-static_assert(kKgKT == 16 && kKgNT == 256 && kKgMB == 32, "tile shapes of the warp layout");
-static_assert((2 * kKgKT * (kKgWLd + kKgILd)) * 4 <= (int)kExecSmem, "tiles exceed shared memory");
+static_assert(kKgKT == 16 && kKgNT == 256, "row-wise tile loads assume 16 x 256 tiles");
 
 // W(i, b) of a split-K contraction; i < 2^31 (the recorder checks).
 __device__ __forceinline__ float kg_weight(const Contract& c, int64_t i, int b) {
@@ -371,32 +365,11 @@ __device__ __forceinline__ float kg_weight(const Contract& c, int64_t i, int b) 
   return v;
 }
 
-// TF32 split of a binary32 value: hi = tf32(x), lo = tf32(x - hi) (x - hi is
-// exact in binary32), both rounded to nearest, ties away (cvt.rna).
-__device__ __forceinline__ void tf32_split(float x, uint32_t* hi, uint32_t* lo) {
-  uint32_t h, l;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - __uint_as_float(h)));
-  *hi = h;
-  *lo = l;
-}
-
-// d += a b for one m16n8k8 TF32 tile (a: 16 x 8 row-major fragment, b: 8 x 8
-// column-major fragment, d: 16 x 8 binary32).
-__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 template <typename I>
 __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
   const Contract& c = op.c;
-  uint32_t* Wh = (uint32_t*)smem;                 // [kKgKT][kKgWLd] hi parts of W
-  uint32_t* Wl = Wh + kKgKT * kKgWLd;             // lo parts
-  uint32_t* Ih = Wl + kKgKT * kKgWLd;             // [kKgKT][kKgILd] hi parts of the input
-  uint32_t* Il = Ih + kKgKT * kKgILd;             // lo parts
+  float* Ws = (float*)smem;                       // [kKgKT][kKgMB]
+  float* Is = Ws + kKgKT * kKgMB;                 // [kKgKT][kKgLd]
   const int t = threadIdx.x;
   const int64_t ncols = c.P * c.Q * c.J;
   const int64_t ntile = (ncols + kKgNT - 1) / kKgNT;
@@ -428,17 +401,14 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
   }
   const int64_t rstep = (int64_t)(kKgNT / kKgKT) * c.isP;   // row-wise: 16 columns on
   const int64_t rcols = ncols - tile * kKgNT;                // row-wise: valid columns
-  // mma role: warp w owns columns [32 w, 32 w + 32) and all 32 b rows:
-  // 2 (b) x 4 (columns) tiles of 16 x 8; lane = 4 g + tq
-  const int warp = t >> 5, lane = t & 31, g = lane >> 2, tq = lane & 3;
-  const int n0 = 32 * warp;
-  float acc[2][4][4];
+  // compute role: outputs b in [8 bg, 8 bg + 8), columns [4 cg, 4 cg + 4)
+  const int cg = t % 64, bg = t / 64;
+  float acc[8][4];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int x = 0; x < 8; ++x)
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+  // the next step's rows are read into registers while this step computes
   constexpr int kRows = kKgKT * kKgNT / 256;      // tile entries each thread loads per step
   float ri[kRows], rw[kKgWPT];
 #define KG_FETCH(k0_)                                                              \
@@ -459,81 +429,54 @@ __device__ void dev_kgemm(const DevOp& op, int64_t blk, unsigned char* smem) {
   }
   if (i0 < i1) KG_FETCH(i0);
   for (int64_t k0 = i0; k0 < i1; k0 += kKgKT) {
+    if (rows) {
 #pragma unroll
-    for (int u = 0; u < kRows; ++u) {
-      const int o = rows ? lr * kKgILd + lc + u * (kKgNT / kKgKT) : u * kKgILd + lc;
-      tf32_split(ri[u], &Ih[o], &Il[o]);
+      for (int u = 0; u < kRows; ++u) Is[lr * kKgLd + lc + u * (kKgNT / kKgKT)] = ri[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) Is[u * kKgLd + lc] = ri[u];
     }
 #pragma unroll
-    for (int h = 0; h < kKgWPT; ++h) {
-      const int e = t + h * 256;
-      const int o = (e / kKgMB) * kKgWLd + e % kKgMB;
-      tf32_split(rw[h], &Wh[o], &Wl[o]);
-    }
+    for (int h = 0; h < kKgWPT; ++h) Ws[t + h * 256] = rw[h];
     __syncthreads();
     if (k0 + kKgKT < i1) KG_FETCH(k0 + kKgKT);
 #pragma unroll
-    for (int ks = 0; ks < kKgKT / 8; ++ks) {
-      const int r0 = (8 * ks + tq) * kKgWLd, r1 = r0 + 4 * kKgWLd;
-      uint32_t ah[2][4], al[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int m = 16 * mt + g;
-        ah[mt][0] = Wh[r0 + m];
-        ah[mt][1] = Wh[r0 + m + 8];
-        ah[mt][2] = Wh[r1 + m];
-        ah[mt][3] = Wh[r1 + m + 8];
-        al[mt][0] = Wl[r0 + m];
-        al[mt][1] = Wl[r0 + m + 8];
-        al[mt][2] = Wl[r1 + m];
-        al[mt][3] = Wl[r1 + m + 8];
-      }
-      const int q0 = (8 * ks + tq) * kKgILd + n0 + g, q1 = q0 + 4 * kKgILd;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const uint32_t bh0 = Ih[q0 + 8 * nt], bh1 = Ih[q1 + 8 * nt];
-        const uint32_t bl0 = Il[q0 + 8 * nt], bl1 = Il[q1 + 8 * nt];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          mma_tf32(acc[mt][nt], al[mt], bh0, bh1);
-          mma_tf32(acc[mt][nt], ah[mt], bl0, bl1);
-          mma_tf32(acc[mt][nt], ah[mt], bh0, bh1);
-        }
-      }
+    for (int kk = 0; kk < kKgKT; ++kk) {
+      const float4 w0 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&Ws[kk * kKgMB + 8 * bg + 4]);
+      const float4 xv = *reinterpret_cast<const float4*>(&Is[kk * kKgLd + 4 * cg]);
+#define KG_ROW(row_, w_)          \
+  acc[row_][0] += (w_) * xv.x;    \
+  acc[row_][1] += (w_) * xv.y;    \
+  acc[row_][2] += (w_) * xv.z;    \
+  acc[row_][3] += (w_) * xv.w;
+      KG_ROW(0, w0.x) KG_ROW(1, w0.y) KG_ROW(2, w0.z) KG_ROW(3, w0.w)
+      KG_ROW(4, w1.x) KG_ROW(5, w1.y) KG_ROW(6, w1.z) KG_ROW(7, w1.w)
+#undef KG_ROW
     }
     __syncthreads();
   }
 #undef KG_FETCH
-  // outputs: tile (mt, nt) element e is b = 16 mt + g (+ 8 for e >= 2),
-  // column 8 nt + 2 tq + (e & 1) of the warp's 32
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
+  for (int y = 0; y < 4; ++y) {
+    const I n = (I)(tile * kKgNT) + (I)(4 * cg + y);
+    if ((int64_t)n >= ncols) continue;
+    const I j = n % (I)c.J, pq = n / (I)c.J;
+    const I q = pq % (I)c.Q, p = pq / (I)c.Q;
+    // partial [split][p][b][q][j] or the output, at b = b0 + 8 bg
+    const int64_t pbase = ((int64_t)split * c.P + p) * c.NB * c.Q * c.J + (int64_t)q * c.J + j;
+    const int64_t pstep = c.Q * c.J;
+    float* o = (float*)c.out + (int64_t)p * c.osP + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
 #pragma unroll
-    for (int e1 = 0; e1 < 2; ++e1) {
-      const I n = (I)(tile * kKgNT) + (I)(n0 + 8 * nt + 2 * tq + e1);
-      if ((int64_t)n >= ncols) continue;
-      const I j = n % (I)c.J, pq = n / (I)c.J;
-      const I q = pq % (I)c.Q, p = pq / (I)c.Q;
-      // partial [split][p][b][q][j] or the output
-      const int64_t pbase = ((int64_t)split * c.P + p) * c.NB * c.Q * c.J + (int64_t)q * c.J + j;
-      const int64_t pstep = c.Q * c.J;
-      float* o = (float*)c.out + (int64_t)p * c.osP + (int64_t)q * c.osQ + (int64_t)j * c.osJ;
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll
-        for (int e2 = 0; e2 < 2; ++e2) {
-          const int bl = 16 * mt + g + 8 * e2;
-          if (bl >= NBg) continue;
-          const int b = b0 + bl;
-          const float v = acc[mt][nt][2 * e2 + e1];
-          if (op.nsplit > 1) {
-            ((float*)op.partial)[pbase + (int64_t)b * pstep] = v;
-          } else {
-            float* ob = o + (int64_t)b * c.osB;
-            const float av = (float)c.alpha * v;
-            *ob = c.accumulate ? *ob + av : av;
-          }
-        }
+    for (int x = 0; x < 8; ++x) {
+      const int b = b0 + 8 * bg + x;
+      if (8 * bg + x >= NBg) continue;
+      if (op.nsplit > 1) {
+        ((float*)op.partial)[pbase + (int64_t)b * pstep] = acc[x][y];
+      } else {
+        float* ob = o + (int64_t)b * c.osB;
+        const float v = (float)c.alpha * acc[x][y];
+        *ob = c.accumulate ? *ob + v : v;
       }
     }
   }
