@@ -894,11 +894,50 @@ static DevOp to_dev(const Op& o) {
   return d;
 }
 
+// A second stream per host thread and device for the split-K GEMM launches
+// of a level, forked from and joined back into the caller's stream (so the
+// two kernels of a level overlap; each thread keeps its own, so concurrent
+// callers never wait on one another's work).
+struct ForkStream {
+  int device = -1;
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static ttnn_status fork_stream(ForkStream** out) {
+  thread_local ForkStream fs[8];
+  int dev = 0;
+  TTNN_TRY_CUDA(cudaGetDevice(&dev));
+  ForkStream* f = nullptr;
+  for (auto& x : fs)
+    if (x.device == dev) f = &x;
+  if (!f) {
+    for (auto& x : fs)
+      if (x.device < 0) {
+        f = &x;
+        break;
+      }
+    if (!f) {
+      *out = nullptr;   // more devices than slots: run the level's kernels in order
+      return TTNN_OK;
+    }
+    TTNN_TRY_CUDA(cudaStreamCreateWithFlags(&f->st, cudaStreamNonBlocking));
+    TTNN_TRY_CUDA(cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming));
+    TTNN_TRY_CUDA(cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming));
+    f->device = dev;
+  }
+  *out = f;
+  return TTNN_OK;
+}
+
 ttnn_status Program::run(cudaStream_t st, bool dump) {
   const int L = levels();
-  // per level: the split-K GEMM ops in one launch of their kernel (first: the
-  // longest blocks start early), every other op in one level_kernel launch
+  // per level: the split-K GEMM ops in one launch of their kernel, every
+  // other op in one level_kernel launch; when a level has both, the GEMM
+  // launch goes on the fork stream and runs beside the other
+  ForkStream* fs = nullptr;
   LevelBatch lb[2];
+  cudaStream_t gst = st;   // stream of the GEMM launches
   auto flush = [&](int k) -> ttnn_status {
     LevelBatch& b = lb[k];
     if (b.nops == 0) return TTNN_OK;
@@ -909,7 +948,7 @@ ttnn_status Program::run(cudaStream_t st, bool dump) {
         return TTNN_EUNSUPPORTED;
       }
       if (k == 0) {
-        kgemm_level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(b);
+        kgemm_level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, gst>>>(b);
         TTNN_TRY(check_launch("kgemm_level_kernel"));
       } else {
         level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(b);
@@ -923,6 +962,18 @@ ttnn_status Program::run(cudaStream_t st, bool dump) {
     for (int k = 0; k < 2; ++k) {
       lb[k].nops = 0;
       lb[k].start[0] = 0;
+    }
+    bool has[2] = {false, false};
+    for (const Op& o : ops_)
+      if (o.level == lvl && o.blocks > 0) has[o.kind == OP_KGEMM ? 0 : 1] = true;
+    gst = st;
+    if (has[0] && has[1] && !dump) {
+      if (!fs) TTNN_TRY(fork_stream(&fs));
+      if (fs) {
+        TTNN_TRY_CUDA(cudaEventRecord(fs->fork, st));
+        TTNN_TRY_CUDA(cudaStreamWaitEvent(fs->st, fs->fork, 0));
+        gst = fs->st;
+      }
     }
     for (int pass = 0; pass < 2; ++pass) {
       for (const Op& o : ops_) {
@@ -966,6 +1017,10 @@ ttnn_status Program::run(cudaStream_t st, bool dump) {
         ++b.nops;
       }
       TTNN_TRY(flush(pass));
+    }
+    if (gst != st) {
+      TTNN_TRY_CUDA(cudaEventRecord(fs->join, gst));
+      TTNN_TRY_CUDA(cudaStreamWaitEvent(st, fs->join, 0));
     }
   }
   return TTNN_OK;
