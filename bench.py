@@ -377,6 +377,57 @@ def run_e2e(api, W, dtype, steps, warmup, torch, host, ws=1, rank=0):
     return ms, host.numel() * host.element_size(), ce * 8
 
 
+def run_config1(api, W, torch, n_lat=200):
+    """Plain TTNN in binary64 on a 24^4 tensor with exact TTN ranks 5 on the
+    balanced tree ((1,2),(3,4)) (N(0,1) cores) plus Gaussian noise of relative
+    Frobenius norm 1e-8; target ranks 5, oversampling 5; the whole tensor in
+    one update.  Host round-trip latency of the update and of the recovery
+    (each waited on), with the Khatri-Rao and the unstructured Gaussian DRMs,
+    and the relative error of the recovered TTN on 20000 seeded entries."""
+    d, n, r, p = 4, 24, 5, 5
+    tr = W.balanced_binary(d)
+    nn = len(tr[0])
+    dims = [n] * d
+    T, _ = W.exact_ttn(tr, dims, [r] * nn, 1001, noise=1e-8)
+    dev = torch.from_numpy(np.ascontiguousarray(T)).cuda()
+    out = {"workload": "24^4 exact TTN ranks 5 + 1e-8 noise, FP64, r = 5, p = 5, one update"}
+    for name, flags in (("kr", 0), ("gaussian", api.FLAG_DENSE_DRM)):
+        plan = api.ttnn_plan_create(tr, dims, [r] * nn, [p] * nn, SEED + 1, sketch_dtype=api.F64,
+                                    flags=flags)
+        st = api.ttnn_state_create(plan)
+        cores = torch.zeros(api.ttnn_plan_sizes(plan)[2], dtype=torch.float64, device="cuda")
+        up, rec, dev_up, host_up = [], [], [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(n_lat + 5):
+            api.ttnn_state_zero(st)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0.record()
+            api.ttnn_update_dense(st, dev)
+            e1.record()
+            th = time.perf_counter()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            api.ttnn_recover(st, cores)
+            t2 = time.perf_counter()
+            if i >= 5:
+                up.append((t1 - t0) * 1e6)
+                rec.append((t2 - t1) * 1e6)
+                dev_up.append(e0.elapsed_time(e1) * 1e3)
+                host_up.append((th - t0) * 1e6)
+        for v in (up, rec, dev_up, host_up):
+            v.sort()
+        err = _sampled_error(api, plan, tr, cores, dims, lambda idx: T[tuple(idx.T)])
+        out[name] = {"update_us": {"p50": up[len(up) // 2], "p99": up[int(0.99 * len(up))],
+                                   "device_p50": dev_up[len(dev_up) // 2],
+                                   "host_call_p50": host_up[len(host_up) // 2]},
+                     "recover_us": {"p50": rec[len(rec) // 2], "p99": rec[int(0.99 * len(rec))]},
+                     "rel_error": err}
+        api.ttnn_state_destroy(st)
+        api.ttnn_plan_destroy(plan)
+    return out
+
+
 def run_streaming(api, W, torch, n_updates=4096, n_lat=256):
     """Streamed order-6 workload: 32^6 caterpillar (tensor train, identity
     single-mode leaves), r = 16, s = 24, BF16 plan; each update is one rank-2
@@ -436,6 +487,26 @@ def run_streaming(api, W, torch, n_updates=4096, n_lat=256):
     rec_ms = (time.perf_counter() - r0) * 1e3
     api.ttnn_state_destroy(state)
     api.ttnn_plan_destroy(plan)
+    # against binary64: the first n_err updates applied to a binary64 and to
+    # a BF16 plan (same tree, ranks and seed; the boxes hold bfloat16
+    # values, exact in both), the recovered TTNs compared on 20000 seeded
+    # entries
+    n_err = 1024
+    idx = _sample_idx(dims)
+    vals = {}
+    for name, dt in (("f64", api.F64), ("bf16", api.BF16)):
+        pl = api.ttnn_plan_create(tr, dims, [16] * nn, [8] * nn, SEED + 3, sketch_dtype=dt)
+        s_ = api.ttnn_state_create(pl)
+        for i in range(n_err):
+            api.ttnn_update_cp(s_, [1.0, 1.0], flist[i])
+            off, ext = geo[i]
+            api.ttnn_update_dense(s_, boxes[i] if dt == api.BF16 else boxes[i].double(), off, ext)
+        c_ = torch.zeros(api.ttnn_plan_sizes(pl)[2], dtype=torch.float64, device="cuda")
+        api.ttnn_recover(s_, c_)
+        vals[name] = _ttn_entries(api, pl, tr, c_, dims, idx)
+        api.ttnn_state_destroy(s_)
+        api.ttnn_plan_destroy(pl)
+    err64 = float(np.linalg.norm(vals["bf16"] - vals["f64"]) / np.linalg.norm(vals["f64"]))
     upd_bytes = n * n * n * 2 + d * n * 2 * 8
     return {"workload": "32^6 tensor train r=16 s=24 BF16; update = rank-2 CP + 32^3 box",
             "updates": n_updates, "updates_per_s": n_updates / (ms * 1e-3),
@@ -443,7 +514,10 @@ def run_streaming(api, W, torch, n_updates=4096, n_lat=256):
             "update_gbs": n_updates * upd_bytes / (ms * 1e-3) / 1e9,
             "launches_per_update": launches / n_updates,
             "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-            "recover_ms": rec_ms}
+            "recover_ms": rec_ms,
+            "bf16_vs_f64": {"note": f"recovered TTN after the first {n_err} updates, BF16 plan "
+                                    "against the binary64 plan, 20000 seeded entries",
+                            "rel_diff": err64}}
 
 
 def _ttn_inner(parent, ch, A, B):
@@ -581,17 +655,14 @@ def run_rounding(api, W, torch, steps=5, warmup=3):
     return out
 
 
-def _sampled_error(api, plan, tree, cores_dev, dims, exact, samples=20000, seed=77):
-    """Relative error of the recovered TTN on `samples` seeded entries against
-    exact(idx) (host evaluation of the cores: leaf slices, then each transfer
-    tensor against its children's vectors)."""
+def _ttn_entries(api, plan, tree, cores_dev, dims, idx):
+    """Entries of the recovered TTN at the multi-indices idx (samples x d):
+    host evaluation of the cores (leaf slices, then each transfer tensor
+    against its children's vectors)."""
     parent, leaf_modes, _ = tree
     nn = len(parent)
     nodes = [api.ttnn_plan_node(plan, v) for v in range(nn)]
     host = cores_dev.cpu().numpy()
-    rng = np.random.default_rng(seed)
-    d = len(dims)
-    idx = np.stack([rng.integers(0, dims[m], size=samples) for m in range(d)], axis=1)
     ch = {v: sorted([c for c in range(nn) if parent[c] == v], key=lambda c: nodes[c]["mode_lo"])
           for v in range(nn)}
     letters = "bcdefghijk"
@@ -609,7 +680,19 @@ def _sampled_error(api, plan, tree, cores_dev, dims, exact, samples=20000, seed=
         spec = head + letters[:m] + "," + ",".join("s" + letters[k] for k in range(m)) + "->s" + head
         return np.einsum(spec, core, *vecs, optimize=True)
 
-    approx = val(parent.index(-1))
+    return val(parent.index(-1))
+
+
+def _sample_idx(dims, samples=20000, seed=77):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.integers(0, n, size=samples) for n in dims], axis=1)
+
+
+def _sampled_error(api, plan, tree, cores_dev, dims, exact, samples=20000, seed=77):
+    """Relative error of the recovered TTN on `samples` seeded entries against
+    exact(idx)."""
+    idx = _sample_idx(dims, samples, seed)
+    approx = _ttn_entries(api, plan, tree, cores_dev, dims, idx)
     want = exact(idx)
     return float(np.linalg.norm(approx - want) / np.linalg.norm(want))
 
@@ -856,7 +939,8 @@ def main():
                          "forms, e2e or serving legs; e.g. for profiling)")
     ap.add_argument("--form", default="bf16", choices=["bf16", "sttnn", "fp32", "bf16x2", "fp8"],
                     help="the form --headline-only times")
-    ap.add_argument("--leg", default=None, choices=["streaming", "serving", "rounding", "hilbert"],
+    ap.add_argument("--leg", default=None,
+                    choices=["config1", "streaming", "serving", "rounding", "hilbert"],
                     help="run only this extra leg and print its JSON (e.g. for profiling)")
     args = ap.parse_args()
     NMODE = args.nmode
@@ -893,7 +977,8 @@ def main():
     hbm, bf16_tf, peak_src = _peaks()
     if args.leg:
         if rank == 0:
-            legs = {"streaming": lambda: run_streaming(api, W, torch),
+            legs = {"config1": lambda: run_config1(api, W, torch),
+                    "streaming": lambda: run_streaming(api, W, torch),
                     "serving": lambda: run_serving(api, W, torch, seconds=args.serve_seconds),
                     "rounding": lambda: run_rounding(api, W, torch),
                     "hilbert": lambda: run_hilbert(api, W, torch)}
@@ -988,6 +1073,8 @@ def main():
                      "quantize_ms": f8["quantize_ms"]},
     }
     if rank == 0 and not args.no_serving:
+        log("config-1 leg")
+        out["config1"] = run_config1(api, W, torch)
         log("streaming leg")
         out["streaming"] = run_streaming(api, W, torch)
         log("serving leg")

@@ -687,31 +687,35 @@ struct Vec4<double> {
   }
 };
 
-// 256 threads; each computes an 8 x 4 block of the 128 x 64 output tile.
-// The next k-tile's elements are fetched into registers while the current
-// one is multiplied out of shared memory.
-template <typename Tin, typename Tacc>
+// 256 threads; the output tile is 128 x BN (BN = 64, 32 or 16: the narrowest
+// that holds the output columns, so narrow products compute no padding), each
+// thread a (BN / 8) x 4 block of it.  The next k-tile's elements are fetched
+// into registers while the current one is multiplied out of shared memory.
+template <typename Tin, typename Tacc, int BN>
 __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t kchunk, Tacc* partial) {
+  constexpr int TX = BN / 4;            // threads along the columns
+  constexpr int TM = GB_M * TX / 256;   // rows per thread
+  constexpr int BPT = BN * GB_K / 256;  // B-tile elements per thread
   __shared__ __align__(16) Tacc As[GB_K][GB_M + GB_PAD];
-  __shared__ __align__(16) Tacc Bs[GB_K][GB_N + GB_PAD];
+  __shared__ __align__(16) Tacc Bs[GB_K][BN + GB_PAD];
   const Tin* A = (const Tin*)g.A;
   const Tin* B = (const Tin*)g.B;
   const int tid = threadIdx.x;
   const int64_t i0 = blockIdx.x * (int64_t)GB_M;
-  const int64_t j0 = blockIdx.y * (int64_t)GB_N;
+  const int64_t j0 = blockIdx.y * (int64_t)BN;
   const int split = blockIdx.z;
   const int64_t kb = split * kchunk;
   const int64_t ke = min(g.K, kb + kchunk);
-  const int ty = tid / 16, tx = tid % 16;   // output rows ty*8.., cols tx*4..
-  Tacc acc[8][4];
+  const int ty = tid / TX, tx = tid % TX;   // output rows ty*TM.., cols tx*4..
+  Tacc acc[TM][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
   const bool a_k_contig = (g.ask == 1);
   const bool b_k_contig = (g.bsk == 1);
-  // this thread's elements of a tile: A 128 x 16 (8 each), B 64 x 16 (4 each)
-  int aii[8], akk[8], bjj[4], bkk[4];
+  // this thread's elements of a tile: A 128 x 16 (8 each), B BN x 16
+  int aii[8], akk[8], bjj[BPT], bkk[BPT];
 #pragma unroll
   for (int l = 0; l < 8; ++l) {
     const int e = tid + l * 256;
@@ -719,12 +723,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
     else { akk[l] = e / GB_M; aii[l] = e % GB_M; }
   }
 #pragma unroll
-  for (int l = 0; l < 4; ++l) {
+  for (int l = 0; l < BPT; ++l) {
     const int e = tid + l * 256;
     if (b_k_contig) { bjj[l] = e / GB_K; bkk[l] = e % GB_K; }
-    else { bkk[l] = e / GB_N; bjj[l] = e % GB_N; }
+    else { bkk[l] = e / BN; bjj[l] = e % BN; }
   }
-  Tacc ra[8], rb[4];
+  Tacc ra[8], rb[BPT];
   auto fetch = [&](int64_t k0) {
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
@@ -732,7 +736,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
       ra[l] = (gi < g.I && gk < ke) ? load_as<Tin, Tacc>(A + gi * g.asi + gk * g.ask) : (Tacc)0;
     }
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < BPT; ++l) {
       const int64_t gj = j0 + bjj[l], gk = k0 + bkk[l];
       rb[l] = (gj < g.Jn && gk < ke) ? load_as<Tin, Tacc>(B + gj * g.bsj + gk * g.bsk) : (Tacc)0;
     }
@@ -742,17 +746,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
 #pragma unroll
     for (int l = 0; l < 8; ++l) As[akk[l]][aii[l]] = ra[l];
 #pragma unroll
-    for (int l = 0; l < 4; ++l) Bs[bkk[l]][bjj[l]] = rb[l];
+    for (int l = 0; l < BPT; ++l) Bs[bkk[l]][bjj[l]] = rb[l];
     __syncthreads();
     if (k0 + GB_K < ke) fetch(k0 + GB_K);
 #pragma unroll
     for (int kk = 0; kk < GB_K; ++kk) {
-      Tacc a[8], b[4];
-      Vec4<Tacc>::load(&As[kk][ty * 8], a);
-      Vec4<Tacc>::load(&As[kk][ty * 8 + 4], a + 4);
+      Tacc a[TM], b[4];
+      if (TM % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < TM / 4; ++q) Vec4<Tacc>::load(&As[kk][ty * TM + 4 * q], a + 4 * q);
+      } else {
+#pragma unroll
+        for (int q = 0; q < TM; ++q) a[q] = As[kk][ty * TM + q];
+      }
       Vec4<Tacc>::load(&Bs[kk][tx * 4], b);
 #pragma unroll
-      for (int x = 0; x < 8; ++x)
+      for (int x = 0; x < TM; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
     }
@@ -760,8 +769,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
   }
   Tacc* C = nsplit > 1 ? partial + (int64_t)split * g.I * g.ldc : (Tacc*)g.C;
 #pragma unroll
-  for (int x = 0; x < 8; ++x) {
-    const int64_t gi = i0 + ty * 8 + x;
+  for (int x = 0; x < TM; ++x) {
+    const int64_t gi = i0 + ty * TM + x;
     if (gi >= g.I) continue;
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
@@ -770,6 +779,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int nsplit, int64_t k
     }
   }
 }
+
+// Column tile of a GEMM: the narrowest of 64 / 32 / 16 that holds Jn.
+static int gemm_bn(const Gemm& g) { return g.Jn <= 16 ? 16 : g.Jn <= 32 ? 32 : GB_N; }
 
 template <typename Tacc>
 __global__ void gemm_reduce_kernel(Gemm g, int nsplit, const Tacc* partial) {
@@ -785,11 +797,13 @@ __global__ void gemm_reduce_kernel(Gemm g, int nsplit, const Tacc* partial) {
 }
 
 int gemm_choose_split(const Gemm& g) {
-  const int64_t tiles = ceil_div(g.I, GB_M) * ceil_div(g.Jn, GB_N);
+  const int64_t tiles = ceil_div(g.I, GB_M) * ceil_div(g.Jn, (int64_t)gemm_bn(g));
   const int64_t want = (int64_t)num_sms() * 4;
   if (tiles >= want) return 1;
   int64_t ns = ceil_div(want, tiles);
-  ns = std::min<int64_t>(ns, ceil_div(g.K, 256));
+  // reductions as short as 64 per split: small products spread over the
+  // GPU (binary64 runs at a few DFMA per clock per SM)
+  ns = std::min<int64_t>(ns, ceil_div(g.K, 64));
   return (int)std::max<int64_t>(1, std::min<int64_t>(ns, 512));
 }
 
@@ -799,12 +813,15 @@ static ttnn_status run_gemm(const Gemm& g, int nsplit, void* partial, cudaStream
   int64_t kchunk = round_up(ceil_div(g.K, nsplit), GB_K);
   nsplit = (int)ceil_div(g.K, kchunk);
   if (nsplit < 1) nsplit = 1;
-  dim3 grid((unsigned)ceil_div(g.I, GB_M), (unsigned)ceil_div(g.Jn, GB_N), (unsigned)nsplit);
+  const int bn = gemm_bn(g);
+  dim3 grid((unsigned)ceil_div(g.I, GB_M), (unsigned)ceil_div(g.Jn, (int64_t)bn), (unsigned)nsplit);
   if (grid.y > 65535 || grid.z > 65535) {
     set_error("gemm grid too large");
     return TTNN_EUNSUPPORTED;
   }
-  gemm_kernel<Tin, Tacc><<<grid, 256, 0, st>>>(g, nsplit, kchunk, (Tacc*)partial);
+  if (bn == 16) gemm_kernel<Tin, Tacc, 16><<<grid, 256, 0, st>>>(g, nsplit, kchunk, (Tacc*)partial);
+  else if (bn == 32) gemm_kernel<Tin, Tacc, 32><<<grid, 256, 0, st>>>(g, nsplit, kchunk, (Tacc*)partial);
+  else gemm_kernel<Tin, Tacc, GB_N><<<grid, 256, 0, st>>>(g, nsplit, kchunk, (Tacc*)partial);
   TTNN_TRY(check_launch("gemm_kernel"));
   if (nsplit > 1) {
     const int64_t n = g.I * g.ldc;
