@@ -42,6 +42,27 @@ struct Bump {
 ttnn_status mode_product(const void* in, int64_t P, int64_t NI, int64_t Q, int64_t J,
                          const void* W, int64_t NB, void* out, double alpha, int accumulate,
                          ElemType et, Bump& ws, cudaStream_t st) {
+  if (Q * J == 1 && alpha == 1.0 && !accumulate && P >= 512) {
+    // out[p][b] = sum_i in[p][i] W[i][b] with many rows: a plain GEMM
+    // (128-row tiles, split-K; fewer rows leave most of a tile idle)
+    Gemm g;
+    g.I = P;
+    g.Jn = NB;
+    g.K = NI;
+    g.A = in;
+    g.asi = NI;
+    g.ask = 1;
+    g.B = W;
+    g.bsj = 1;
+    g.bsk = NB;
+    g.C = out;
+    g.ldc = NB;
+    g.in_type = et == ET_F64 ? 0 : 1;
+    const int ns = gemm_choose_split(g);
+    char* part = ns > 1 ? ws.alloc((int64_t)ns * P * NB * (et == ET_F64 ? 8 : 4)) : nullptr;
+    if (ws.dry) return TTNN_OK;
+    return launch_gemm(g, ns, part, st);
+  }
   Contract c;
   c.P = P;
   c.NI = NI;
