@@ -795,9 +795,18 @@ def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=60.0):
                 stats["throttle_s"] += time.perf_counter() - tw
 
     def drain():
+        """Waits for every outstanding ticket; returns the time at which all
+        were done (a stream's requests complete in order, so its last ticket
+        done means all of its tickets are: those are waited on first, the
+        rest are then only collected)."""
+        for q in outstanding.values():
+            if q:
+                finish(q.pop())
+        t_done = time.perf_counter()
         for q in outstanding.values():
             while q:
                 finish(q.popleft())
+        return t_done
 
     sids, dims_of = [], []
     t_open = time.perf_counter()
@@ -841,8 +850,7 @@ def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=60.0):
         if now - ta > 1e-3:
             late += 1
         submit(sids[s_], dims_of[s_], mu, idx)
-    drain()
-    wall = time.perf_counter() - t0
+    wall = drain() - t0
     rep = api.ttnn_server_stats(srv)
     dev_bytes = rep["device_bytes"]
     offered = dict(throttled=stats["throttled"], throttle_s=stats["throttle_s"])
@@ -855,8 +863,7 @@ def run_serving(api, W, torch, n_streams=256, rate=22000.0, seconds=60.0):
     t1 = time.perf_counter()
     for (s_, mu, idx) in burst:
         submit(sids[s_], dims_of[s_], mu, idx)
-    drain()
-    cap_s = time.perf_counter() - t1
+    cap_s = drain() - t1
     cap = api.ttnn_server_stats(srv)
     api.ttnn_server_destroy(srv)
     return {"workload": f"{n_streams} streams (d 3-6, n in 16..128, binary/TT/Tucker, r 4-32, "
