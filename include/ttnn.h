@@ -366,8 +366,10 @@ ttnn_status ttnn_fp8_quantize(ttnn_plan_t plan, const float* src, const int64_t*
  * events around its phases on the stream it runs on.  ttnn_profile_read
  * synchronises those events and returns the summed milliseconds and the
  * number of recorded intervals of one phase since the last read, then clears
- * them.  phase 0 = first-level pass kernel(s), 1 = tree walk and
- * accumulation, 2 = recovery.  At most 4096 intervals are kept per phase. */
+ * them.  phase 0 = first-level pass kernel(s) with their partial-sum
+ * reductions, 1 = tree walk and accumulation, 2 = recovery, 3 = the
+ * tensor-core pass kernel alone (whole dense updates not batched by a
+ * server).  At most 4096 intervals are kept per phase. */
 ttnn_status ttnn_profile(ttnn_plan_t plan, int32_t enable);
 ttnn_status ttnn_profile_read(ttnn_plan_t plan, int32_t phase, double* total_ms, int32_t* count);
 /* Counts of first-level passes this plan has run on the tensor cores

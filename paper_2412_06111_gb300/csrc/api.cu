@@ -580,7 +580,7 @@ ttnn_status ttnn_profile(ttnn_plan_t P, int32_t enable) {
 }
 
 ttnn_status ttnn_profile_read(ttnn_plan_t P, int32_t phase, double* total_ms, int32_t* count) {
-  TTNN_CHECK_ARG(P && phase >= 0 && phase < 3, "bad argument");
+  TTNN_CHECK_ARG(P && phase >= 0 && phase < 4, "bad argument");
   double tot = 0.0;
   int cnt = 0;
   ttnn_status s = TTNN_OK;

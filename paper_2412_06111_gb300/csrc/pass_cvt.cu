@@ -635,6 +635,7 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
     tc::pass_cvt_kernel<tc::MODE_FP8><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
   }
   TTNN_TRY(check_launch("tc pass_cvt_kernel"));
+  if (P.prof_kernel_end) cudaEventRecord(P.prof_kernel_end, st);
   const int sms = tc::sm_count();
   tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,
                                                nR, P.wLpad, (float*)D2);

@@ -686,6 +686,7 @@ ttnn_status launch_tc_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int6
     tc::pass_kernel<<<g.grid, tc::kThreads, g.smem, st>>>(mA, mBR, mBL, prm);
     TTNN_TRY(check_launch("tc pass_kernel"));
   }
+  if (P.prof_kernel_end) cudaEventRecord(P.prof_kernel_end, st);
   const int sms = tc::sm_count();
   if (P.wLpad > 0) {
     tc::reduce_partials<<<sms * 4, 256, 0, st>>>(prm.D2p, g.G, (int64_t)g.C * g.tiles * tc::kTileN * P.wLpad,

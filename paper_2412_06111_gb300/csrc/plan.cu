@@ -1365,8 +1365,19 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
         return launch(P, data, nL, nR, sR, nR, sL, nL, D1, D2, tile_scale, tw, need, s, false,
                       nullptr);
       };
-      if (batch) batch->passes.push_back(go);
-      else TTNN_TRY(go(st));
+      if (batch) {
+        batch->passes.push_back(go);
+      } else {
+        // profiling: the pass kernel alone, from just before its launch to
+        // the event the launch records right after it
+        cudaEvent_t k0 = prof_event(P, st), k1 = nullptr;
+        if (k0 && cudaEventCreate(&k1) != cudaSuccess) k1 = nullptr;
+        P.prof_kernel_end = k1;
+        const ttnn_status ls = go(st);
+        P.prof_kernel_end = nullptr;
+        prof_push(P, 3, k0, k1);
+        TTNN_TRY(ls);
+      }
     }
     // released: in stream order the walk (which reuses the bytes) runs after
     // the pass, deferred or not

@@ -94,7 +94,10 @@ struct ttnn_plan_s {
   int last_walk_ops = 0, last_walk_levels = 0;   // shape of the last update's walk program
   // profiling: event pairs per phase (0 pass, 1 walk, 2 recovery)
   int profile = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[3];
+  // profiled intervals: 0 pass phase, 1 walk, 2 recovery, 3 the first-level
+  // pass kernel alone (to its end, before any partial-sum reduction)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[4];
+  cudaEvent_t prof_kernel_end = nullptr;   // recorded by a pass launch right after its kernel
   std::vector<cudaEvent_t> prof_pool;   // events of read intervals, reused
 };
 
