@@ -58,6 +58,8 @@ static void free_plan(ttnn_plan_s* P) {
   cudaFree(P->sideL);
   cudaFree(P->yW);
   cudaFree(P->xWo);
+  cudaFree(P->sideRs);
+  cudaFree(P->sideLs);
   cudaFree(P->dxy);
   cudaFree(P->ws);
   cudaFree(P->ws_rec);
@@ -226,6 +228,20 @@ ttnn_status ttnn_plan_create(const ttnn_tree* tree, int32_t d, const int64_t* di
     if (!yc.identity && !omega_via_d2(P, nL, nR)) {
       if ((s = palloc(&P.yW, (int64_t)yc.s * yc.n * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);
       if ((s = make_side_yw(P, fb, P.yW, yc.n, st))) return fail(s);
+    }
+    // binary32 plans whose whole-tensor pass fits the tensor cores: the side
+    // blocks split into bf16 hi + lo
+    if (P.dtype == TTNN_F32 && P.sideR && P.sideL && nL % 8 == 0 && nR % 8 == 0 &&
+        !(P.flags & TTNN_FLAG_SIMT_PASS)) {
+      const int64_t eR = (int64_t)P.wRpad * nR, eL = (int64_t)P.wLpad * nL;
+      if ((s = palloc(&P.sideRs, eR * 4)) != TTNN_OK) return fail(s);
+      if ((s = palloc(&P.sideLs, eL * 4)) != TTNN_OK) return fail(s);
+      if ((s = launch_split_bf16((const float*)P.sideR, eR, P.sideRs, (char*)P.sideRs + eR * 2,
+                                 st)) != TTNN_OK)
+        return fail(s);
+      if ((s = launch_split_bf16((const float*)P.sideL, eL, P.sideLs, (char*)P.sideLs + eL * 2,
+                                 st)) != TTNN_OK)
+        return fail(s);
     }
     if (omega_via_d2(P, nL, nR)) {
       if ((s = palloc(&P.xWo, (int64_t)P.rXL * nR * (P.walk_f64 ? 8 : 4))) != TTNN_OK) return fail(s);

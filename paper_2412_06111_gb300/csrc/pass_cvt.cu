@@ -32,6 +32,9 @@ constexpr int kConvThreads = 256;   // converter warps 6..13
 constexpr int kCvtThreads = 192 + kConvThreads;
 constexpr int MODE_SPLIT = 1;
 constexpr int MODE_FP8 = 2;
+constexpr int MODE_SPLIT3 = 3;   // binary32 M and binary32 DRM blocks, both split
+template <int MODE>
+__host__ __device__ constexpr bool is_split() { return MODE == MODE_SPLIT || MODE == MODE_SPLIT3; }
 
 struct CvtParams {
   int64_t nL, nR;
@@ -50,10 +53,12 @@ struct CvtParams {
 template <int MODE>
 struct Layout {
   // operand bytes (bf16 tiles the MMAs read), raw bytes kept apart from them
-  static constexpr uint32_t op = MODE == MODE_SPLIT ? 65536u : 32768u;
-  static constexpr uint32_t raw = MODE == MODE_SPLIT ? 0u : 16384u;
+  static constexpr uint32_t op = is_split<MODE>() ? 65536u : 32768u;
+  static constexpr uint32_t raw = is_split<MODE>() ? 0u : 16384u;
   // distance between the two 64-column boxes of one operand tile
-  static constexpr uint32_t box = MODE == MODE_SPLIT ? 32768u : 16384u;
+  static constexpr uint32_t box = is_split<MODE>() ? 32768u : 16384u;
+  // DRM blocks per stage / row block: bf16 (hi) or, SPLIT3, hi and lo
+  static constexpr uint32_t bparts = MODE == MODE_SPLIT3 ? 2u : 1u;
 };
 
 __device__ __forceinline__ void named_sync_conv() {
@@ -147,7 +152,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kCvtThreads, 1)
     pass_cvt_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapBR,
-                    const __grid_constant__ CUtensorMap mapBL, const CvtParams p) {
+                    const __grid_constant__ CUtensorMap mapBL,
+                    const __grid_constant__ CUtensorMap mapBRlo,
+                    const __grid_constant__ CUtensorMap mapBLlo, const CvtParams p) {
   using Lay = Layout<MODE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[4], bar_conv[4], bar_empty[4];
@@ -161,8 +168,8 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
   const int S = p.stages;
   const uint32_t br_bytes = (uint32_t)p.wRpad * 128 * 2;
   const uint32_t bl_bytes = (uint32_t)p.wLpad * 128 * 2;
-  const uint32_t stage_bytes = Lay::op + Lay::raw + br_bytes;
-  const uint32_t raw_tx = MODE == MODE_SPLIT ? 65536u : 16384u;
+  const uint32_t stage_bytes = Lay::op + Lay::raw + Lay::bparts * br_bytes;
+  const uint32_t raw_tx = is_split<MODE>() ? 65536u : 16384u;
   const uint32_t base = smem_u32(smem);
   const uint32_t bl_base = base + S * stage_bytes;
 
@@ -218,10 +225,15 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
         const int row = b * kTileM;
         ok = mbar_wait(smem_u32(&bar_blempty[ub]), ((u >> 1) & 1) ^ 1, &abort_flag);
         if (!ok) break;
-        const uint32_t blb = bl_base + ub * bl_bytes;
-        mbar_expect_tx(smem_u32(&bar_blfull[ub]), bl_bytes);
+        const uint32_t blb = bl_base + ub * Lay::bparts * bl_bytes;
+        mbar_expect_tx(smem_u32(&bar_blfull[ub]), Lay::bparts * bl_bytes);
         tma_2d(blb, &mapBL, row, 0, smem_u32(&bar_blfull[ub]), pol_keep);
         tma_2d(blb + bl_bytes / 2, &mapBL, row + 64, 0, smem_u32(&bar_blfull[ub]), pol_keep);
+        if (MODE == MODE_SPLIT3) {
+          tma_2d(blb + bl_bytes, &mapBLlo, row, 0, smem_u32(&bar_blfull[ub]), pol_keep);
+          tma_2d(blb + bl_bytes + bl_bytes / 2, &mapBLlo, row + 64, 0, smem_u32(&bar_blfull[ub]),
+                 pol_keep);
+        }
         bl_used |= 1u << ub;
         bl_ph = (bl_ph & ~(1u << ub)) | ((uint32_t)((u >> 1) & 1) << ub);
         for (int t = 0; t < nt; ++t) {
@@ -230,8 +242,8 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
           const uint32_t sb = base + stage * stage_bytes;
           const uint32_t bar = smem_u32(&bar_full[stage]);
           const int col = (int)(col0 + t * kTileN);
-          mbar_expect_tx(bar, raw_tx + br_bytes);
-          if (MODE == MODE_SPLIT) {
+          mbar_expect_tx(bar, raw_tx + Lay::bparts * br_bytes);
+          if (is_split<MODE>()) {
             tma_2d(sb, &mapA, col, row, bar, pol_stream);
             tma_2d(sb + 32768, &mapA, col + 64, row, bar, pol_stream);
           } else {
@@ -240,6 +252,10 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
           const uint32_t sbr = sb + Lay::op + Lay::raw;
           tma_2d(sbr, &mapBR, col, 0, bar, pol_keep);
           tma_2d(sbr + br_bytes / 2, &mapBR, col + 64, 0, bar, pol_keep);
+          if (MODE == MODE_SPLIT3) {
+            tma_2d(sbr + br_bytes, &mapBRlo, col, 0, bar, pol_keep);
+            tma_2d(sbr + br_bytes + br_bytes / 2, &mapBRlo, col + 64, 0, bar, pol_keep);
+          }
           used |= 1u << stage;
           last_ph = (last_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == S) {
@@ -264,7 +280,7 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
       // ---------------- MMA issuer ----------------
       const uint32_t id1 = idesc_bf16(kTileM, p.wRpad, false);
       const uint32_t id2 = idesc_bf16(kTileN, p.wLpad, true);
-      constexpr int nparts = MODE == MODE_SPLIT ? 2 : 1;   // hi (+ lo)
+      constexpr int nparts = is_split<MODE>() ? 2 : 1;   // hi (+ lo)
       int stage = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
         if (ok) ok = mbar_wait(smem_u32(&bar_blfull[buf]), (u >> 1) & 1, &abort_flag);
         if (!ok) break;
         fence_after();
-        const uint32_t blb = bl_base + buf * bl_bytes;
+        const uint32_t blb = bl_base + buf * Lay::bparts * bl_bytes;
         const uint32_t d1 = tmem + d1_col + buf * p.wRpad;
         for (int t = 0; t < nt; ++t) {
           ok = mbar_wait(smem_u32(&bar_conv[stage]), ph, &abort_flag);
@@ -292,6 +308,16 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
               mma_bf16(d1, da, db, id1, (part | t | kk) != 0);
             }
           }
+          if (MODE == MODE_SPLIT3) {
+            // hi part of M against the lo part of the DRM block
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t da = sdesc(sa + (kk >> 2) * Lay::box + (kk & 3) * 32, 16, 1024);
+              const uint64_t db =
+                  sdesc(sbr + br_bytes + (kk >> 2) * (br_bytes / 2) + (kk & 3) * 32, 16, 1024);
+              mma_bf16(d1, da, db, id1, true);
+            }
+          }
           const uint32_t d2 = tmem + d2_col + t * p.wLpad;
 #pragma unroll
           for (int part = 0; part < nparts; ++part) {
@@ -301,6 +327,15 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
               const uint64_t da = sdesc(pa + kk * 2048, Lay::box, 1024);
               const uint64_t db = sdesc(blb + (kk >> 2) * (bl_bytes / 2) + (kk & 3) * 32, 16, 1024);
               mma_bf16(d2, da, db, id2, (part | u | kk) != 0);
+            }
+          }
+          if (MODE == MODE_SPLIT3) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t da = sdesc(sa + kk * 2048, Lay::box, 1024);
+              const uint64_t db =
+                  sdesc(blb + bl_bytes + (kk >> 2) * (bl_bytes / 2) + (kk & 3) * 32, 16, 1024);
+              mma_bf16(d2, da, db, id2, true);
             }
           }
           mma_commit(smem_u32(&bar_empty[stage]));
@@ -339,7 +374,7 @@ __global__ void __launch_bounds__(kCvtThreads, 1)
         ok = conv_all(mbar_wait(smem_u32(&bar_full[stage]), ph, &abort_flag));
         if (!ok) break;
         uint8_t* st = smem + stage * stage_bytes;
-        if (MODE == MODE_SPLIT) {
+        if (is_split<MODE>()) {
           convert_split_half(st, 0, ct);
           convert_split_half(st, 1, ct);
         } else {
@@ -450,10 +485,12 @@ static bool cvt_geometry(int mode, const ttnn_plan_s& P, int64_t nL, int64_t nR,
   if (tiles < 1) return false;
   // as few chunks as TMEM allows, tiles spread evenly over them
   tiles = (int)((ntile + (ntile + tiles - 1) / tiles - 1) / ((ntile + tiles - 1) / tiles));
-  const int64_t op = mode == MODE_SPLIT ? 65536 : 32768, raw = mode == MODE_SPLIT ? 0 : 16384;
-  const int64_t stage_bytes = op + raw + (int64_t)P.wRpad * 256;
-  const int64_t bl = 2 * (int64_t)P.wLpad * 256;
-  const int stages = (int)std::min<int64_t>(mode == MODE_SPLIT ? 3 : 4,
+  const bool split = mode == MODE_SPLIT || mode == MODE_SPLIT3;
+  const int64_t bparts = mode == MODE_SPLIT3 ? 2 : 1;
+  const int64_t op = split ? 65536 : 32768, raw = split ? 0 : 16384;
+  const int64_t stage_bytes = op + raw + bparts * (int64_t)P.wRpad * 256;
+  const int64_t bl = 2 * bparts * (int64_t)P.wLpad * 256;
+  const int stages = (int)std::min<int64_t>(split ? 3 : 4,
                                             (kSmemBudget - 1024 - bl) / stage_bytes);
   if (stages < 2) return false;
   g->tiles = tiles;
@@ -552,7 +589,29 @@ ttnn_status launch_quantize_fp8(const float* src, int64_t rows, int64_t cols, ui
 }
 
 static int cvt_mode(const ttnn_plan_s& P) {
+  if (P.dtype == TTNN_F32) return P.sideRs && P.sideLs ? tc::MODE_SPLIT3 : 0;
   return P.dtype == TTNN_BF16X2 ? tc::MODE_SPLIT : P.dtype == TTNN_E4M3 ? tc::MODE_FP8 : 0;
+}
+
+// hi = bf16(x), lo = bf16(x - hi) (both rounded to nearest; x - hi is exact
+// in binary32): the two bfloat16 blocks a binary32 DRM block is carried as
+// on the tensor cores.
+__global__ void split_bf16_kernel(const float* src, int64_t n, __nv_bfloat16* hi,
+                                  __nv_bfloat16* lo) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float x = src[e];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+ttnn_status launch_split_bf16(const float* src, int64_t n, void* hi, void* lo, cudaStream_t st) {
+  if (n == 0) return TTNN_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)tc::sm_count() * 16);
+  split_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, n, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+  return check_launch("split_bf16_kernel");
 }
 
 ttnn_status cvt_pass_supported(const ttnn_plan_s& P, int64_t nL, int64_t nR) {
@@ -595,17 +654,34 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
     set_error("E4M3 pass: tile scales missing or misaligned");
     return TTNN_EINVAL;
   }
-  CUtensorMap mA, mBR, mBL;
-  if (mode == tc::MODE_SPLIT)
+  CUtensorMap mA, mBR, mBL, mBRlo, mBLlo;
+  if (mode == tc::MODE_SPLIT || mode == tc::MODE_SPLIT3)
     TTNN_TRY(tc::encode_map(&mA, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nR, nL, 64u, 128u,
                             CU_TENSOR_MAP_SWIZZLE_NONE));
   else
     TTNN_TRY(tc::encode_map(&mA, A, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, nR, nL, 128u, 128u,
                             CU_TENSOR_MAP_SWIZZLE_NONE));
-  TTNN_TRY(tc::encode_map(&mBR, sR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nR, P.wRpad, 64u,
+  // SPLIT3: the plan's whole-tensor blocks as bf16 hi and lo halves
+  const void* bR = sR;
+  const void* bL = sL;
+  if (mode == tc::MODE_SPLIT3) {
+    bR = P.sideRs;
+    bL = P.sideLs;
+  }
+  TTNN_TRY(tc::encode_map(&mBR, bR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nR, P.wRpad, 64u,
                           (uint32_t)P.wRpad, CU_TENSOR_MAP_SWIZZLE_128B));
-  TTNN_TRY(tc::encode_map(&mBL, sL, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nL, P.wLpad, 64u,
+  TTNN_TRY(tc::encode_map(&mBL, bL, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nL, P.wLpad, 64u,
                           (uint32_t)P.wLpad, CU_TENSOR_MAP_SWIZZLE_128B));
+  mBRlo = mBR;
+  mBLlo = mBL;
+  if (mode == tc::MODE_SPLIT3) {
+    TTNN_TRY(tc::encode_map(&mBRlo, (const char*)bR + (int64_t)P.wRpad * nR * 2,
+                            CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nR, P.wRpad, 64u,
+                            (uint32_t)P.wRpad, CU_TENSOR_MAP_SWIZZLE_128B));
+    TTNN_TRY(tc::encode_map(&mBLlo, (const char*)bL + (int64_t)P.wLpad * nL * 2,
+                            CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nL, P.wLpad, 64u,
+                            (uint32_t)P.wLpad, CU_TENSOR_MAP_SWIZZLE_128B));
+  }
   tc::CvtParams prm;
   prm.nL = nL;
   prm.nR = nR;
@@ -629,10 +705,16 @@ ttnn_status launch_cvt_pass(const ttnn_plan_s& P, const void* A, int64_t nL, int
   if (g.C > 1) TTNN_TRY_CUDA(cudaMemsetAsync(prm.cnt, 0, (size_t)g.nb * 16, st));
   if (mode == tc::MODE_SPLIT) {
     TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_SPLIT>, 1));
-    tc::pass_cvt_kernel<tc::MODE_SPLIT><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
+    tc::pass_cvt_kernel<tc::MODE_SPLIT><<<g.grid, tc::kCvtThreads, g.smem, st>>>(
+        mA, mBR, mBL, mBRlo, mBLlo, prm);
+  } else if (mode == tc::MODE_SPLIT3) {
+    TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_SPLIT3>, 3));
+    tc::pass_cvt_kernel<tc::MODE_SPLIT3><<<g.grid, tc::kCvtThreads, g.smem, st>>>(
+        mA, mBR, mBL, mBRlo, mBLlo, prm);
   } else {
     TTNN_TRY(tc::smem_limit_once((const void*)tc::pass_cvt_kernel<tc::MODE_FP8>, 2));
-    tc::pass_cvt_kernel<tc::MODE_FP8><<<g.grid, tc::kCvtThreads, g.smem, st>>>(mA, mBR, mBL, prm);
+    tc::pass_cvt_kernel<tc::MODE_FP8><<<g.grid, tc::kCvtThreads, g.smem, st>>>(
+        mA, mBR, mBL, mBRlo, mBLlo, prm);
   }
   TTNN_TRY(check_launch("tc pass_cvt_kernel"));
   if (P.prof_kernel_end) cudaEventRecord(P.prof_kernel_end, st);

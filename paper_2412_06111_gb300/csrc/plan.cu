@@ -1322,8 +1322,12 @@ ttnn_status run_dense_update(ttnn_plan_s& P, void* acc, const void* data, const 
   // the pass's own temporaries are released right after it and are not
   // program buffers: keep them out of the dependency registry
   ws.prog = nullptr;
-  const bool cvt = P.dtype == TTNN_BF16X2 || P.dtype == TTNN_E4M3;
-  const bool use_tc = P.tc_ok && !(P.flags & TTNN_FLAG_SIMT_PASS) &&
+  // binary32 plans: whole-tensor updates on the tensor cores with the split
+  // (bf16 hi + lo) data and DRM blocks
+  const bool f32s = P.dtype == TTNN_F32 && box.full && P.sideRs && P.sideLs &&
+                    !(P.flags & TTNN_FLAG_SIMT_PASS);
+  const bool cvt = P.dtype == TTNN_BF16X2 || P.dtype == TTNN_E4M3 || f32s;
+  const bool use_tc = (P.tc_ok || f32s) && !(P.flags & TTNN_FLAG_SIMT_PASS) &&
                       (cvt ? cvt_pass_supported(P, nL, nR) : tc_pass_supported(P, nL, nR)) ==
                           TTNN_OK;
   if (r1) {

@@ -66,6 +66,10 @@ struct ttnn_plan_s {
   void* sideL = nullptr;
   void* yW = nullptr;           // walk-type copy of the pass Y block (full box)
   void* xWo = nullptr;          // walk-type copy of the L side's X block over the R modes (full box)
+  // binary32 plans: the cached side blocks as bf16 hi then lo halves (the
+  // tensor-core pass of whole-tensor updates)
+  void* sideRs = nullptr;
+  void* sideLs = nullptr;
   void* dxy = nullptr;          // unstructured DRMs of every node, walk type (TTNN_FLAG_DENSE_DRM)
   char* ws = nullptr;
   int64_t ws_bytes = 0;
@@ -171,6 +175,7 @@ ttnn_status launch_quantize_fp8(const float* src, int64_t rows, int64_t cols, ui
 // to *defer instead of launched (blocks that need computing are launched).
 ttnn_status make_side(ttnn_plan_s& P, const Box& box, int which, void* out, int64_t ld,
                       cudaStream_t st, std::vector<GatherJob>* defer = nullptr);
+ttnn_status launch_split_bf16(const float* src, int64_t n, void* hi, void* lo, cudaStream_t st);
 ttnn_status make_side_xo(ttnn_plan_s& P, const Box& box, void* out, int64_t ld, cudaStream_t st);
 // Omega of an L-side Y child is taken through D2 (a reduction over the R
 // index) for whole 2-D boxes of nL x nR
