@@ -164,7 +164,35 @@ __device__ __forceinline__ void fold_d1_rows(int* slot, int C, const float* D1p,
   const float4* src = reinterpret_cast<const float4*>(D1p) + row0 * per;
   float4* out = reinterpret_cast<float4*>(D1) + row0 * per;
   const int n4 = 32 * per;
-  for (int e0 = lane; e0 < n4; e0 += 128) {
+  if (C <= 4) {
+    // every partial's loads of a batch in flight at once (one L2 round trip
+    // per batch instead of one per partial), then the sums in chunk order
+    for (int e0 = lane; e0 < n4; e0 += 128) {
+      float4 v[4][4];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = e0 + 32 * j;
+          v[cc][j] = (cc < C && e < n4) ? __ldcg(src + cc * cs4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float4 acc = v[0][j];
+#pragma unroll
+        for (int cc = 1; cc < 4; ++cc) {
+          if (cc >= C) break;
+          acc.x += v[cc][j].x;
+          acc.y += v[cc][j].y;
+          acc.z += v[cc][j].z;
+          acc.w += v[cc][j].w;
+        }
+        const int e = e0 + 32 * j;
+        if (e < n4 && e < lim) out[e] = acc;
+      }
+    }
+  }
+  for (int e0 = lane; C > 4 && e0 < n4; e0 += 128) {
     float4 acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
