@@ -75,6 +75,59 @@ ttnn_status launch_convert_f64_to_f32(const double* src, float* dst, int64_t n, 
   return check_launch("convert_kernel");
 }
 
+// Several binary64 -> binary32 copies in one launch: block b converts
+// kConvBlock consecutive elements of the segment whose block range holds b,
+// two per load (16-byte loads, 8-byte stores) when the segment's ends allow.
+constexpr int kConvBlock = 2048;
+
+__global__ void convert_batch_kernel(const __grid_constant__ ConvertBatch b) {
+  int lo = 0, hi = b.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (b.start[mid] <= (int64_t)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const double* src = b.src[lo];
+  float* dst = b.dst[lo];
+  const int64_t n = b.n[lo];
+  const int64_t e0 = ((int64_t)blockIdx.x - b.start[lo]) * kConvBlock;
+  const int64_t e1 = e0 + kConvBlock < n ? e0 + kConvBlock : n;
+  if (b.pairs[lo]) {
+    // e0 is even and both pointers are aligned for pairs
+    for (int64_t e = e0 + 2 * threadIdx.x; e < e1; e += 2 * blockDim.x) {
+      if (e + 1 < e1) {
+        const double2 v = *reinterpret_cast<const double2*>(src + e);
+        *reinterpret_cast<float2*>(dst + e) = make_float2((float)v.x, (float)v.y);
+      } else {
+        dst[e] = (float)src[e];
+      }
+    }
+  } else {
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) dst[e] = (float)src[e];
+  }
+}
+
+ttnn_status launch_convert_batch(const ConvertBatch& batch, cudaStream_t st) {
+  if (batch.count <= 0 || batch.count > kConvertSegs) {
+    set_error("internal: conversion batch of %d segments", batch.count);
+    return TTNN_EUNSUPPORTED;
+  }
+  ConvertBatch b = batch;
+  int64_t blocks = 0;
+  for (int k = 0; k < b.count; ++k) {
+    b.start[k] = blocks;
+    b.pairs[k] = ((uintptr_t)b.src[k] % 16 == 0) && ((uintptr_t)b.dst[k] % 8 == 0);
+    blocks += ceil_div(b.n[k], (int64_t)kConvBlock);
+  }
+  if (blocks == 0) return TTNN_OK;
+  if (blocks >= (int64_t(1) << 31)) {
+    set_error("conversion batch too large");
+    return TTNN_EUNSUPPORTED;
+  }
+  convert_batch_kernel<<<(unsigned)blocks, 256, 0, st>>>(b);
+  return check_launch("convert_batch_kernel");
+}
+
 // ---------------------------------------------------------------------------
 // pass-side Khatri-Rao blocks
 // ---------------------------------------------------------------------------

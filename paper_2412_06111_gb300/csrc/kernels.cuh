@@ -61,6 +61,18 @@ int gemm_choose_split(const Gemm& g);
 ttnn_status launch_philox(uint64_t seed, int kind, int ident, int64_t rows, int64_t cols,
                           int round_fmt, double* dst, cudaStream_t st);
 ttnn_status launch_convert_f64_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+// Up to kConvertSegs binary64 -> binary32 copies (dst[k][e] = (float)src[k][e],
+// e < n[k]) in one launch; start / pairs are filled by the launcher.
+constexpr int kConvertSegs = 64;
+struct ConvertBatch {
+  int count = 0;
+  const double* src[kConvertSegs];
+  float* dst[kConvertSegs];
+  int64_t n[kConvertSegs];
+  int64_t start[kConvertSegs];
+  int pairs[kConvertSegs];
+};
+ttnn_status launch_convert_batch(const ConvertBatch& batch, cudaStream_t st);
 
 // Side (pass DRM) block: out[col][row] for col < w, row < nrows (leading dim
 // ld_out >= nrows), in the pass storage format (0 f64, 1 f32, 2 bf16, 3 e4m3).

@@ -1685,6 +1685,7 @@ ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores
   auto R = [&](int v) { return (int64_t)ranks_in[v]; };
   // input cores in the walk type (binary32 plans: converted copies)
   std::vector<const char*> core(nn, nullptr);
+  ConvertBatch conv;
   for (int v = 0; v < nn; ++v) {
     const TNode& nd = P.nodes[v];
     int64_t el = 1;
@@ -1697,10 +1698,18 @@ ttnn_status run_ttn_update(ttnn_plan_s& P, void* acc, const double* const* cores
       prog.buffer(core[v], el * 8);
     } else {
       char* b = ws.alloc(el * 4);
-      if (!dry) TTNN_TRY(launch_convert_f64_to_f32(cores_in[v], (float*)b, el, st));
+      if (conv.count == kConvertSegs) {
+        if (!dry) TTNN_TRY(launch_convert_batch(conv, st));
+        conv.count = 0;
+      }
+      conv.src[conv.count] = cores_in[v];
+      conv.dst[conv.count] = (float*)b;
+      conv.n[conv.count] = el;
+      ++conv.count;
       core[v] = b;
     }
   }
+  if (!dry && conv.count > 0) TTNN_TRY(launch_convert_batch(conv, st));
   auto core_view = [&](int v) {
     const TNode& nd = P.nodes[v];
     View w;
