@@ -675,7 +675,11 @@ __global__ void __launch_bounds__(kExecThreads, 3) level_kernel(const __grid_con
 // The split-K GEMM ops of a level in a kernel of their own: its code stays
 // small enough for the instruction caches (the generic level kernel's many op
 // kinds do not, and its ops stall on instruction fetch).
-__global__ void __launch_bounds__(kExecThreads, 2) kgemm_level_kernel(const __grid_constant__ LevelBatch lb) {
+// MINB resident blocks per SM: 2 (128 registers) for levels of a few waves,
+// 3 (80 registers) for levels of many waves, where the extra warps hide more
+// shared-memory latency and the coarser last wave costs little.
+template <int MINB>
+__global__ void __launch_bounds__(kExecThreads, MINB) kgemm_level_kernel(const __grid_constant__ LevelBatch lb) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int64_t b = blockIdx.x;
   int lo = 0, hi = lb.nops - 1;
@@ -948,7 +952,11 @@ ttnn_status Program::run(cudaStream_t st, bool dump) {
         return TTNN_EUNSUPPORTED;
       }
       if (k == 0) {
-        kgemm_level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, gst>>>(b);
+        // at least three full waves at three blocks per SM: the 80-register form
+        if (blocks >= 9 * (int64_t)exec_sms())
+          kgemm_level_kernel<3><<<(unsigned)blocks, kExecThreads, kExecSmem, gst>>>(b);
+        else
+          kgemm_level_kernel<2><<<(unsigned)blocks, kExecThreads, kExecSmem, gst>>>(b);
         TTNN_TRY(check_launch("kgemm_level_kernel"));
       } else {
         level_kernel<<<(unsigned)blocks, kExecThreads, kExecSmem, st>>>(b);
