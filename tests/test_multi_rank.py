@@ -92,3 +92,34 @@ def test_slab_sketches_allreduce_to_whole_tensor_sketch(tmp_path, world):
     A = O.reconstruct(t, O.recover(t, got, gps, gpr)[0])
     B = O.reconstruct(t, O.recover(t, Om, Ps, Pr)[0])
     assert np.linalg.norm(A - B) <= 1e-10 * np.linalg.norm(B)
+
+
+def _bench_rank_main(rank, world, port, out_dir):
+    """One CPU rank of the bench's launch bookkeeping: _dist() joins the
+    process group from the torchrun environment variables (gloo without a
+    GPU), _barrier() and _max_over_ranks() give every rank the slowest rank's
+    time, as the timed region of the multi-GPU bench does."""
+    # CPU ranks even on a machine with a GPU (no two ranks on one device)
+    os.environ["CUDA_VISIBLE_DEVICES"] = ""
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    r, ws = bench._dist()
+    assert (r, ws) == (rank, world)
+    assert dist.get_backend() == "gloo"
+    bench._barrier(ws)
+    ms = 1.0 + 0.25 * rank                      # each rank's own step time
+    got = bench._max_over_ranks(ms, ws)
+    np.save(os.path.join(out_dir, f"bench{rank}.npy"), np.array([got]))
+    bench._barrier(ws)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_bench_timing_takes_the_slowest_rank(tmp_path, world):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.spawn(_bench_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    for r in range(world):
+        assert np.load(tmp_path / f"bench{r}.npy")[0] == 1.0 + 0.25 * (world - 1)
