@@ -67,3 +67,56 @@ def test_rounding_input_is_a_direct_sum_with_the_stated_norms():
         assert np.sum(s_all > 1e-10 * s_all[0]) == min(rd + rn, *M.shape)
         checked += 1
     assert checked == len(tr[0]) - 1
+
+
+def test_streaming_updates_recipe():
+    # rank-2 CP term with N(0, 1) factors + one 32^3 box of N(0, 0.01) values
+    # over three distinct modes, the other modes fixed at one index
+    dims = [32] * 6
+    ups = W.streaming_updates(dims, 64, 5)
+    vals = []
+    for u in ups:
+        assert np.array_equal(u["cp_weights"], np.ones(2))
+        assert [f.shape for f in u["cp_factors"]] == [(32, 2)] * 6
+        ext, off = u["box_extent"], u["box_offset"]
+        assert sorted(ext) == [1, 1, 1, 32, 32, 32]
+        assert all(0 <= o and o + e <= n for o, e, n in zip(off, ext, dims))
+        assert u["box_data"].shape == tuple(ext)
+        vals.append(u["box_data"].ravel())
+    v = np.concatenate(vals)
+    assert abs(v.std() - 0.1) < 0.002 and abs(v.mean()) < 0.002
+
+
+def test_hilbert_entries():
+    H = W.hilbert(3, 4)
+    for idx in itertools.product(range(4), repeat=3):
+        assert H[idx] == 1.0 / (1.0 + sum(idx))
+
+
+def test_serving_stream_specs_stay_in_the_stated_ranges():
+    rng = np.random.default_rng(9)
+    kinds = set()
+    for _ in range(400):
+        sp = W.serving_stream_spec(rng)
+        d = len(sp["dims"])
+        assert 3 <= d <= 6 and set(sp["dims"]) <= {16, 32, 64, 128}
+        assert np.prod(sp["dims"], dtype=float) <= 2e8
+        assert 4 <= sp["r"] <= 32 and sp["p"] == sp["r"] // 2
+        parent, leaf_modes, _ = sp["tree"]
+        assert sorted(m for lm in leaf_modes for m in lm) == list(range(d))
+        kinds.add(sp["kind"])
+    assert kinds == {"binary", "tt", "tucker"}
+
+
+def test_poisson_slices_rate_and_choices():
+    rng = np.random.default_rng(3)
+    dims_of = [[16, 32, 64], [128, 16, 16, 16]]
+    ev = W.poisson_slices(rng, 2, dims_of, 2000.0, 5.0)
+    t = np.array([e[0] for e in ev])
+    assert np.all(np.diff(t) > 0) and t[-1] < 5.0
+    # 10000 arrivals expected; a Poisson count has standard deviation 100
+    assert abs(len(ev) - 10000) < 500
+    for _, s, mu, i in ev:
+        assert 0 <= s < 2 and 0 <= mu < len(dims_of[s]) and 0 <= i < dims_of[s][mu]
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() * 2000.0 - 1.0) < 0.05
