@@ -56,6 +56,8 @@ def _kind_py(t):
 
 def test_every_bound_function_matches_its_declaration():
     decl = _declarations()
+    # the binding covers exactly the declared entry points
+    assert set(decl) == set(S.SIGS), sorted(set(decl) ^ set(S.SIGS))
     for name, (res, args) in S.SIGS.items():
         assert name in decl, name
         ret, params = decl[name]
