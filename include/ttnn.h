@@ -71,7 +71,10 @@ typedef enum {
   TTNN_EINVAL = 1,       /* invalid argument, tree, size or pointer */
   TTNN_ENOMEM = 2,       /* device or host allocation failed */
   TTNN_ECUDA = 3,        /* a CUDA call or kernel launch failed */
-  TTNN_ENUMERIC = 4,     /* non-finite values met (e.g. NaN in an update) */
+  TTNN_ENUMERIC = 4,     /* non-finite values; reserved: non-finite scalar arguments
+                            (CP weights, lambda) are refused with TTNN_EINVAL, and tensor
+                            data are not scanned (a NaN or Inf in an update reaches the
+                            sketches and the recovered cores) */
   TTNN_ETIMEOUT = 5,     /* a bounded device wait ran out */
   TTNN_EBUSY = 6,        /* resource in use (serving: no free slot) */
   TTNN_EUNSUPPORTED = 7  /* valid request this library does not implement */

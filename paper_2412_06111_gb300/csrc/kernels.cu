@@ -964,35 +964,4 @@ ttnn_status launch_eye(double* dst, int64_t n, cudaStream_t st) {
   return check_launch("eye_kernel");
 }
 
-template <typename T>
-__global__ void finite_kernel(const T* x, int64_t n, int* flag) {
-  bool bad = false;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const float v = to_f32(x[e]);
-    if (!isfinite(v)) bad = true;
-  }
-  if (bad) atomicOr(flag, 1);
-}
-
-__global__ void finite_kernel_f64(const double* x, int64_t n, int* flag) {
-  bool bad = false;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    if (!isfinite(x[e])) bad = true;
-  if (bad) atomicOr(flag, 1);
-}
-
-ttnn_status launch_finite_check(const void* data, int64_t n, int type, int* flag, cudaStream_t st) {
-  if (n == 0) return TTNN_OK;
-  const int64_t blocks = std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
-  switch (type) {
-    case 0: finite_kernel_f64<<<(unsigned)blocks, 256, 0, st>>>((const double*)data, n, flag); break;
-    case 1: finite_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float*)data, n, flag); break;
-    case 2: finite_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>((const __nv_bfloat16*)data, n, flag); break;
-    default: return TTNN_OK;
-  }
-  return check_launch("finite_kernel");
-}
-
 }  // namespace ttnn

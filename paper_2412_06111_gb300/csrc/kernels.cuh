@@ -139,7 +139,6 @@ ttnn_status launch_to_walk(const void* src, int src_store, const float* scale, v
 ttnn_status launch_fill_zero(void* p, int64_t bytes, cudaStream_t st);
 ttnn_status launch_axpy(void* y, const void* x, double alpha, int64_t n, int is_f64, cudaStream_t st);
 ttnn_status launch_eye(double* dst, int64_t n, cudaStream_t st);
-ttnn_status launch_finite_check(const void* data, int64_t n, int type, int* flag, cudaStream_t st);
 
 // Recovery (binary64): for each job, QR of Omega (s x r, state type) into
 // Q (s x r) with diag R >= 0, one-sided Jacobi SVD of R and the
