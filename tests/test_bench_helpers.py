@@ -77,3 +77,23 @@ def test_network_inner_product_equals_the_dense_one(name):
     want = float(np.vdot(W.ttn_dense(tree, A), W.ttn_dense(tree, B)))
     got = bench._ttn_inner(parent, ch, A, B)
     assert abs(got - want) <= 1e-12 * max(1.0, abs(want)) * 10
+
+
+@pytest.mark.parametrize("ws", [1, 2, 4, 8])
+def test_weak_scaling_slabs(ws):
+    """Under N ranks the bench's tensor has N * 64 points on mode 0 and rank k
+    owns the 64 x 64^4 slab at mode-0 offset 64 k (the whole tensor at N = 1):
+    every rank streams a 64^5 block, and the slabs tile the tensor."""
+    n = bench.NMODE
+    covered = []
+    for rank in range(ws):
+        dims, (off, ext) = bench._geometry(ws, rank)
+        assert dims == [n * ws] + [n] * (bench.D - 1)
+        if ws == 1:
+            assert off is None and ext is None
+            covered.append((0, n))
+            continue
+        assert ext == [n] * bench.D
+        assert off == [n * rank] + [0] * (bench.D - 1)
+        covered.append((off[0], off[0] + ext[0]))
+    assert sorted(covered) == [(n * k, n * (k + 1)) for k in range(ws)]
